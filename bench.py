@@ -1,0 +1,349 @@
+"""Benchmark: aFSAI set-up + PCG to relative residual 1e-8 on one GB300.
+
+Workload (default): FP64 aFSAI-PCG on 3D linear elasticity, trilinear hex
+elements on a 48^3 grid, 3 dofs per node (n = 352,947, ~27M nonzeros),
+Young's modulus lognormal (sigma 1) per element, Poisson ratio 0.3, z = 0
+face clamped; kiter = 10, s = 3, eps = 1e-3; seeded right-hand side
+b = A x*, x* ~ U[-1, 1].  A step is one whole solve: aFSAI set-up (pattern
+search, gather, Cholesky, scaling, G^T) followed by PCG from x = 0 until
+||r|| <= 1e-8 ||b||, with A and b resident in device memory.  The metric is
+seconds per solve (lower is better).
+
+Other keys of the JSON line:
+  e2e          the same solve through afsai_solve_host from pinned host
+               buffers (H2D of A and b, D2H of x inside the timed region)
+  mixed        the precision form on the same input (FP32 G, FP32 Cholesky
+               with one FP64 refinement step), seconds per solve
+  roofline     the dominant kernel against its roof (measured with CUDA
+               events on the launching stream inside the timed region)
+  cpu_baseline the FP64 CPU oracle on a bounded sample of the same solve,
+               scaled to seconds per solve
+  clocks       SM clocks and throttle reasons sampled during the timed region
+
+--impl reference times the CPU oracle (the only reference this method has:
+the paper's code is not public) on the host cores for the same workload.
+Multi-GPU (--gpus N under torchrun): every rank solves its own copy of the
+workload (independent problems, no collective on the data path); value is
+the max-over-ranks time divided by the number of solves of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "aFSAI set-up+PCG s/solve to relres 1e-8 (FP64; mixed reported beside)"
+WORKLOAD = "elasticity_hex48_fp64"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--scale", type=int, default=None, help="grid size override (testing only)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "gb300" else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(v, world, device=None):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sms) if sms else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def setup_flops(rowptr_G, steps, s, nnz_row_avg):
+    """Algorithmic FP64 flops of the set-up: per row and step k with pattern
+    size m_k: m_k^3/3 (Cholesky) + 2 m_k^2 (triangular solves) +
+    2 nnz_row |P_{k-1}| (Kaporin gradient), with m_k = min(1 + k s, m_final)."""
+    m_final = np.diff(rowptr_G).astype(np.float64)
+    total = 0.0
+    kmax = int(steps.max()) if steps.size else 0
+    for k in range(1, kmax + 1):
+        act = steps >= k
+        mk = np.minimum(1 + k * s, m_final[act])
+        mprev = np.minimum(1 + (k - 1) * s, m_final[act])
+        total += float(np.sum(mk ** 3 / 3.0 + 2 * mk ** 2 + 2 * nnz_row_avg * mprev))
+    return total
+
+
+def spmv_bytes(n, nnz, val_bytes=8, x_bytes=8, y_bytes=8):
+    """Compulsory bytes of y = A x: values, columns, row pointers, x once,
+    y once."""
+    return nnz * (val_bytes + 4) + 4 * (n + 1) + n * x_bytes + n * y_bytes
+
+
+def make_workload(scale):
+    from paper_2010_14175_gb300 import matgen as mg
+
+    A, b, xs, p = mg.workload("elast48", scale=scale)
+    return A, b, p
+
+
+def cpu_oracle_estimate(A, b, p, iters, pcg_iters=10):
+    """The CPU oracle on a bounded sample of one solve: its full FP64 set-up
+    (timed) plus `pcg_iters` oracle PCG iterations with that G (timed),
+    scaled to `iters` iterations."""
+    import oracle
+
+    t0 = time.perf_counter()
+    G = oracle.afsai_setup(A, p["kiter"], p["s"], p["eps"])
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.pcg(A, G, b, rtol=1e-300, maxit=pcg_iters)
+    t_it = (time.perf_counter() - t0) / pcg_iters
+    return t_setup + t_it * iters, oracle.num_threads(), (
+        f"full oracle set-up ({t_setup:.2f} s) + {pcg_iters} oracle PCG iterations "
+        f"({t_it * 1e3:.1f} ms each) scaled to {iters} iterations")
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the CPU oracle on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import oracle
+
+    A, b, p = make_workload(args.scale)
+    # iteration count of the oracle's own full solve (measured once)
+    G = oracle.afsai_setup(A, p["kiter"], p["s"], p["eps"])
+    _, iters, _, rt = oracle.pcg(A, G, b, rtol=1e-8, maxit=20000)
+    del G
+    for _ in range(args.warmup):
+        cpu_oracle_estimate(A, b, p, iters)
+    vals = []
+    for _ in range(args.steps):
+        v, cores, sample = cpu_oracle_estimate(A, b, p, iters)
+        vals.append(v)
+    value = float(np.median(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "s/solve", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
+        "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "kiter": p["kiter"], "s": p["s"],
+                   "eps": p["eps"], "rtol": 1e-8, "oracle_iters": iters, "oracle_relres_true": rt},
+        "cpu_baseline": {"value": value, "unit": "s/solve", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "s/solve", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+
+    from paper_2010_14175_gb300 import afsai
+
+    assert torch.cuda.is_available(), "bench needs a GPU"
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = afsai.load()
+    A, b, p = make_workload(args.scale)
+    Ad = afsai.DeviceCSR.from_host(A, device=dev)
+    bd = torch.from_numpy(b).to(dev)
+    x = torch.zeros_like(bd)
+    stream = torch.cuda.current_stream(dev)
+    prm = afsai.params(p["kiter"], p["s"], p["eps"])
+    prm_mixed = afsai.params(p["kiter"], p["s"], p["eps"], 0, 1, 1)
+
+    def one_solve(prm_):
+        x.zero_()
+        M = afsai.afsai_setup(Ad, prm_, stream)
+        info = afsai.pcg_solve(Ad, M, bd, x, rtol=1e-8, maxit=20000, stream=stream)
+        sinfo = M.info()
+        return M, sinfo, info
+
+    for _ in range(args.warmup):
+        M, sinfo, pinfo = one_solve(prm)
+        M.close()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = afsai.kernel_launches()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    setup_ms, solve_ms, iters, kernel_ms = [], [], [], []
+    ev0.record(stream)
+    last = None
+    for _ in range(args.steps):
+        M, sinfo, pinfo = one_solve(prm)
+        setup_ms.append(sinfo["setup_ms"])
+        kernel_ms.append(sinfo["kernel_ms"])
+        solve_ms.append(pinfo["solve_ms"])
+        iters.append(pinfo["iters"])
+        if last is not None:
+            last[0].close()
+        last = (M, sinfo, pinfo)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = afsai.kernel_launches() - launches0
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    ms_total = max_over_ranks(ms_total, world, dev)
+    M, sinfo, pinfo = last
+    value = ms_total / 1e3 / (args.steps * world)
+
+    # dominant kernel: the fused set-up kernel (one launch per step)
+    kern_ms = float(np.mean(kernel_ms))
+    rp, ci, va = M.export()
+    psi, steps = M.rows()
+    flops = setup_flops(rp, steps, p["s"], A.nnz / A.n)
+    fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12  # TFLOP/s: SMs x DFMA/clk x 2 x max clock
+    roof = {"kernel": "afsai_setup_kernel", "bound": "alu", "achieved": flops / (kern_ms * 1e-3) / 1e12,
+            "peak": fp64_peak, "unit": "TFLOP/s", "frac": None, "traffic": None,
+            "kernel_ms": kern_ms, "algorithmic_flops": flops,
+            "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived, not measured)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    M.close()
+
+    mixed = None
+    if not args.no_mixed:
+        for _ in range(2):
+            Mm, sm_, pm_ = one_solve(prm_mixed)
+            Mm.close()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            Mm, sm_, pm_ = one_solve(prm_mixed)
+            Mm.close()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mixed = {"value": e0.elapsed_time(e1) / 1e3 / args.steps, "unit": "s/solve", "iters": pm_["iters"],
+                 "relres_true": pm_["relres_true"], "g_prec": "fp32", "chol_prec": "fp32+fp64 refinement",
+                 "setup_ms": sm_["setup_ms"], "solve_ms": pm_["solve_ms"]}
+
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+        Ah = type(A)(A.n, pin(A.rowptr).numpy(), pin(A.col).numpy(), pin(A.val).numpy())
+        bh = pin(b).numpy()
+        xh = torch.zeros(A.n, dtype=torch.float64).pin_memory().numpy()
+        afsai.afsai_solve_host(Ah, prm, bh, xh, rtol=1e-8, maxit=20000, stream=stream)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            afsai.afsai_solve_host(Ah, prm, bh, xh, rtol=1e-8, maxit=20000, stream=stream)
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - t0) / args.steps
+        e2e = {"value": te, "unit": "s/solve", "h2d_bytes_per_step": int(4 * (A.n + 1) + 12 * A.nnz + 8 * A.n),
+               "d2h_bytes_per_step": int(8 * A.n)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample = cpu_oracle_estimate(A, b, p, int(np.median(iters)))
+        cpu = {"value": v, "unit": "s/solve", "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "s/solve", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
+            "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "kiter": p["kiter"], "s": p["s"],
+                       "eps": p["eps"], "rtol": 1e-8, "l2": "inputs larger than L2 (A is %.0f MB)" % (A.nnz * 12e-6),
+                       "parallelism": f"replicas x{world}"},
+            "setup_ms": float(np.median(setup_ms)), "solve_ms": float(np.median(solve_ms)),
+            "pcg_iters": int(np.median(iters)), "relres_true": pinfo["relres_true"], "nnz_G": sinfo["nnz_G"],
+            "gpu_launches": int(launches), "roofline": roof, "mixed": mixed, "e2e": e2e, "cpu_baseline": cpu,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * afsai.h - C ABI of the GB300 (sm_103a) adaptive FSAI preconditioner and
+ * aFSAI-preconditioned conjugate gradient library (libafsai.so).
+ *
+ * Method: Isotton, Janna, Bernaschi, "A GPU-accelerated Adaptive FSAI
+ * preconditioner for Massively Parallel Simulations" (arXiv 2010.14175),
+ * Section 2 (set-up), Section 3 (kernels: Kaporin gradient, systems gather,
+ * batched Cholesky, miniwarp SpMV) and Section 5.2 (PCG to an 8-order
+ * residual reduction).
+ *
+ * Conventions shared by every entry point:
+ *   - Plain C types only; no exceptions cross the boundary.  Every call
+ *     returns an afsai_status; on failure a thread-local message is available
+ *     from afsai_last_error().
+ *   - "device pointer" = memory of the current CUDA device (cudaMalloc,
+ *     cudaMallocAsync or a framework allocator).  "host pointer" = CPU
+ *     memory (pinned memory makes the host<->device copies faster).
+ *   - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is enqueued on it; calls that must read a result on the host
+ *     (status, counts, iteration numbers) synchronise that stream.
+ *   - The caller owns every buffer it passes.  The library owns what it
+ *     returns through an opaque handle until the matching destroy call.
+ *   - Matrices are CSR with int32 row pointers and column indices, 0-based,
+ *     columns strictly increasing within each row, full symmetric storage
+ *     (both triangles), diagonal present and positive.  The set-up assumes
+ *     A is symmetric positive definite and reads the lower part of row r
+ *     for A[r, j], j <= r, and row r for a_jr by symmetry.
+ */
+#ifndef AFSAI_H
+#define AFSAI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define AFSAI_API __attribute__((visibility("default")))
+#else
+#define AFSAI_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AFSAI_OK = 0,
+    AFSAI_EINVAL = 1,   /* invalid argument or malformed CSR */
+    AFSAI_ENOMEM = 2,   /* device or host allocation failed */
+    AFSAI_ENOTSPD = 3,  /* a non-positive pivot in a row system (A not SPD) */
+    AFSAI_ENOCONV = 4,  /* PCG did not reach rtol within maxit iterations */
+    AFSAI_ECUDA = 5,    /* a CUDA runtime call failed */
+    AFSAI_ETIMEOUT = 6, /* a bounded device-side wait ran out */
+    AFSAI_EAGAIN = 7,   /* result not ready yet (serving) */
+    AFSAI_EBUSY = 8,    /* no free slot or memory (serving admission) */
+    AFSAI_ENOTSUP = 9   /* parameters beyond what this build supports */
+} afsai_status;
+
+/* A sparse matrix in CSR.  rowptr: n+1 entries, col/val: nnz entries.
+ * Whether the pointers are host or device memory is stated per call. */
+typedef struct {
+    int32_t n;
+    int64_t nnz;
+    const int32_t* rowptr;
+    const int32_t* col;
+    const double* val;
+} afsai_csr;
+
+/* Parameters of the adaptive set-up (Section 2, "three user-specified
+ * parameters": k_max, s, epsilon).
+ *   kiter      number of pattern enlargement steps per row (k_max), >= 0;
+ *              a row holds at most 1 + kiter*s entries (<= 128 here).
+ *   s          entries added per step, >= 1.
+ *   eps        tolerance of the Kaporin-number reduction test, >= 0.
+ *   exit_mode  0: stop a row after step k when
+ *                 (psi_{k-1} - psi_k) < eps * psi_{k-1}   (default reading
+ *                 of "relative tolerance on the Kaporin number reduction");
+ *              1: the printed test psi_k / psi_0 <= eps (Eq. "exit_crit").
+ *   g_prec     storage and arithmetic of G and G^T in the application:
+ *              0 fp64, 1 fp32, 2 bf16 (fp32 accumulation for 1 and 2).
+ *   chol_prec  0: FP64 Cholesky of every row system (bit-exact with the
+ *              plain FP64 definition); 1: FP32 Cholesky followed by one
+ *              FP64 iterative-refinement step.  The Kaporin gradient and the
+ *              selection stay FP64 in both. */
+typedef struct {
+    int32_t kiter;
+    int32_t s;
+    double eps;
+    int32_t exit_mode;
+    int32_t g_prec;
+    int32_t chol_prec;
+} afsai_params;
+
+/* Opaque preconditioner: G (lower triangular, CSR, sorted columns), its
+ * explicitly stored transpose G^T, and per-row set-up results, all in
+ * device memory owned by the library. */
+typedef struct afsai_precond afsai_precond;
+
+typedef struct {
+    int32_t n;          /* rows */
+    int64_t nnz_G;      /* entries of G (= entries of G^T) */
+    int32_t max_row;    /* longest row of G */
+    int32_t g_prec;     /* as in afsai_params */
+    int32_t n_retry;    /* rows whose candidate table overflowed shared
+                           memory and were redone with a larger table */
+    double setup_ms;    /* device time of the whole set-up (CUDA events) */
+    double kernel_ms;   /* device time of the fused pattern-search kernel */
+} afsai_info;
+
+typedef struct {
+    int32_t iters;       /* PCG iterations performed */
+    int32_t converged;   /* 1 if ||r_k|| <= rtol ||b|| was reached */
+    double relres_rec;   /* recursive ||r_k|| / ||b|| at exit */
+    double relres_true;  /* ||b - A x|| / ||b|| recomputed at exit */
+    double solve_ms;     /* device time of the solve (CUDA events) */
+} pcg_info;
+
+/* Builds the aFSAI preconditioner of A (Section 2): for every row i, grow
+ * the pattern P_i from {i} by the s candidates j < i of largest Kaporin
+ * gradient |(A g_i)_j| (Eq. "grapsi"), solve A[P_i,P_i] g_i = e_m by
+ * Cholesky (Eq. "DensSys"), stop after kiter steps or on the exit test
+ * (Eq. "exit_crit"), and scale G[i,P_i] = g_i / sqrt(g_i,m) so that
+ * diag(G A G^T) = I (Eq. "diagScal").  Then builds G^T.
+ *   A       device pointers; must stay valid during the call only.
+ *   params  host pointer.
+ *   out     receives a new handle (free with afsai_destroy).
+ * Synchronises `stream`.  Errors: EINVAL (bad parameters or CSR: n <= 0,
+ * rowptr not monotone or rowptr[0] != 0 or rowptr[n] != nnz, a column out
+ * of range or not strictly increasing, a missing or non-positive diagonal),
+ * ENOTSUP (1 + kiter*s > 128), ENOTSPD (a non-positive pivot; the handle is
+ * not created), ENOMEM, ECUDA. */
+AFSAI_API afsai_status afsai_setup(const afsai_csr* A, const afsai_params* params, void* stream, afsai_precond** out);
+
+/* z = G^T (G r), the preconditioner application M^{-1} r (Eq. "prec"), as
+ * two CSR SpMVs (G, then the stored G^T; Section 3 "miniwarp" SpMV).
+ * r, z: device vectors of n doubles (must not overlap).  Asynchronous. */
+AFSAI_API afsai_status afsai_apply(const afsai_precond* M, const double* r, double* z, void* stream);
+
+/* y = A x (CSR SpMV, FP64).  A, x, y device pointers.  Asynchronous. */
+AFSAI_API afsai_status afsai_spmv(const afsai_csr* A, const double* x, double* y, void* stream);
+
+/* Preconditioned conjugate gradients for A x = b with M^{-1} = G^T G
+ * (M = NULL gives unpreconditioned CG).  x (device, n doubles) is the
+ * initial guess on entry and the solution on exit; b device.  Stops when
+ * the recursive residual satisfies ||r_k||_2 <= rtol ||b||_2 (Section 5.2:
+ * 8 orders of reduction for rtol = 1e-8) or after maxit iterations.  The
+ * iteration runs on the device (CUDA graphs); the host only polls a flag.
+ * Synchronises `stream`.  info (host, may be NULL) receives the outcome.
+ * Returns OK, ENOCONV (maxit reached), EINVAL, ENOMEM, ECUDA. */
+AFSAI_API afsai_status pcg_solve(const afsai_csr* A, const afsai_precond* M, const double* b, double* x, double rtol,
+                       int32_t maxit, void* stream, pcg_info* info);
+
+/* End-to-end solve from HOST buffers: copies A and b to the device, builds
+ * the preconditioner, runs PCG from x = 0 and copies x back (x_host: n
+ * doubles).  Device memory is allocated and freed inside the call.
+ * setup_info and info may be NULL.  Synchronises `stream`. */
+AFSAI_API afsai_status afsai_solve_host(const afsai_csr* A_host, const afsai_params* params, const double* b_host,
+                              double* x_host, double rtol, int32_t maxit, void* stream, afsai_info* setup_info,
+                              pcg_info* info);
+
+/* Sizes and timings of a preconditioner (host struct). */
+AFSAI_API afsai_status afsai_get_info(const afsai_precond* M, afsai_info* info);
+
+/* Copies G or G^T to HOST buffers: rowptr n+1, col nnz_G, val nnz_G
+ * (converted to double whatever g_prec is).  Any pointer may be NULL to
+ * skip it.  Synchronous. */
+AFSAI_API afsai_status afsai_export_G(const afsai_precond* M, int32_t* rowptr, int32_t* col, double* val);
+AFSAI_API afsai_status afsai_export_Gt(const afsai_precond* M, int32_t* rowptr, int32_t* col, double* val);
+
+/* Copies per-row set-up results to HOST buffers of n entries: psi (final
+ * Kaporin row measure psi_i = 1 / g_i,m, Eq. "kap_min") and the number of
+ * enlargement steps performed.  Either pointer may be NULL. */
+AFSAI_API afsai_status afsai_export_rows(const afsai_precond* M, double* psi, int32_t* steps);
+
+AFSAI_API void afsai_destroy(afsai_precond* M);
+
+/* Message of the last failure on the calling thread ("" if none). */
+AFSAI_API const char* afsai_last_error(void);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (kernels inside CUDA graph launches included). */
+AFSAI_API int64_t afsai_kernel_launches(void);
+
+/* Library version string. */
+AFSAI_API const char* afsai_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AFSAI_H */

@@ -1,0 +1,254 @@
+"""Python binding of libafsai.so: argument marshalling only.
+
+Every step of the set-up, the preconditioner application and PCG runs in
+the CUDA library (``csrc/``) behind the C ABI declared in
+``include/afsai.h``.  PyTorch is used for device memory and streams:
+tensors are passed by ``data_ptr()`` and the current stream by handle.
+There is no CPU fallback: if the library is missing or no GPU is present,
+the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+STATUS = {
+    0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOTSPD", 4: "ENOCONV", 5: "ECUDA", 6: "ETIMEOUT", 7: "EAGAIN",
+    8: "EBUSY", 9: "ENOTSUP",
+}
+OK, EINVAL, ENOMEM, ENOTSPD, ENOCONV, ECUDA, ETIMEOUT, EAGAIN, EBUSY, ENOTSUP = range(10)
+
+# names exported by include/afsai.h (checked by the ABI test)
+EXPORTS = (
+    "afsai_setup", "afsai_apply", "afsai_spmv", "pcg_solve", "afsai_solve_host", "afsai_get_info",
+    "afsai_export_G", "afsai_export_Gt", "afsai_export_rows", "afsai_destroy", "afsai_last_error", "afsai_version",
+    "afsai_kernel_launches",
+)
+
+
+class AfsaiError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("kiter", ctypes.c_int32), ("s", ctypes.c_int32), ("eps", ctypes.c_double),
+                ("exit_mode", ctypes.c_int32), ("g_prec", ctypes.c_int32), ("chol_prec", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz_G", ctypes.c_int64), ("max_row", ctypes.c_int32),
+                ("g_prec", ctypes.c_int32), ("n_retry", ctypes.c_int32), ("setup_ms", ctypes.c_double),
+                ("kernel_ms", ctypes.c_double)]
+
+
+class PcgInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("converged", ctypes.c_int32), ("relres_rec", ctypes.c_double),
+                ("relres_true", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+
+
+def _as_dict(s):
+    return {k: getattr(s, k) for k, _ in s._fields_}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libafsai.so (building it first if needed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libafsai.so not built ({path}); run paper_2010_14175_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        st = ctypes.c_int
+        lib.afsai_setup.argtypes = [ctypes.POINTER(Csr), ctypes.POINTER(Params), P, ctypes.POINTER(P)]
+        lib.afsai_setup.restype = st
+        lib.afsai_apply.argtypes = [P, P, P, P]
+        lib.afsai_apply.restype = st
+        lib.afsai_spmv.argtypes = [ctypes.POINTER(Csr), P, P, P]
+        lib.afsai_spmv.restype = st
+        lib.pcg_solve.argtypes = [ctypes.POINTER(Csr), P, P, P, ctypes.c_double, ctypes.c_int32, P,
+                                  ctypes.POINTER(PcgInfo)]
+        lib.pcg_solve.restype = st
+        lib.afsai_solve_host.argtypes = [ctypes.POINTER(Csr), ctypes.POINTER(Params), P, P, ctypes.c_double,
+                                         ctypes.c_int32, P, ctypes.POINTER(Info), ctypes.POINTER(PcgInfo)]
+        lib.afsai_solve_host.restype = st
+        lib.afsai_get_info.argtypes = [P, ctypes.POINTER(Info)]
+        lib.afsai_get_info.restype = st
+        for fn in (lib.afsai_export_G, lib.afsai_export_Gt):
+            fn.argtypes = [P, P, P, P]
+            fn.restype = st
+        lib.afsai_export_rows.argtypes = [P, P, P]
+        lib.afsai_export_rows.restype = st
+        lib.afsai_destroy.argtypes = [P]
+        lib.afsai_destroy.restype = None
+        lib.afsai_last_error.argtypes = []
+        lib.afsai_last_error.restype = ctypes.c_char_p
+        lib.afsai_version.argtypes = []
+        lib.afsai_version.restype = ctypes.c_char_p
+        lib.afsai_kernel_launches.argtypes = []
+        lib.afsai_kernel_launches.restype = ctypes.c_int64
+        _lib = lib
+        return lib
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().afsai_kernel_launches())
+
+
+def _check(status):
+    if status != OK:
+        raise AfsaiError(status, load().afsai_last_error().decode())
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class DeviceCSR:
+    """A CSR matrix in device memory (torch tensors int32/int32/float64)."""
+
+    def __init__(self, n, rowptr, col, val):
+        self.n = int(n)
+        self.rowptr, self.col, self.val = rowptr, col, val
+        self.nnz = int(col.numel())
+
+    @classmethod
+    def from_host(cls, A, device="cuda"):
+        import torch
+
+        return cls(A.n, torch.from_numpy(np.ascontiguousarray(A.rowptr, dtype=np.int32)).to(device),
+                   torch.from_numpy(np.ascontiguousarray(A.col, dtype=np.int32)).to(device),
+                   torch.from_numpy(np.ascontiguousarray(A.val, dtype=np.float64)).to(device))
+
+    def c(self) -> Csr:
+        return Csr(self.n, self.nnz, self.rowptr.data_ptr(), self.col.data_ptr(), self.val.data_ptr())
+
+
+def params(kiter, s, eps, exit_mode=0, g_prec=0, chol_prec=0) -> Params:
+    return Params(int(kiter), int(s), float(eps), int(exit_mode), int(g_prec), int(chol_prec))
+
+
+class Precond:
+    """Owns an afsai_precond* (G, G^T, per-row results in device memory)."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = Info()
+        _check(load().afsai_get_info(self._h, ctypes.byref(inf)))
+        return _as_dict(inf)
+
+    def export(self, transpose=False):
+        """(rowptr, col, val) of G (or G^T) as numpy arrays (val as float64)."""
+        inf = self.info()
+        n, nnz = inf["n"], inf["nnz_G"]
+        rp = np.zeros(n + 1, dtype=np.int32)
+        ci = np.zeros(max(nnz, 1), dtype=np.int32)
+        va = np.zeros(max(nnz, 1), dtype=np.float64)
+        fn = load().afsai_export_Gt if transpose else load().afsai_export_G
+        _check(fn(self._h, rp.ctypes.data_as(ctypes.c_void_p), ci.ctypes.data_as(ctypes.c_void_p),
+                  va.ctypes.data_as(ctypes.c_void_p)))
+        return rp, ci[:nnz], va[:nnz]
+
+    def rows(self):
+        """(psi, steps) per row as numpy arrays."""
+        n = self.info()["n"]
+        psi = np.zeros(n, dtype=np.float64)
+        steps = np.zeros(n, dtype=np.int32)
+        _check(load().afsai_export_rows(self._h, psi.ctypes.data_as(ctypes.c_void_p),
+                                        steps.ctypes.data_as(ctypes.c_void_p)))
+        return psi, steps
+
+    def close(self):
+        if self._h:
+            load().afsai_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def afsai_setup(A: DeviceCSR, prm: Params, stream=None) -> Precond:
+    lib = load()
+    h = ctypes.c_void_p()
+    csr = A.c()
+    _check(lib.afsai_setup(ctypes.byref(csr), ctypes.byref(prm), _stream(stream), ctypes.byref(h)))
+    return Precond(h)
+
+
+def afsai_apply(M: Precond, r, z, stream=None):
+    _check(load().afsai_apply(M.handle, _ptr(r), _ptr(z), _stream(stream)))
+
+
+def afsai_spmv(A: DeviceCSR, x, y, stream=None):
+    csr = A.c()
+    _check(load().afsai_spmv(ctypes.byref(csr), _ptr(x), _ptr(y), _stream(stream)))
+
+
+def pcg_solve(A: DeviceCSR, M, b, x, rtol=1e-8, maxit=10000, stream=None, raise_on_noconv=True) -> dict:
+    inf = PcgInfo()
+    csr = A.c()
+    st = load().pcg_solve(ctypes.byref(csr), M.handle if M is not None else None, _ptr(b), _ptr(x), float(rtol),
+                          int(maxit), _stream(stream), ctypes.byref(inf))
+    if st != OK and not (st == ENOCONV and not raise_on_noconv):
+        _check(st)
+    out = _as_dict(inf)
+    out["status"] = st
+    return out
+
+
+def afsai_solve_host(A, prm: Params, b: np.ndarray, x: np.ndarray, rtol=1e-8, maxit=10000, stream=None):
+    """End-to-end solve from host arrays (A: object with n, rowptr, col, val
+    numpy arrays; b, x: float64 numpy arrays, x receives the solution)."""
+    rp = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(A.col, dtype=np.int32)
+    va = np.ascontiguousarray(A.val, dtype=np.float64)
+    assert b.dtype == np.float64 and x.dtype == np.float64 and b.flags.c_contiguous and x.flags.c_contiguous
+    csr = Csr(A.n, int(ci.size), rp.ctypes.data, ci.ctypes.data, va.ctypes.data)
+    sinf, pinf = Info(), PcgInfo()
+    st = load().afsai_solve_host(ctypes.byref(csr), ctypes.byref(prm), b.ctypes.data_as(ctypes.c_void_p),
+                                 x.ctypes.data_as(ctypes.c_void_p), float(rtol), int(maxit), _stream(stream),
+                                 ctypes.byref(sinf), ctypes.byref(pinf))
+    if st not in (OK, ENOCONV):
+        _check(st)
+    return _as_dict(sinf), _as_dict(pinf)

@@ -1,0 +1,144 @@
+// Internal declarations shared by the translation units of libafsai.so.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "afsai.h"
+
+namespace afsai {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+afsai_status fail(afsai_status st, const std::string& msg);
+
+#define AFSAI_CUDA_TRY(expr)                                                                   \
+    do {                                                                                       \
+        cudaError_t e_ = (expr);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            return ::afsai::fail(e_ == cudaErrorMemoryAllocation ? AFSAI_ENOMEM : AFSAI_ECUDA, \
+                                 std::string(#expr) + ": " + cudaGetErrorString(e_));          \
+        }                                                                                      \
+    } while (0)
+
+#define AFSAI_TRY(expr)                         \
+    do {                                        \
+        afsai_status s_ = (expr);               \
+        if (s_ != AFSAI_OK) return s_;          \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// device buffers (stream-ordered allocation)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    cudaStream_t st = nullptr;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    afsai_status alloc(size_t count, cudaStream_t s) {
+        release();
+        st = s;
+        n = count;
+        if (count == 0) return AFSAI_OK;
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&p), count * sizeof(T), s);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            n = 0;
+            return fail(AFSAI_ENOMEM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+        }
+        return AFSAI_OK;
+    }
+    void release() {
+        if (p) cudaFreeAsync(p, st);
+        p = nullptr;
+        n = 0;
+    }
+    T* detach() {
+        T* q = p;
+        p = nullptr;
+        n = 0;
+        return q;
+    }
+};
+
+// G / G^T storage: values in one of three types.
+enum ValType : int32_t { VAL_F64 = 0, VAL_F32 = 1, VAL_BF16 = 2 };
+
+inline size_t val_bytes(int32_t vt) { return vt == VAL_F64 ? 8 : (vt == VAL_F32 ? 4 : 2); }
+
+struct CsrDev {
+    int32_t n = 0;
+    int64_t nnz = 0;
+    int32_t* rowptr = nullptr;
+    int32_t* col = nullptr;
+    void* val = nullptr;  // double / float / __nv_bfloat16 by vtype
+    int32_t vtype = VAL_F64;
+    int32_t max_row = 0;
+};
+
+}  // namespace afsai
+
+struct afsai_precond {
+    afsai::CsrDev G;
+    afsai::CsrDev Gt;
+    double* psi = nullptr;     // n
+    int32_t* steps = nullptr;  // n
+    afsai_params params{};
+    afsai_info info{};
+    int device = 0;
+};
+
+namespace afsai {
+
+// ---------------------------------------------------------------------------
+// entry points of the translation units
+// ---------------------------------------------------------------------------
+
+// Validates a device CSR (see afsai.h); synchronises the stream.
+afsai_status validate_csr(const afsai_csr* A, cudaStream_t st, int32_t* max_row_nnz);
+
+// Set-up (setup.cu).  Fills M->G, M->Gt, M->psi, M->steps.
+afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_row_nnz, cudaStream_t st,
+                        afsai_precond* M);
+
+// Sparse building blocks (sparse.cu).
+afsai_status exclusive_scan_i32(const int32_t* in, int32_t* out, int32_t n, cudaStream_t st, int64_t* total_host);
+afsai_status build_transpose(const CsrDev& G, CsrDev* Gt, cudaStream_t st);
+afsai_status spmv_csr(const CsrDev& A, const double* x, double* y, cudaStream_t st);
+afsai_status apply_precond(const afsai_precond* M, const double* r, double* t, double* z, cudaStream_t st);
+void free_csr(CsrDev* A, cudaStream_t st);
+
+// PCG (pcg.cu).
+afsai_status pcg_impl(const afsai_csr* A, const afsai_precond* M, const double* b, double* x, double rtol,
+                      int32_t maxit, cudaStream_t st, pcg_info* info);
+
+inline CsrDev view_of(const afsai_csr* A) {
+    CsrDev v;
+    v.n = A->n;
+    v.nnz = A->nnz;
+    v.rowptr = const_cast<int32_t*>(A->rowptr);
+    v.col = const_cast<int32_t*>(A->col);
+    v.val = const_cast<double*>(A->val);
+    v.vtype = VAL_F64;
+    return v;
+}
+
+inline int ceil_div(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) / b); }
+
+int num_sms();
+
+// Kernel launch accounting (reported by afsai_kernel_launches()).
+void count_launches(int64_t k);
+int64_t launches_so_far();
+void set_launches(int64_t v);
+
+}  // namespace afsai

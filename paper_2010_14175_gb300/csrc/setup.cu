@@ -1,0 +1,675 @@
+// aFSAI set-up on the GPU (Section 2 of the paper; kernels of Section 3).
+//
+// One warp owns one row i for the whole adaptive iteration, so the three
+// kernels the paper launches per step (Kaporin gradient + selection,
+// systems gather, batched Cholesky) and the exit test run fused in one
+// launch with no intermediate global state:
+//
+//   init      P = {i}, g = 1/a_ii, psi_0 = a_ii              (G_0 = I)
+//   step k    gradient  (A g)_j over j < i, accumulated in a per-warp hash
+//                       table in shared memory: rows r in P in ascending
+//                       order, each row's entries spread over the lanes
+//                       (distinct columns per row, so no two lanes touch one
+//                       slot in the same pass), acc = fma(a_rj, g_r, acc)
+//                                                        (Eq. "grapsi")
+//             select    s times a warp-shuffle arg-max of |acc| (ties to the
+//                       smaller column) over the slots not in P
+//             merge     sorted insertion into P (i stays last)
+//             gather    A[P,P] lower triangle, packed, in shared memory
+//                       (aliases the hash table, which is dead by then)
+//             Cholesky  right-looking; the trailing update of each column is
+//                       spread over all lanes as (r, q) pairs so FP64 warp
+//                       instructions stay full           (Eq. "DensSys")
+//             solve     L z = e_m, L^T g = z column by column
+//             exit      psi = 1/g_m; relative-decrease or literal test
+//                                                        (Eq. "exit_crit")
+//   finish    G[i,P] = g / sqrt(g_m)                     (Eq. "diagScal")
+//
+// Every floating-point operation mirrors the plain FP64 definition of the
+// method one for one (explicit fma, IEEE division and square root, fixed
+// order per element), so the FP64 set-up is bit-identical to it: same
+// patterns, same values.  The TU is compiled with --fmad=false so that no
+// multiply-add is contracted behind the code's back.
+//
+// With chol_prec = 1 the dense solve runs in FP32 (factorisation and both
+// triangular solves) followed by one FP64 refinement step
+//   res = e_m - A[P,P] g (FP64),  L L^T d = res (FP32),  g += d (FP64),
+// while the gradient and the selection stay FP64.
+//
+// Rows whose candidate set overflows the shared-memory table are listed and
+// redone by a second launch that keeps the table in global memory.
+#include <algorithm>
+#include <climits>
+#include <string>
+
+#include "afsai_internal.cuh"
+
+namespace afsai {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int32_t kRowOk = 0;
+constexpr int32_t kRowNotSpd = 3;
+constexpr int32_t kRowOverflow = 10;
+constexpr int kSetupThreads = 256;
+
+struct SetupArgs {
+    int32_t n;
+    const int32_t* __restrict__ rowptr;
+    const int32_t* __restrict__ col;
+    const double* __restrict__ val;
+    int32_t kiter;
+    int32_t s;
+    int32_t exit_mode;
+    double eps;
+    int64_t mcap;  // row stride of the per-row outputs
+    int32_t* __restrict__ out_len;
+    int32_t* __restrict__ out_col;
+    double* __restrict__ out_val;
+    double* __restrict__ psi;
+    int32_t* __restrict__ steps;
+    int32_t* __restrict__ status;
+    const int32_t* __restrict__ rows;  // optional row list (retry pass)
+    int32_t nrows;
+    int32_t* __restrict__ retry_rows;
+    int32_t* __restrict__ counters;  // [0] retry count, [1] not-SPD count
+    int32_t* __restrict__ gkey;      // global table (retry pass)
+    double* __restrict__ gval;
+    int32_t ght_log2;
+};
+
+template <int MCAP, int HT>
+struct WarpWs {
+    double g[MCAP];
+    int32_t P[MCAP];
+    int32_t newj[MCAP];
+    int32_t nkeys;  // keys in the candidate table this step
+    int32_t pad_;
+    union {
+        struct {
+            double val[HT];
+            int32_t key[HT];
+        } h;
+        struct {
+            double M[MCAP * (MCAP + 1) / 2];   // FP64 gather / factor
+            float Mf[MCAP * (MCAP + 1) / 2];   // FP32 factor (chol_prec = 1)
+        } d;
+    } u;
+};
+
+__device__ __forceinline__ int tri(int r) { return (r * (r + 1)) >> 1; }
+
+__device__ __forceinline__ int find_sorted(const int32_t* P, int m, int32_t c) {
+    int lo = 0, hi = m - 1;
+    while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        const int32_t v = P[mid];
+        if (v == c) return mid;
+        if (v < c)
+            lo = mid + 1;
+        else
+            hi = mid - 1;
+    }
+    return -1;
+}
+
+// Fibonacci hashing of a column index into 2^log2 slots.
+__device__ __forceinline__ uint32_t slot_of(int32_t j, int log2) {
+    return (static_cast<uint32_t>(j) * 0x9E3779B1u) >> (32 - log2);
+}
+
+// Inserts j (or finds it) and returns its slot; -1 if the table is full.
+// `full` is set once the table holds more than 7/8 of its slots, which
+// sends the row to the retry pass with a larger table (bounded probing).
+__device__ __forceinline__ int table_insert(int32_t* key, int log2, int32_t j, int32_t* nkeys, bool& full) {
+    const uint32_t mask = (1u << log2) - 1u;
+    uint32_t h = slot_of(j, log2);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const int32_t cur = atomicCAS(&key[h], -1, j);
+        if (cur == -1) {
+            if (atomicAdd(nkeys, 1) >= static_cast<int32_t>((mask + 1) - ((mask + 1) >> 3))) full = true;
+            return static_cast<int>(h);
+        }
+        if (cur == j) return static_cast<int>(h);
+        h = (h + 1) & mask;
+    }
+    full = true;
+    return -1;
+}
+
+__device__ __forceinline__ int table_find(const int32_t* key, int log2, int32_t j) {
+    const uint32_t mask = (1u << log2) - 1u;
+    uint32_t h = slot_of(j, log2);
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
+        const int32_t cur = key[h];
+        if (cur == j) return static_cast<int>(h);
+        if (cur == -1) return -1;
+        h = (h + 1) & mask;
+    }
+    return -1;
+}
+
+// (col, (row-)index) pair of the lower triangle trailing block: linear
+// index idx -> (rr, qq) with qq <= rr, idx = rr(rr+1)/2 + qq.
+__device__ __forceinline__ void tri_unrank(int idx, int& rr, int& qq) {
+    int r = static_cast<int>((sqrtf(8.0f * static_cast<float>(idx) + 1.0f) - 1.0f) * 0.5f);
+    if (tri(r + 1) <= idx) ++r;
+    if (tri(r) > idx) --r;
+    rr = r;
+    qq = idx - tri(r);
+}
+
+// Right-looking Cholesky of the packed lower triangle M (m x m) in place.
+// Returns false (warp-uniform) on a non-positive pivot.
+template <typename T>
+__device__ bool warp_cholesky(T* M, int m, int lane) {
+    for (int c = 0; c < m; ++c) {
+        const T piv = M[tri(c) + c];
+        if (!(piv > T(0))) return false;
+        const T d = sqrt(piv);
+        for (int r = c + 1 + lane; r < m; r += 32) M[tri(r) + c] = M[tri(r) + c] / d;
+        __syncwarp();
+        if (lane == 0) M[tri(c) + c] = d;
+        const int w = m - c - 1;
+        const int T_ = (w * (w + 1)) >> 1;
+        for (int idx = lane; idx < T_; idx += 32) {
+            int rr, qq;
+            tri_unrank(idx, rr, qq);
+            const int r = c + 1 + rr, q = c + 1 + qq;
+            M[tri(r) + q] = fma(-M[tri(r) + c], M[tri(q) + c], M[tri(r) + q]);
+        }
+        __syncwarp();
+    }
+    return true;
+}
+
+// Solves L L^T x = rhs in place in x (x holds rhs on entry), column
+// oriented as in the plain definition: forward L z = rhs, back L^T x = z.
+// When `em` is true the right-hand side is e_m and the forward solve
+// reduces to z = e_m / L_mm.
+template <typename T>
+__device__ void warp_llt_solve(const T* L, T* x, int m, bool em, int lane) {
+    if (em) {
+        for (int t = lane; t < m; t += 32) x[t] = T(0);
+        __syncwarp();
+        if (lane == 0) x[m - 1] = T(1) / L[tri(m - 1) + m - 1];
+        __syncwarp();
+    } else {
+        for (int c = 0; c < m; ++c) {
+            const T zc = x[c] / L[tri(c) + c];
+            __syncwarp();
+            if (lane == 0) x[c] = zc;
+            for (int r = c + 1 + lane; r < m; r += 32) x[r] = fma(-L[tri(r) + c], zc, x[r]);
+            __syncwarp();
+        }
+    }
+    for (int c = m - 1; c >= 0; --c) {
+        const T gc = x[c] / L[tri(c) + c];
+        __syncwarp();
+        if (lane == 0) x[c] = gc;
+        for (int r = lane; r < c; r += 32) x[r] = fma(-L[tri(c) + r], gc, x[r]);
+        __syncwarp();
+    }
+}
+
+template <int MCAP, int HT, bool CHOL32>
+__device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, int32_t* key, double* hv,
+                          int log2, int lane) {
+    const int ht = 1 << log2;
+    // a_ii (validated present and positive)
+    double aii = 0.0;
+    bool found = false;
+    {
+        const int32_t e0 = a.rowptr[i], e1 = a.rowptr[i + 1];
+        for (int32_t e = e0 + lane; e < e1; e += 32)
+            if (a.col[e] == i) {
+                aii = a.val[e];
+                found = true;
+            }
+        const unsigned bal = __ballot_sync(kFull, found);
+        aii = __shfl_sync(kFull, aii, bal ? (__ffs(bal) - 1) : 0);
+        if (!bal) aii = 0.0;
+    }
+    if (lane == 0) {
+        w.P[0] = i;
+        w.g[0] = 1.0 / aii;
+    }
+    __syncwarp();
+    int m = 1;
+    const double psi0 = aii;
+    double psi_prev = psi0;
+    int steps = 0;
+    int32_t status = (aii > 0.0) ? kRowOk : kRowNotSpd;
+
+    for (int k = 1; k <= a.kiter && status == kRowOk; ++k) {
+        // ---- Kaporin gradient over j < i (Eq. "grapsi") ----
+        for (int t = lane; t < ht; t += 32) {
+            key[t] = -1;
+            hv[t] = 0.0;
+        }
+        if (lane == 0) w.nkeys = 0;
+        __syncwarp();
+        bool ovf = false;
+        for (int t = 0; t < m; ++t) {
+            const int32_t r = w.P[t];
+            const double gr = w.g[t];
+            const int32_t e0 = a.rowptr[r], e1 = a.rowptr[r + 1];
+            for (int32_t e = e0 + lane; e < e1; e += 32) {
+                const int32_t j = __ldg(&a.col[e]);
+                if (j < i) {
+                    const int slot = table_insert(key, log2, j, &w.nkeys, ovf);
+                    if (slot >= 0) hv[slot] = fma(__ldg(&a.val[e]), gr, hv[slot]);
+                }
+            }
+            __syncwarp();
+        }
+        if (__any_sync(kFull, ovf)) {
+            status = kRowOverflow;
+            break;
+        }
+        // members of P are not eligible: zero their accumulated gradient
+        for (int t = lane; t < m - 1; t += 32) {
+            const int slot = table_find(key, log2, w.P[t]);
+            if (slot >= 0) hv[slot] = 0.0;
+        }
+        __syncwarp();
+        // ---- select the s largest |gradient| (ties: smaller column) ----
+        int npick = 0;
+        for (int u = 0; u < a.s; ++u) {
+            unsigned long long best = 0ull;
+            int32_t bestj = INT_MAX;
+            int bslot = -1;
+            for (int t = lane; t < ht; t += 32) {
+                const int32_t j = key[t];
+                if (j < 0) continue;
+                const unsigned long long ab =
+                    static_cast<unsigned long long>(__double_as_longlong(hv[t])) & 0x7fffffffffffffffull;
+                if (ab == 0ull || ab > 0x7ff0000000000000ull) continue;  // zero or NaN
+                if (ab > best || (ab == best && j < bestj)) {
+                    best = ab;
+                    bestj = j;
+                    bslot = t;
+                }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const unsigned long long ob = __shfl_xor_sync(kFull, best, off);
+                const int32_t oj = __shfl_xor_sync(kFull, bestj, off);
+                const int os = __shfl_xor_sync(kFull, bslot, off);
+                if (ob > best || (ob == best && oj < bestj)) {
+                    best = ob;
+                    bestj = oj;
+                    bslot = os;
+                }
+            }
+            if (best == 0ull) break;
+            if (lane == 0) {
+                hv[bslot] = 0.0;
+                w.newj[npick] = bestj;
+            }
+            ++npick;
+            __syncwarp();
+        }
+        if (npick == 0) break;
+        // ---- merge into the sorted pattern ----
+        if (lane == 0) {
+            for (int u = 0; u < npick; ++u) {
+                const int32_t j = w.newj[u];
+                int pos = m + u;
+                while (pos > 0 && w.P[pos - 1] > j) {
+                    w.P[pos] = w.P[pos - 1];
+                    --pos;
+                }
+                w.P[pos] = j;
+            }
+        }
+        m += npick;
+        ++steps;
+        __syncwarp();
+
+        // ---- systems gather: packed lower triangle of A[P,P] ----
+        double* M = w.u.d.M;
+        const int nt = tri(m);
+        for (int t = lane; t < nt; t += 32) M[t] = 0.0;
+        __syncwarp();
+        for (int a_ = 0; a_ < m; ++a_) {
+            const int32_t r = w.P[a_];
+            const int32_t e0 = a.rowptr[r], e1 = a.rowptr[r + 1];
+            for (int32_t e = e0 + lane; e < e1; e += 32) {
+                const int32_t c = __ldg(&a.col[e]);
+                if (c <= r) {
+                    const int b = find_sorted(w.P, a_ + 1, c);
+                    if (b >= 0) M[tri(a_) + b] = __ldg(&a.val[e]);
+                }
+            }
+        }
+        __syncwarp();
+
+        // ---- dense solve A[P,P] g = e_m ----
+        if (!CHOL32) {
+            if (!warp_cholesky<double>(M, m, lane)) {
+                status = kRowNotSpd;
+                break;
+            }
+            warp_llt_solve<double>(M, w.g, m, true, lane);
+        } else {
+            // FP32 factor in its own packed buffer; the FP64 gather is kept
+            // for the refinement residual.
+            float* Lf = w.u.d.Mf;
+            for (int t = lane; t < nt; t += 32) Lf[t] = static_cast<float>(M[t]);
+            __syncwarp();
+            if (!warp_cholesky<float>(Lf, m, lane)) {
+                status = kRowNotSpd;
+                break;
+            }
+            float* xf = reinterpret_cast<float*>(w.newj);  // m floats of scratch
+            warp_llt_solve<float>(Lf, xf, m, true, lane);
+            for (int t = lane; t < m; t += 32) w.g[t] = static_cast<double>(xf[t]);
+            __syncwarp();
+            // one FP64 refinement step: res = e_m - A[P,P] g (symmetric, lower stored)
+            for (int r = lane; r < m; r += 32) {
+                double acc = (r == m - 1) ? 1.0 : 0.0;
+                for (int q = 0; q < m; ++q) {
+                    const double arq = (q <= r) ? M[tri(r) + q] : M[tri(q) + r];
+                    acc = fma(-arq, w.g[q], acc);
+                }
+                xf[r] = static_cast<float>(acc);
+            }
+            __syncwarp();
+            warp_llt_solve<float>(Lf, xf, m, false, lane);
+            for (int t = lane; t < m; t += 32) w.g[t] = w.g[t] + static_cast<double>(xf[t]);
+            __syncwarp();
+        }
+        const double psi = 1.0 / w.g[m - 1];
+        const bool stop = (a.exit_mode == 0) ? ((psi_prev - psi) < a.eps * psi_prev) : ((psi / psi0) <= a.eps);
+        psi_prev = psi;
+        if (stop) break;
+    }
+
+    if (status == kRowOk) {
+        const double sq = sqrt(w.g[m - 1]);
+        const int64_t o = static_cast<int64_t>(i) * a.mcap;
+        for (int t = lane; t < m; t += 32) {
+            a.out_col[o + t] = w.P[t];
+            a.out_val[o + t] = w.g[t] / sq;
+        }
+        if (lane == 0) {
+            a.out_len[i] = m;
+            a.psi[i] = psi_prev;
+            a.steps[i] = steps;
+            a.status[i] = kRowOk;
+        }
+    } else if (lane == 0) {
+        a.out_len[i] = 0;
+        a.status[i] = status;
+        if (status == kRowOverflow) {
+            const int32_t slot = atomicAdd(&a.counters[0], 1);
+            a.retry_rows[slot] = i;
+        } else {
+            atomicAdd(&a.counters[1], 1);
+        }
+    }
+    __syncwarp();
+}
+
+template <int MCAP, int HT, bool GTABLE, bool CHOL32>
+__global__ void __launch_bounds__(kSetupThreads) afsai_setup_kernel(SetupArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using WS = WarpWs<MCAP, HT>;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    WS& w = reinterpret_cast<WS*>(smem_raw)[warp];
+    const int64_t gwarp = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + warp;
+    const int64_t nwarps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    int32_t* key;
+    double* hv;
+    int log2;
+    if (GTABLE) {
+        key = a.gkey + (gwarp << a.ght_log2);
+        hv = a.gval + (gwarp << a.ght_log2);
+        log2 = a.ght_log2;
+    } else {
+        key = w.u.h.key;
+        hv = w.u.h.val;
+        log2 = __ffs(HT) - 1;
+    }
+    const int64_t nrows = a.rows ? a.nrows : a.n;
+    for (int64_t t = gwarp; t < nrows; t += nwarps) {
+        const int32_t i = a.rows ? a.rows[t] : static_cast<int32_t>(t);
+        afsai_row<MCAP, HT, CHOL32>(a, i, w, key, hv, log2, lane);
+    }
+}
+
+// Shared memory per warp: the union must also hold the FP64 triangle plus
+// an FP32 copy of it for the FP32 factorisation.
+template <int MCAP, int HT>
+constexpr size_t ws_bytes() {
+    return sizeof(WarpWs<MCAP, HT>);
+}
+
+template <int MCAP, int HT, bool GTABLE, bool CHOL32>
+afsai_status launch_setup(const SetupArgs& a, int64_t nrows, int64_t max_warps, cudaStream_t st) {
+    auto kern = afsai_setup_kernel<MCAP, HT, GTABLE, CHOL32>;
+    // as many warps per block as fit in ~200 KB of shared memory (max 8)
+    const size_t per_warp = ws_bytes<MCAP, HT>();
+    const int warps_per_block = static_cast<int>(std::max<size_t>(1, std::min<size_t>(8, (200u * 1024u) / per_warp)));
+    const int threads = warps_per_block * 32;
+    const size_t smem = per_warp * warps_per_block;
+    AFSAI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    int per_sm = 0;
+    AFSAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+    if (per_sm < 1) return fail(AFSAI_ENOTSUP, "set-up workspace does not fit in shared memory");
+    int64_t blocks = static_cast<int64_t>(per_sm) * num_sms();
+    const int64_t need = (nrows + warps_per_block - 1) / warps_per_block;
+    if (blocks > need) blocks = need;
+    if (blocks * warps_per_block > max_warps) blocks = max_warps / warps_per_block;  // global table capacity
+    if (blocks < 1) blocks = 1;
+    kern<<<static_cast<unsigned>(blocks), threads, smem, st>>>(a);
+    AFSAI_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return AFSAI_OK;
+}
+
+template <int MCAP, int HT>
+afsai_status dispatch_chol(const SetupArgs& a, int64_t nrows, int64_t max_warps, bool gtable, bool chol32,
+                          cudaStream_t st) {
+    if (gtable)
+        return chol32 ? launch_setup<MCAP, HT, true, true>(a, nrows, max_warps, st)
+                      : launch_setup<MCAP, HT, true, false>(a, nrows, max_warps, st);
+    return chol32 ? launch_setup<MCAP, HT, false, true>(a, nrows, max_warps, st)
+                  : launch_setup<MCAP, HT, false, false>(a, nrows, max_warps, st);
+}
+
+afsai_status dispatch(int mcap_t, int ht, const SetupArgs& a, int64_t nrows, int64_t max_warps, bool gtable,
+                      bool chol32, cudaStream_t st) {
+    switch (mcap_t) {
+        case 16:
+            return ht == 256 ? dispatch_chol<16, 256>(a, nrows, max_warps, gtable, chol32, st)
+                             : dispatch_chol<16, 1024>(a, nrows, max_warps, gtable, chol32, st);
+        case 32:
+            return ht == 256 ? dispatch_chol<32, 256>(a, nrows, max_warps, gtable, chol32, st)
+                             : dispatch_chol<32, 1024>(a, nrows, max_warps, gtable, chol32, st);
+        case 64:
+            return dispatch_chol<64, 1024>(a, nrows, max_warps, gtable, chol32, st);
+        case 128:
+            return dispatch_chol<128, 1024>(a, nrows, max_warps, gtable, chol32, st);
+        default:
+            return fail(AFSAI_ENOTSUP, "pattern capacity above 128");
+    }
+}
+
+// Per-row compaction into CSR with value conversion, plus column counts of
+// G (for the transpose) and the longest row.
+template <typename VT>
+__global__ void compact_rows_kernel(int32_t n, int64_t mcap, const int32_t* __restrict__ len,
+                                    const int32_t* __restrict__ ocol, const double* __restrict__ oval,
+                                    const int32_t* __restrict__ rowptr, int32_t* __restrict__ col,
+                                    VT* __restrict__ val, int32_t* __restrict__ colcount, int32_t* __restrict__ maxrow) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    int localmax = 0;
+    for (int64_t i = gw; i < n; i += nw) {
+        const int m = len[i];
+        const int32_t base = rowptr[i];
+        for (int t = lane; t < m; t += 32) {
+            const int32_t c = ocol[i * mcap + t];
+            col[base + t] = c;
+            val[base + t] = static_cast<VT>(oval[i * mcap + t]);
+            atomicAdd(&colcount[c], 1);
+        }
+        localmax = m > localmax ? m : localmax;
+    }
+    if (lane == 0 && localmax > 0) atomicMax(maxrow, localmax);
+}
+
+}  // namespace
+
+afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_row_nnz, cudaStream_t st,
+                        afsai_precond* M) {
+    const int32_t n = A->n;
+    const int64_t mcap = 1 + static_cast<int64_t>(p->kiter) * p->s;
+    if (mcap > 128) return fail(AFSAI_ENOTSUP, "1 + kiter*s must be <= 128");
+    const int mcap_t = mcap <= 16 ? 16 : (mcap <= 32 ? 32 : (mcap <= 64 ? 64 : 128));
+    // Shared table size: candidates are bounded by |P| * (longest row); the
+    // table keeps a load factor <= 3/4 up to that bound, else it relies on
+    // the overflow retry.
+    const int64_t cand_bound = mcap * static_cast<int64_t>(max_row_nnz);
+    int ht = 1024;
+    if (mcap_t <= 32 && cand_bound * 4 <= 256 * 3) ht = 256;
+    const bool chol32 = p->chol_prec == 1;
+
+    cudaEvent_t ev0, ev1;
+    AFSAI_CUDA_TRY(cudaEventCreate(&ev0));
+    AFSAI_CUDA_TRY(cudaEventCreate(&ev1));
+    AFSAI_CUDA_TRY(cudaEventRecord(ev0, st));
+
+    DevBuf<int32_t> len, ocol, status, retry, counters;
+    DevBuf<double> oval;
+    AFSAI_TRY(len.alloc(n, st));
+    AFSAI_TRY(ocol.alloc(static_cast<size_t>(n) * mcap, st));
+    AFSAI_TRY(oval.alloc(static_cast<size_t>(n) * mcap, st));
+    AFSAI_TRY(status.alloc(n, st));
+    AFSAI_TRY(retry.alloc(n, st));
+    AFSAI_TRY(counters.alloc(4, st));
+    AFSAI_CUDA_TRY(cudaMemsetAsync(counters.p, 0, 4 * sizeof(int32_t), st));
+    AFSAI_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&M->psi), sizeof(double) * n, st));
+    AFSAI_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&M->steps), sizeof(int32_t) * n, st));
+
+    SetupArgs a{};
+    a.n = n;
+    a.rowptr = A->rowptr;
+    a.col = A->col;
+    a.val = A->val;
+    a.kiter = p->kiter;
+    a.s = p->s;
+    a.exit_mode = p->exit_mode;
+    a.eps = p->eps;
+    a.mcap = mcap;
+    a.out_len = len.p;
+    a.out_col = ocol.p;
+    a.out_val = oval.p;
+    a.psi = M->psi;
+    a.steps = M->steps;
+    a.status = status.p;
+    a.rows = nullptr;
+    a.nrows = n;
+    a.retry_rows = retry.p;
+    a.counters = counters.p;
+    cudaEvent_t evk0, evk1;
+    AFSAI_CUDA_TRY(cudaEventCreate(&evk0));
+    AFSAI_CUDA_TRY(cudaEventCreate(&evk1));
+    AFSAI_CUDA_TRY(cudaEventRecord(evk0, st));
+    AFSAI_TRY(dispatch(mcap_t, ht, a, n, INT64_MAX, false, chol32, st));
+    AFSAI_CUDA_TRY(cudaEventRecord(evk1, st));
+
+    int32_t hc[4];
+    AFSAI_CUDA_TRY(cudaMemcpyAsync(hc, counters.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    AFSAI_CUDA_TRY(cudaStreamSynchronize(st));
+    float kms = 0.f;
+    cudaEventElapsedTime(&kms, evk0, evk1);
+    cudaEventDestroy(evk0);
+    cudaEventDestroy(evk1);
+    const int32_t nretry = hc[0];
+    if (nretry > 0) {
+        // redo the overflowed rows with a global-memory table per warp
+        int log2 = 6;
+        while ((int64_t(1) << log2) < 2 * cand_bound) ++log2;
+        int64_t warps = std::min<int64_t>(nretry, static_cast<int64_t>(num_sms()) * 64);
+        warps = (warps + 7) / 8 * 8;  // whole blocks of up to 8 warps
+        const int64_t slots = warps << log2;
+        DevBuf<int32_t> gkey, rows2, counters2;
+        DevBuf<double> gval;
+        AFSAI_TRY(gkey.alloc(slots, st));
+        AFSAI_TRY(gval.alloc(slots, st));
+        AFSAI_TRY(rows2.alloc(nretry, st));
+        AFSAI_TRY(counters2.alloc(4, st));
+        AFSAI_CUDA_TRY(cudaMemcpyAsync(rows2.p, retry.p, sizeof(int32_t) * nretry, cudaMemcpyDeviceToDevice, st));
+        AFSAI_CUDA_TRY(cudaMemsetAsync(counters2.p, 0, 4 * sizeof(int32_t), st));
+        SetupArgs b = a;
+        b.rows = rows2.p;
+        b.nrows = nretry;
+        b.counters = counters2.p;
+        b.gkey = gkey.p;
+        b.gval = gval.p;
+        b.ght_log2 = log2;
+        AFSAI_TRY(dispatch(mcap_t, ht, b, nretry, warps, true, chol32, st));
+        int32_t hc2[4];
+        AFSAI_CUDA_TRY(cudaMemcpyAsync(hc2, counters2.p, sizeof(hc2), cudaMemcpyDeviceToHost, st));
+        AFSAI_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hc2[0] != 0) return fail(AFSAI_ENOTSUP, "candidate table overflow in the retry pass");
+        hc[1] += hc2[1];
+    }
+    if (hc[1] > 0) {
+        return fail(AFSAI_ENOTSPD, "non-positive pivot in " + std::to_string(hc[1]) + " row system(s)");
+    }
+
+    // CSR of G
+    CsrDev& G = M->G;
+    G.n = n;
+    G.vtype = p->g_prec;
+    AFSAI_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&G.rowptr), sizeof(int32_t) * (n + 1), st));
+    int64_t nnz = 0;
+    AFSAI_TRY(exclusive_scan_i32(len.p, G.rowptr, n, st, &nnz));
+    G.nnz = nnz;
+    AFSAI_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&G.col), sizeof(int32_t) * std::max<int64_t>(nnz, 1), st));
+    AFSAI_CUDA_TRY(cudaMallocAsync(&G.val, val_bytes(G.vtype) * std::max<int64_t>(nnz, 1), st));
+    DevBuf<int32_t> colcount;
+    AFSAI_TRY(colcount.alloc(static_cast<size_t>(n) + 1, st));
+    AFSAI_CUDA_TRY(cudaMemsetAsync(colcount.p, 0, sizeof(int32_t) * (n + 1), st));
+    AFSAI_CUDA_TRY(cudaMemsetAsync(counters.p, 0, sizeof(int32_t), st));
+    {
+        const int threads = 256;
+        const int blocks = std::max(1, std::min(ceil_div(static_cast<int64_t>(n) * 32, threads), num_sms() * 16));
+        if (G.vtype == VAL_F64)
+            compact_rows_kernel<double><<<blocks, threads, 0, st>>>(n, mcap, len.p, ocol.p, oval.p, G.rowptr, G.col,
+                                                                   static_cast<double*>(G.val), colcount.p, counters.p);
+        else if (G.vtype == VAL_F32)
+            compact_rows_kernel<float><<<blocks, threads, 0, st>>>(n, mcap, len.p, ocol.p, oval.p, G.rowptr, G.col,
+                                                                  static_cast<float*>(G.val), colcount.p, counters.p);
+        else
+            compact_rows_kernel<__nv_bfloat16><<<blocks, threads, 0, st>>>(
+                n, mcap, len.p, ocol.p, oval.p, G.rowptr, G.col, static_cast<__nv_bfloat16*>(G.val), colcount.p,
+                counters.p);
+        AFSAI_CUDA_TRY(cudaGetLastError());
+        count_launches(1);
+    }
+    AFSAI_CUDA_TRY(cudaMemcpyAsync(&G.max_row, counters.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    AFSAI_TRY(build_transpose(G, &M->Gt, st));
+    AFSAI_CUDA_TRY(cudaEventRecord(ev1, st));
+    AFSAI_CUDA_TRY(cudaEventSynchronize(ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    M->info.n = n;
+    M->info.nnz_G = nnz;
+    M->info.max_row = G.max_row;
+    M->info.g_prec = G.vtype;
+    M->info.n_retry = nretry;
+    M->info.setup_ms = ms;
+    M->info.kernel_ms = kms;
+    return AFSAI_OK;
+}
+
+}  // namespace afsai

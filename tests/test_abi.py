@@ -1,0 +1,88 @@
+"""C ABI checks that need no GPU: the library builds for sm_103a, loads,
+exports every entry point include/afsai.h declares, and the ctypes
+structures of the binding match the C layout compiled from the header."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "afsai.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"AFSAI_API\s+[\w\s\*]+?\b(\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2010_14175_gb300 import afsai
+
+    return afsai.load()
+
+
+def test_library_exports_every_declared_function(lib):
+    from paper_2010_14175_gb300 import afsai
+
+    names = declared_functions()
+    assert len(names) >= 12
+    assert set(names) == set(afsai.EXPORTS)
+    out = subprocess.run(["nm", "-D", "--defined-only", afsai.library_path()], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r" T (\w+)$", out, re.M))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert getattr(lib, n) is not None
+
+
+def test_library_is_sm103a_only(lib):
+    from paper_2010_14175_gb300 import build
+
+    assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+    out = subprocess.run(["cuobjdump", "--list-elf", build.LIB], capture_output=True, text=True)
+    if out.returncode == 0:
+        assert "sm_103a" in out.stdout
+        assert "sm_100" not in out.stdout.replace("sm_103a", "")
+
+
+def test_host_only_calls(lib):
+    from paper_2010_14175_gb300 import afsai
+
+    assert lib.afsai_version().decode().startswith("afsai-gb300")
+    # argument checks run before any CUDA call
+    st = lib.afsai_setup(None, None, None, None)
+    assert st == afsai.EINVAL
+    assert b"NULL" in lib.afsai_last_error()
+    assert lib.afsai_get_info(None, None) == afsai.EINVAL
+    lib.afsai_destroy(None)
+
+
+def test_struct_layout_matches_header(tmp_path):
+    from paper_2010_14175_gb300 import afsai
+
+    src = tmp_path / "layout.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "afsai.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\\n", sizeof(afsai_csr), sizeof(afsai_params), sizeof(afsai_info), sizeof(pcg_info));
+  printf("%zu %zu %zu\\n", offsetof(afsai_csr, val), offsetof(afsai_params, chol_prec), offsetof(pcg_info, solve_ms));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    sizes = [int(v) for v in out]
+    assert sizes[0] == ctypes.sizeof(afsai.Csr)
+    assert sizes[1] == ctypes.sizeof(afsai.Params)
+    assert sizes[2] == ctypes.sizeof(afsai.Info)
+    assert sizes[3] == ctypes.sizeof(afsai.PcgInfo)
+    assert sizes[4] == afsai.Csr.val.offset
+    assert sizes[5] == afsai.Params.chol_prec.offset
+    assert sizes[6] == afsai.PcgInfo.solve_ms.offset

@@ -1,0 +1,152 @@
+"""GPU set-up parity: the CUDA aFSAI set-up (FP64 Cholesky) against the CPU
+oracle on the same seeded matrices, through the C ABI.
+
+Bar: identical patterns P_i and identical FP64 values of G (the kernel
+mirrors the plain FP64 definition operation for operation), identical psi
+and step counts, and G^T equal to the transpose of G.  Sizes span several
+thread blocks and warps with ragged tails; edge cases cover the diagonal
+pattern (kiter = 0), a full lower pattern, candidate-table overflow, both
+exit tests and malformed or indefinite input.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from paper_2010_14175_gb300 import matgen as mg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2010_14175_gb300 import afsai
+
+    afsai.load()
+    return afsai
+
+
+def run_gpu(afsai, A, kiter, s, eps, exit_mode=0, g_prec=0, chol_prec=0):
+    Ad = afsai.DeviceCSR.from_host(A)
+    M = afsai.afsai_setup(Ad, afsai.params(kiter, s, eps, exit_mode, g_prec, chol_prec))
+    rp, ci, va = M.export()
+    trp, tci, tva = M.export(transpose=True)
+    psi, steps = M.rows()
+    info = M.info()
+    M.close()
+    return dict(rowptr=rp, col=ci, val=va, trowptr=trp, tcol=tci, tval=tva, psi=psi, steps=steps, info=info)
+
+
+def assert_identical(g, ref, A):
+    assert np.array_equal(g["rowptr"], ref.rowptr), "row lengths differ"
+    assert np.array_equal(g["col"], ref.col), "patterns differ"
+    if not np.array_equal(g["val"], ref.val):
+        d = np.abs(g["val"] - ref.val) / np.abs(ref.val)
+        raise AssertionError(f"G values differ: max rel {d.max():.3e} at {int(np.argmax(d))}")
+    assert np.array_equal(g["psi"], ref.psi)
+    assert np.array_equal(g["steps"], ref.steps)
+    # explicit transpose: rows sorted, values identical to G^T
+    Gt = sp.csr_matrix((ref.val, ref.col, ref.rowptr), shape=(A.n, A.n)).T.tocsr()
+    Gt.sort_indices()
+    assert np.array_equal(g["trowptr"], Gt.indptr)
+    assert np.array_equal(g["tcol"], Gt.indices)
+    assert np.array_equal(g["tval"], Gt.data)
+
+
+CASES = [
+    ("poisson20", lambda: mg.poisson7(20), 5, 2, 1e-3, 0),
+    ("poisson_ragged", lambda: mg.poisson7(13, 7, 11), 5, 2, 1e-3, 0),
+    ("laplace1d", lambda: mg.laplace1d(1001), 10, 1, 0.05, 0),
+    ("laplace1d_literal", lambda: mg.laplace1d(777), 10, 1, 0.6, 1),
+    ("hetero24", lambda: mg.diffusion7_hetero(24, 99), 5, 2, 1e-3, 0),
+    ("elast6", lambda: mg.elasticity_hex(6, 17), 10, 3, 1e-3, 0),
+    ("fe27_aniso", lambda: mg.stencil27_fe(9, 8, 7, scale=(1.0, 1.0, 100.0)), 8, 2, 1e-3, 0),
+    ("poisson2d_aniso", lambda: mg.poisson5_2d(41, 37, scale=(1.0, 1e3)), 8, 2, 1e-3, 0),
+    ("random_spd", lambda: mg.random_spd(700, 0.01, 5), 6, 3, 1e-3, 0),
+    ("eps0_full_kiter", lambda: mg.poisson7(9), 7, 2, 0.0, 0),
+    ("kiter0_jacobi", lambda: mg.diffusion7_hetero(10, 3), 0, 1, 1e-3, 0),
+    ("dense_full_pattern", lambda: mg.random_spd(40, 1.0, 2, dense=True), 1, 64, 0.0, 0),
+    ("large_s", lambda: mg.poisson7(8), 3, 20, 1e-3, 0),
+    ("mcap_128", lambda: mg.random_spd(300, 0.05, 8), 21, 6, 0.0, 0),
+]
+
+
+@pytest.mark.parametrize("name,make,kiter,s,eps,mode", CASES, ids=[c[0] for c in CASES])
+def test_setup_bit_identical(gpu, oracle_mod, name, make, kiter, s, eps, mode):
+    A = make()
+    ref = oracle_mod.afsai_setup(A, kiter, s, eps, mode)
+    g = run_gpu(gpu, A, kiter, s, eps, mode)
+    assert g["info"]["nnz_G"] == ref.nnz
+    assert_identical(g, ref, A)
+
+
+def test_candidate_table_overflow_retry(gpu, oracle_mod):
+    # ~300 entries per row and 7-entry patterns: well over 1000 distinct
+    # candidates for the later rows, beyond the shared-memory table
+    A = mg.random_spd(3000, 0.1, 41)
+    ref = oracle_mod.afsai_setup(A, 3, 2, 0.0)
+    g = run_gpu(gpu, A, 3, 2, 0.0)
+    assert g["info"]["n_retry"] > 0
+    assert_identical(g, ref, A)
+
+
+def test_single_row_and_tiny(gpu, oracle_mod):
+    from paper_2010_14175_gb300.matgen import CSR
+
+    A = CSR(1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([4.0]))
+    ref = oracle_mod.afsai_setup(A, 5, 2, 1e-3)
+    g = run_gpu(gpu, A, 5, 2, 1e-3)
+    assert_identical(g, ref, A)
+    A2 = mg.laplace1d(2)
+    assert_identical(run_gpu(gpu, A2, 5, 2, 1e-3), oracle_mod.afsai_setup(A2, 5, 2, 1e-3), A2)
+
+
+def test_malformed_csr_rejected(gpu):
+    import torch
+
+    afsai = gpu
+    A = mg.poisson7(4)
+
+    def setup_of(rowptr, col, val, n=None):
+        Ad = afsai.DeviceCSR(A.n if n is None else n, torch.from_numpy(rowptr).cuda(), torch.from_numpy(col).cuda(),
+                             torch.from_numpy(val).cuda())
+        return afsai.afsai_setup(Ad, afsai.params(5, 2, 1e-3))
+
+    col = A.col.copy()
+    col[1], col[2] = col[2], col[1]  # unsorted row
+    with pytest.raises(afsai.AfsaiError) as e:
+        setup_of(A.rowptr, col, A.val)
+    assert e.value.status == afsai.EINVAL
+    col = A.col.copy()
+    col[5] = A.n  # out of range
+    with pytest.raises(afsai.AfsaiError) as e:
+        setup_of(A.rowptr, col, A.val)
+    assert e.value.status == afsai.EINVAL
+    val = A.val.copy()
+    val[A.col == np.repeat(np.arange(A.n), np.diff(A.rowptr))] *= -1.0  # negative diagonal
+    with pytest.raises(afsai.AfsaiError) as e:
+        setup_of(A.rowptr, A.col, val)
+    assert e.value.status == afsai.EINVAL
+    rp = A.rowptr.copy()
+    rp[3] = rp[2] - 1  # non-monotone
+    with pytest.raises(afsai.AfsaiError) as e:
+        setup_of(rp, A.col, A.val)
+    assert e.value.status == afsai.EINVAL
+    with pytest.raises(afsai.AfsaiError) as e:
+        afsai.afsai_setup(afsai.DeviceCSR.from_host(A), afsai.params(20, 7, 1e-3))  # 1 + kiter*s > 128
+    assert e.value.status == afsai.ENOTSUP
+
+
+def test_indefinite_matrix_reports_not_spd(gpu, oracle_mod):
+    afsai = gpu
+    from paper_2010_14175_gb300.matgen import CSR
+
+    # positive diagonal, indefinite: [[1, 2], [2, 1]]
+    A = CSR(2, np.array([0, 2, 4], np.int32), np.array([0, 1, 0, 1], np.int32), np.array([1.0, 2.0, 2.0, 1.0]))
+    with pytest.raises(RuntimeError):
+        oracle_mod.afsai_setup(A, 1, 1, 0.0)
+    with pytest.raises(afsai.AfsaiError) as e:
+        afsai.afsai_setup(afsai.DeviceCSR.from_host(A), afsai.params(1, 1, 0.0))
+    assert e.value.status == afsai.ENOTSPD
