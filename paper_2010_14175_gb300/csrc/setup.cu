@@ -75,25 +75,32 @@ struct SetupArgs {
     int32_t* __restrict__ counters;  // [0] retry count, [1] not-SPD count
     int32_t* __restrict__ gkey;      // global table (retry pass)
     double* __restrict__ gval;
+    int32_t* __restrict__ glist;
     int32_t ght_log2;
 };
 
 template <int MCAP, int HT>
 struct WarpWs {
-    double g[MCAP];
-    int32_t P[MCAP];
-    int32_t newj[MCAP];
-    int32_t nkeys;  // keys in the candidate table this step
+    double g[MCAP];                        // current (unscaled) solution, also the solve's z
+    double Mraw[MCAP * (MCAP + 1) / 2];    // gathered A[P,P], packed lower, persists across steps
+    int32_t P[MCAP];                       // pattern, sorted ascending (i last)
+    int32_t newj[MCAP];                    // picks of this step (reused as FP32 scratch)
+    int32_t rb[MCAP];                      // row bounds of the pattern's rows of A
+    int32_t re[MCAP];
+    int32_t isnew[MCAP];                   // 1 for positions inserted this step
+    int32_t opos[MCAP];                    // new position of each old position
+    int32_t nkeys;                         // keys in the candidate table this step
     int32_t pad_;
     union {
         struct {
             double val[HT];
             int32_t key[HT];
+            int32_t list[HT];              // slots in insertion order (compact candidate list)
         } h;
         struct {
-            double M[MCAP * (MCAP + 1) / 2];   // FP64 gather / factor
-            float Mf[MCAP * (MCAP + 1) / 2];   // FP32 factor (chol_prec = 1)
-        } d;
+            double L[MCAP * (MCAP + 1) / 2];   // FP64 factor (chol_prec = 0) / old Mraw during the move
+            float Lf[MCAP * (MCAP + 1) / 2];   // FP32 factor (chol_prec = 1)
+        } f;
     } u;
 };
 
@@ -119,15 +126,19 @@ __device__ __forceinline__ uint32_t slot_of(int32_t j, int log2) {
 }
 
 // Inserts j (or finds it) and returns its slot; -1 if the table is full.
-// `full` is set once the table holds more than 7/8 of its slots, which
-// sends the row to the retry pass with a larger table (bounded probing).
-__device__ __forceinline__ int table_insert(int32_t* key, int log2, int32_t j, int32_t* nkeys, bool& full) {
+// New slots are appended to the compact list.  `full` is set once the
+// table holds more than 7/8 of its slots, which sends the row to the retry
+// pass with a larger table (bounded probing).
+__device__ __forceinline__ int table_insert(int32_t* key, int32_t* list, int log2, int32_t j, int32_t* nkeys,
+                                            bool& full) {
     const uint32_t mask = (1u << log2) - 1u;
     uint32_t h = slot_of(j, log2);
     for (uint32_t probe = 0; probe <= mask; ++probe) {
         const int32_t cur = atomicCAS(&key[h], -1, j);
         if (cur == -1) {
-            if (atomicAdd(nkeys, 1) >= static_cast<int32_t>((mask + 1) - ((mask + 1) >> 3))) full = true;
+            const int32_t at = atomicAdd(nkeys, 1);
+            list[at] = static_cast<int32_t>(h);
+            if (at >= static_cast<int32_t>((mask + 1) - ((mask + 1) >> 3))) full = true;
             return static_cast<int>(h);
         }
         if (cur == j) return static_cast<int>(h);
@@ -149,23 +160,26 @@ __device__ __forceinline__ int table_find(const int32_t* key, int log2, int32_t 
     return -1;
 }
 
-// (col, (row-)index) pair of the lower triangle trailing block: linear
-// index idx -> (rr, qq) with qq <= rr, idx = rr(rr+1)/2 + qq.
-__device__ __forceinline__ void tri_unrank(int idx, int& rr, int& qq) {
-    int r = static_cast<int>((sqrtf(8.0f * static_cast<float>(idx) + 1.0f) - 1.0f) * 0.5f);
-    if (tri(r + 1) <= idx) ++r;
-    if (tri(r) > idx) --r;
-    rr = r;
-    qq = idx - tri(r);
+// x > 0 for an IEEE double, decided on the integer pipe: positive finite or
+// +inf (NaN and non-positive values give false, as the FP comparison does).
+__device__ __forceinline__ bool positive(double x) {
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b <= 0x7ff0000000000000ll;
+}
+__device__ __forceinline__ bool positive(float x) {
+    const int b = __float_as_int(x);
+    return b > 0 && b <= 0x7f800000;
 }
 
 // Right-looking Cholesky of the packed lower triangle M (m x m) in place.
-// Returns false (warp-uniform) on a non-positive pivot.
+// The trailing update of column c is spread over the lanes as (r, q) pairs
+// through the per-block table `pairs` (idx -> rr << 8 | qq, idx = rr(rr+1)/2
+// + qq).  Returns false (warp-uniform) on a non-positive pivot.
 template <typename T>
-__device__ bool warp_cholesky(T* M, int m, int lane) {
+__device__ bool warp_cholesky(T* M, int m, int lane, const uint16_t* pairs) {
     for (int c = 0; c < m; ++c) {
         const T piv = M[tri(c) + c];
-        if (!(piv > T(0))) return false;
+        if (!positive(piv)) return false;
         const T d = sqrt(piv);
         for (int r = c + 1 + lane; r < m; r += 32) M[tri(r) + c] = M[tri(r) + c] / d;
         __syncwarp();
@@ -173,9 +187,8 @@ __device__ bool warp_cholesky(T* M, int m, int lane) {
         const int w = m - c - 1;
         const int T_ = (w * (w + 1)) >> 1;
         for (int idx = lane; idx < T_; idx += 32) {
-            int rr, qq;
-            tri_unrank(idx, rr, qq);
-            const int r = c + 1 + rr, q = c + 1 + qq;
+            const int pr = pairs[idx];
+            const int r = c + 1 + (pr >> 8), q = c + 1 + (pr & 0xff);
             M[tri(r) + q] = fma(-M[tri(r) + c], M[tri(q) + c], M[tri(r) + q]);
         }
         __syncwarp();
@@ -214,32 +227,37 @@ __device__ void warp_llt_solve(const T* L, T* x, int m, bool em, int lane) {
 
 template <int MCAP, int HT, bool CHOL32>
 __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, int32_t* key, double* hv,
-                          int log2, int lane) {
+                          int32_t* list, int log2, int lane, const uint16_t* pairs) {
     const int ht = 1 << log2;
+    const int32_t* __restrict__ colA = a.col;
+    const double* __restrict__ valA = a.val;
     // a_ii (validated present and positive)
     double aii = 0.0;
-    bool found = false;
     {
         const int32_t e0 = a.rowptr[i], e1 = a.rowptr[i + 1];
+        bool found = false;
         for (int32_t e = e0 + lane; e < e1; e += 32)
-            if (a.col[e] == i) {
-                aii = a.val[e];
+            if (__ldg(&colA[e]) == i) {
+                aii = __ldg(&valA[e]);
                 found = true;
             }
         const unsigned bal = __ballot_sync(kFull, found);
         aii = __shfl_sync(kFull, aii, bal ? (__ffs(bal) - 1) : 0);
         if (!bal) aii = 0.0;
-    }
-    if (lane == 0) {
-        w.P[0] = i;
-        w.g[0] = 1.0 / aii;
+        if (lane == 0) {
+            w.P[0] = i;
+            w.g[0] = 1.0 / aii;
+            w.Mraw[0] = aii;
+            w.rb[0] = e0;
+            w.re[0] = e1;
+        }
     }
     __syncwarp();
     int m = 1;
     const double psi0 = aii;
     double psi_prev = psi0;
     int steps = 0;
-    int32_t status = (aii > 0.0) ? kRowOk : kRowNotSpd;
+    int32_t status = positive(aii) ? kRowOk : kRowNotSpd;
 
     for (int k = 1; k <= a.kiter && status == kRowOk; ++k) {
         // ---- Kaporin gradient over j < i (Eq. "grapsi") ----
@@ -251,14 +269,15 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
         __syncwarp();
         bool ovf = false;
         for (int t = 0; t < m; ++t) {
-            const int32_t r = w.P[t];
             const double gr = w.g[t];
-            const int32_t e0 = a.rowptr[r], e1 = a.rowptr[r + 1];
-            for (int32_t e = e0 + lane; e < e1; e += 32) {
-                const int32_t j = __ldg(&a.col[e]);
+            const int32_t e1 = w.re[t];
+            // columns are sorted: stop at the first chunk with no j < i
+            for (int32_t e = w.rb[t] + lane;; e += 32) {
+                const int32_t j = e < e1 ? __ldg(&colA[e]) : INT_MAX;
+                if (!__any_sync(kFull, j < i)) break;
                 if (j < i) {
-                    const int slot = table_insert(key, log2, j, &w.nkeys, ovf);
-                    if (slot >= 0) hv[slot] = fma(__ldg(&a.val[e]), gr, hv[slot]);
+                    const int slot = table_insert(key, list, log2, j, &w.nkeys, ovf);
+                    if (slot >= 0) hv[slot] = fma(__ldg(&valA[e]), gr, hv[slot]);
                 }
             }
             __syncwarp();
@@ -273,22 +292,23 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
             if (slot >= 0) hv[slot] = 0.0;
         }
         __syncwarp();
+        const int nk = w.nkeys;
         // ---- select the s largest |gradient| (ties: smaller column) ----
         int npick = 0;
         for (int u = 0; u < a.s; ++u) {
             unsigned long long best = 0ull;
             int32_t bestj = INT_MAX;
             int bslot = -1;
-            for (int t = lane; t < ht; t += 32) {
-                const int32_t j = key[t];
-                if (j < 0) continue;
+            for (int t = lane; t < nk; t += 32) {
+                const int sl = list[t];
+                const int32_t j = key[sl];
                 const unsigned long long ab =
-                    static_cast<unsigned long long>(__double_as_longlong(hv[t])) & 0x7fffffffffffffffull;
+                    static_cast<unsigned long long>(__double_as_longlong(hv[sl])) & 0x7fffffffffffffffull;
                 if (ab == 0ull || ab > 0x7ff0000000000000ull) continue;  // zero or NaN
                 if (ab > best || (ab == best && j < bestj)) {
                     best = ab;
                     bestj = j;
-                    bslot = t;
+                    bslot = sl;
                 }
             }
 #pragma unroll
@@ -311,54 +331,81 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
             __syncwarp();
         }
         if (npick == 0) break;
-        // ---- merge into the sorted pattern ----
+
+        // ---- merge into the sorted pattern; move the gathered triangle ----
+        const int mold = m;
+        m += npick;
+        ++steps;
+        // old triangle -> scratch (the hash table is dead from here on)
+        double* scratch = w.u.f.L;
+        const int told = tri(mold);
+        for (int t = lane; t < told; t += 32) scratch[t] = w.Mraw[t];
+        __syncwarp();
         if (lane == 0) {
+            for (int t = 0; t < m; ++t) w.isnew[t] = 0;
             for (int u = 0; u < npick; ++u) {
                 const int32_t j = w.newj[u];
-                int pos = m + u;
+                int pos = mold + u;
                 while (pos > 0 && w.P[pos - 1] > j) {
                     w.P[pos] = w.P[pos - 1];
+                    w.rb[pos] = w.rb[pos - 1];
+                    w.re[pos] = w.re[pos - 1];
+                    w.isnew[pos] = w.isnew[pos - 1];
                     --pos;
                 }
                 w.P[pos] = j;
+                w.isnew[pos] = 1;
             }
+            for (int q = 0, cnt = 0; q < m; ++q)
+                if (!w.isnew[q]) w.opos[cnt++] = q;
         }
-        m += npick;
-        ++steps;
         __syncwarp();
-
-        // ---- systems gather: packed lower triangle of A[P,P] ----
-        double* M = w.u.d.M;
-        const int nt = tri(m);
-        for (int t = lane; t < nt; t += 32) M[t] = 0.0;
+        const int tnew = tri(m);
+        for (int t = lane; t < tnew; t += 32) w.Mraw[t] = 0.0;
+        // row bounds of the new rows
+        for (int t = lane; t < m; t += 32)
+            if (w.isnew[t]) {
+                w.rb[t] = a.rowptr[w.P[t]];
+                w.re[t] = a.rowptr[w.P[t] + 1];
+            }
         __syncwarp();
-        for (int a_ = 0; a_ < m; ++a_) {
-            const int32_t r = w.P[a_];
-            const int32_t e0 = a.rowptr[r], e1 = a.rowptr[r + 1];
+        // old entries to their new positions (the order of old indices is kept)
+        for (int t = lane; t < told; t += 32) {
+            const int pr = pairs[t];
+            w.Mraw[tri(w.opos[pr >> 8]) + w.opos[pr & 0xff]] = scratch[t];
+        }
+        __syncwarp();
+        // ---- systems gather: rows of the new indices (A symmetric) ----
+        for (int pj = 0; pj < m; ++pj) {
+            if (!w.isnew[pj]) continue;
+            const int32_t e0 = w.rb[pj], e1 = w.re[pj];
             for (int32_t e = e0 + lane; e < e1; e += 32) {
-                const int32_t c = __ldg(&a.col[e]);
-                if (c <= r) {
-                    const int b = find_sorted(w.P, a_ + 1, c);
-                    if (b >= 0) M[tri(a_) + b] = __ldg(&a.val[e]);
-                }
+                const int32_t c = __ldg(&colA[e]);
+                const int pc = find_sorted(w.P, m, c);
+                if (pc < 0) continue;
+                if (pc <= pj)
+                    w.Mraw[tri(pj) + pc] = __ldg(&valA[e]);
+                else if (!w.isnew[pc])
+                    w.Mraw[tri(pc) + pj] = __ldg(&valA[e]);
             }
         }
         __syncwarp();
 
         // ---- dense solve A[P,P] g = e_m ----
         if (!CHOL32) {
-            if (!warp_cholesky<double>(M, m, lane)) {
+            double* L = w.u.f.L;
+            for (int t = lane; t < tnew; t += 32) L[t] = w.Mraw[t];
+            __syncwarp();
+            if (!warp_cholesky<double>(L, m, lane, pairs)) {
                 status = kRowNotSpd;
                 break;
             }
-            warp_llt_solve<double>(M, w.g, m, true, lane);
+            warp_llt_solve<double>(L, w.g, m, true, lane);
         } else {
-            // FP32 factor in its own packed buffer; the FP64 gather is kept
-            // for the refinement residual.
-            float* Lf = w.u.d.Mf;
-            for (int t = lane; t < nt; t += 32) Lf[t] = static_cast<float>(M[t]);
+            float* Lf = w.u.f.Lf;
+            for (int t = lane; t < tnew; t += 32) Lf[t] = static_cast<float>(w.Mraw[t]);
             __syncwarp();
-            if (!warp_cholesky<float>(Lf, m, lane)) {
+            if (!warp_cholesky<float>(Lf, m, lane, pairs)) {
                 status = kRowNotSpd;
                 break;
             }
@@ -370,7 +417,7 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
             for (int r = lane; r < m; r += 32) {
                 double acc = (r == m - 1) ? 1.0 : 0.0;
                 for (int q = 0; q < m; ++q) {
-                    const double arq = (q <= r) ? M[tri(r) + q] : M[tri(q) + r];
+                    const double arq = (q <= r) ? w.Mraw[tri(r) + q] : w.Mraw[tri(q) + r];
                     acc = fma(-arq, w.g[q], acc);
                 }
                 xf[r] = static_cast<float>(acc);
@@ -416,27 +463,42 @@ template <int MCAP, int HT, bool GTABLE, bool CHOL32>
 __global__ void __launch_bounds__(kSetupThreads) afsai_setup_kernel(SetupArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using WS = WarpWs<MCAP, HT>;
+    constexpr int kPairs = MCAP * (MCAP + 1) / 2;
+    const int nwarp_blk = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    WS& w = reinterpret_cast<WS*>(smem_raw)[warp];
-    const int64_t gwarp = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + warp;
-    const int64_t nwarps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    WS* ws = reinterpret_cast<WS*>(smem_raw);
+    uint16_t* pairs = reinterpret_cast<uint16_t*>(ws + nwarp_blk);
+    // (rr, qq) of the packed trailing triangle, shared by the block
+    for (int idx = threadIdx.x; idx < kPairs; idx += blockDim.x) {
+        int r = static_cast<int>((sqrtf(8.0f * static_cast<float>(idx) + 1.0f) - 1.0f) * 0.5f);
+        if (tri(r + 1) <= idx) ++r;
+        if (tri(r) > idx) --r;
+        pairs[idx] = static_cast<uint16_t>((r << 8) | (idx - tri(r)));
+    }
+    __syncthreads();
+    WS& w = ws[warp];
+    const int64_t gwarp = static_cast<int64_t>(blockIdx.x) * nwarp_blk + warp;
+    const int64_t nwarps = static_cast<int64_t>(gridDim.x) * nwarp_blk;
     int32_t* key;
     double* hv;
+    int32_t* list;
     int log2;
     if (GTABLE) {
         key = a.gkey + (gwarp << a.ght_log2);
         hv = a.gval + (gwarp << a.ght_log2);
+        list = a.glist + (gwarp << a.ght_log2);
         log2 = a.ght_log2;
     } else {
         key = w.u.h.key;
         hv = w.u.h.val;
+        list = w.u.h.list;
         log2 = __ffs(HT) - 1;
     }
     const int64_t nrows = a.rows ? a.nrows : a.n;
     for (int64_t t = gwarp; t < nrows; t += nwarps) {
         const int32_t i = a.rows ? a.rows[t] : static_cast<int32_t>(t);
-        afsai_row<MCAP, HT, CHOL32>(a, i, w, key, hv, log2, lane);
+        afsai_row<MCAP, HT, CHOL32>(a, i, w, key, hv, list, log2, lane, pairs);
     }
 }
 
@@ -452,9 +514,11 @@ afsai_status launch_setup(const SetupArgs& a, int64_t nrows, int64_t max_warps, 
     auto kern = afsai_setup_kernel<MCAP, HT, GTABLE, CHOL32>;
     // as many warps per block as fit in ~200 KB of shared memory (max 8)
     const size_t per_warp = ws_bytes<MCAP, HT>();
-    const int warps_per_block = static_cast<int>(std::max<size_t>(1, std::min<size_t>(8, (200u * 1024u) / per_warp)));
+    const size_t pairs_bytes = (sizeof(uint16_t) * (MCAP * (MCAP + 1) / 2) + 15) / 16 * 16;
+    const int warps_per_block =
+        static_cast<int>(std::max<size_t>(1, std::min<size_t>(8, (200u * 1024u - pairs_bytes) / per_warp)));
     const int threads = warps_per_block * 32;
-    const size_t smem = per_warp * warps_per_block;
+    const size_t smem = per_warp * warps_per_block + pairs_bytes;
     AFSAI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     int per_sm = 0;
     AFSAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
@@ -485,14 +549,14 @@ afsai_status dispatch(int mcap_t, int ht, const SetupArgs& a, int64_t nrows, int
     switch (mcap_t) {
         case 16:
             return ht == 256 ? dispatch_chol<16, 256>(a, nrows, max_warps, gtable, chol32, st)
-                             : dispatch_chol<16, 1024>(a, nrows, max_warps, gtable, chol32, st);
+                             : dispatch_chol<16, 512>(a, nrows, max_warps, gtable, chol32, st);
         case 32:
             return ht == 256 ? dispatch_chol<32, 256>(a, nrows, max_warps, gtable, chol32, st)
-                             : dispatch_chol<32, 1024>(a, nrows, max_warps, gtable, chol32, st);
+                             : dispatch_chol<32, 512>(a, nrows, max_warps, gtable, chol32, st);
         case 64:
-            return dispatch_chol<64, 1024>(a, nrows, max_warps, gtable, chol32, st);
+            return dispatch_chol<64, 512>(a, nrows, max_warps, gtable, chol32, st);
         case 128:
-            return dispatch_chol<128, 1024>(a, nrows, max_warps, gtable, chol32, st);
+            return dispatch_chol<128, 512>(a, nrows, max_warps, gtable, chol32, st);
         default:
             return fail(AFSAI_ENOTSUP, "pattern capacity above 128");
     }
@@ -535,8 +599,8 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
     // table keeps a load factor <= 3/4 up to that bound, else it relies on
     // the overflow retry.
     const int64_t cand_bound = mcap * static_cast<int64_t>(max_row_nnz);
-    int ht = 1024;
-    if (mcap_t <= 32 && cand_bound * 4 <= 256 * 3) ht = 256;
+    int ht = 512;
+    if (mcap_t <= 32 && cand_bound * 8 <= 256 * 7) ht = 256;
     const bool chol32 = p->chol_prec == 1;
 
     cudaEvent_t ev0, ev1;
@@ -598,9 +662,10 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
         int64_t warps = std::min<int64_t>(nretry, static_cast<int64_t>(num_sms()) * 64);
         warps = (warps + 7) / 8 * 8;  // whole blocks of up to 8 warps
         const int64_t slots = warps << log2;
-        DevBuf<int32_t> gkey, rows2, counters2;
+        DevBuf<int32_t> gkey, glist, rows2, counters2;
         DevBuf<double> gval;
         AFSAI_TRY(gkey.alloc(slots, st));
+        AFSAI_TRY(glist.alloc(slots, st));
         AFSAI_TRY(gval.alloc(slots, st));
         AFSAI_TRY(rows2.alloc(nretry, st));
         AFSAI_TRY(counters2.alloc(4, st));
@@ -612,6 +677,7 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
         b.counters = counters2.p;
         b.gkey = gkey.p;
         b.gval = gval.p;
+        b.glist = glist.p;
         b.ght_log2 = log2;
         AFSAI_TRY(dispatch(mcap_t, ht, b, nretry, warps, true, chol32, st));
         int32_t hc2[4];
