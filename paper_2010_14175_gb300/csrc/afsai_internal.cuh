@@ -116,6 +116,7 @@ afsai_status build_transpose(const CsrDev& G, CsrDev* Gt, cudaStream_t st);
 afsai_status spmv_csr(const CsrDev& A, const double* x, double* y, cudaStream_t st);
 afsai_status apply_precond(const afsai_precond* M, const double* r, double* t, double* z, cudaStream_t st);
 void free_csr(CsrDev* A, cudaStream_t st);
+int32_t* error_flag();  // device flag set by a bounded device-side wait that ran out
 
 // PCG (pcg.cu).
 afsai_status pcg_impl(const afsai_csr* A, const afsai_precond* M, const double* b, double* x, double rtol,

@@ -2,17 +2,19 @@
 // stopping at ||r_k|| <= rtol ||b|| (Section 5.2: an 8-order reduction).
 //
 // Standard (Hestenes-Stiefel) PCG, one iteration =
-//   q = A p,            pq = p.q,  alpha = rz / pq           [spmv_dot]
+//   q = A p,            pq = p.q,  alpha = rz / pq           [spmv A + dot]
 //   x += alpha p, r -= alpha q,    rr = r.r, convergence test [update_xr]
-//   t = G r                                                   [spmv_G]
-//   z = G^T t,          rz' = r.z, beta = rz' / rz            [spmv_Gt_dot]
+//   t = G r                                                   [spmv G]
+//   z = G^T t,          rz' = r.z, beta = rz' / rz            [spmv G^T + dot]
 //   p = z + beta p                                            [update_p]
-// All scalars live in device memory.  Each reduction is deterministic: every
-// block writes one partial, and the last block to finish (atomic ticket)
-// sums the partials in a fixed order and derives alpha, beta or the
-// convergence flag.  Once converged, every kernel returns at entry, so
-// iterations can be enqueued ahead in a CUDA graph of several iterations
-// and the host only polls the flag between graph launches.
+// The three SpMVs are the TMA-staged kernels of spmv_tiled.cuh with the
+// dot product fused into their epilogue.  All scalars live in device
+// memory.  Each reduction is deterministic: every block writes one partial,
+// and the last block to finish (atomic ticket) sums the partials in a fixed
+// order and derives alpha, beta or the convergence flag.  Once converged,
+// every kernel returns at entry, so iterations are enqueued ahead in a CUDA
+// graph of several iterations and the host only polls the flag between
+// graph launches.
 //
 // Residual, dot products, alpha and beta are FP64 whatever the precision of
 // G; with an FP32/BF16 G the two triangular products run in FP32.
@@ -20,9 +22,9 @@
 #include <cmath>
 #include <cstdlib>
 #include <type_traits>
-#include <vector>
 
 #include "afsai_internal.cuh"
+#include "spmv_tiled.cuh"
 
 namespace afsai {
 namespace {
@@ -37,17 +39,19 @@ struct Scalars {
     double rr;
     double bb;
     double tol2;
-    int32_t done;   // 0 running, 1 converged, 2 maxit reached
+    int32_t done;  // 0 running, 1 converged, 2 maxit reached, 3 device wait expired
     int32_t iters;
     int32_t maxit;
-    int32_t pad;
+    int32_t err;   // set by a bounded wait that ran out
     unsigned ticket[8];
 };
 
-// Block sum of one or two values (fixed shuffle tree, then warp 0).
+// Block sum of K values (fixed shuffle tree, then warp 0).  blockDim.x is
+// a multiple of 32 and at most 1024.
 template <int K>
 __device__ __forceinline__ void block_sum(double (&v)[K], double (*sh)[32]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
 #pragma unroll
@@ -58,7 +62,7 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double (*sh)[32]) {
     if (warp == 0) {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-            double w = lane < (kThreads >> 5) ? sh[k][lane] : 0.0;
+            double w = lane < nwarps ? sh[k][lane] : 0.0;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(kFull, w, o);
             v[k] = w;
@@ -98,28 +102,8 @@ __device__ bool grid_sum(double (&v)[K], double* partials, unsigned* ticket) {
     return true;
 }
 
-template <typename VT>
-__device__ __forceinline__ double ld_f64(const VT* p) {
-    return static_cast<double>(__ldg(p));
-}
-__device__ __forceinline__ float ld_f32(const float* p) { return __ldg(p); }
-__device__ __forceinline__ float ld_f32(const __nv_bfloat16* p) { return __bfloat162float(*p); }
-
-// Row i of an FP64 CSR times x, by a group of L lanes (L = 1: sequential).
-template <int L>
-__device__ __forceinline__ double row_dot_f64(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                              const double* __restrict__ val, const double* __restrict__ x, int64_t i,
-                                              int64_t n, int sub) {
-    double acc = 0.0;
-    if (i < n) {
-        const int32_t b = rowptr[i], e = rowptr[i + 1];
-        for (int32_t k = b + sub; k < e; k += L) acc = fma(__ldg(&val[k]), __ldg(&x[__ldg(&col[k])]), acc);
-    }
-    if (L > 1) {
-#pragma unroll
-        for (int o = L >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o, L);
-    }
-    return acc;
+__device__ __forceinline__ void abort_solve(Scalars* s) {
+    if (threadIdx.x == 0) atomicExch(&s->done, 3);
 }
 
 // ---- init: r = b - q (q = A x), rr = r.r, bb = b.b ----------------------
@@ -154,25 +138,37 @@ __global__ void k_init_p(int32_t n, const double* __restrict__ r, const double* 
     if (grid_sum<1>(v, partials, &s->ticket[1]) && threadIdx.x == 0) s->rz = v[0];
 }
 
-// ---- q = A p, pq = p.q, alpha = rz / pq ----------------------------------
-template <int L>
-__global__ void k_spmv_A_dot(int32_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                             const double* __restrict__ val, const double* __restrict__ p, double* __restrict__ q,
-                             Scalars* s, double* partials) {
-    if (s->done) return;
-    const int sub = threadIdx.x & (L - 1);
-    const int64_t g0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / L;
-    const int64_t ng = (static_cast<int64_t>(gridDim.x) * blockDim.x) / L;
-    const int64_t nloop = (n + ng - 1) / ng;
-    double v[1] = {0.0};
-    for (int64_t it = 0; it < nloop; ++it) {
-        const int64_t i = g0 + it * ng;
-        const double qi = row_dot_f64<L>(rowptr, col, val, p, i, n, sub);
-        if (i < n && sub == 0) {
-            q[i] = qi;
-            v[0] = fma(p[i], qi, v[0]);
-        }
+// Epilogues of the tiled SpMVs.
+template <typename ACC, typename YT>
+struct EpiStore {
+    YT* y;
+    __device__ void row(int64_t i, ACC a) { y[i] = static_cast<YT>(a); }
+};
+template <typename ACC>
+struct EpiStoreDot {
+    double* y;
+    const double* w;
+    double dot;
+    __device__ void row(int64_t i, ACC a) {
+        const double d = static_cast<double>(a);
+        y[i] = d;
+        dot = fma(w[i], d, dot);
     }
+};
+
+// ---- q = A p, pq = p.q, alpha = rz / pq ----------------------------------
+template <int MODE>
+__global__ void k_spmv_A_dot(int32_t n, int64_t nnz, const int32_t* __restrict__ rowptr,
+                             const int32_t* __restrict__ col, const double* __restrict__ val,
+                             const double* __restrict__ p, double* __restrict__ q, Scalars* s, double* partials,
+                             int cap) {
+    if (s->done) return;
+    EpiStoreDot<double> epi{q, p, 0.0};
+    if (!tiled::spmv_rows<MODE, double, double, double>(n, nnz, rowptr, col, val, p, cap, &s->err, epi)) {
+        abort_solve(s);
+        return;
+    }
+    double v[1] = {epi.dot};
     if (grid_sum<1>(v, partials, &s->ticket[2]) && threadIdx.x == 0) s->alpha = s->rz / v[0];
 }
 
@@ -199,84 +195,29 @@ __global__ void k_update_xr(int32_t n, double* __restrict__ x, double* __restric
     }
 }
 
-// ---- t = G r (FP64 G) ------------------------------------------------------
-template <int L>
-__global__ void k_spmv_G_f64(int32_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                             const double* __restrict__ val, const double* __restrict__ r, double* __restrict__ t,
-                             const Scalars* s, int init) {
+// ---- t = G r (ACC/YT: double for an FP64 G, float otherwise) ---------------
+template <int MODE, typename VT, typename ACC>
+__global__ void k_spmv_G(int32_t n, int64_t nnz, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                         const VT* __restrict__ val, const double* __restrict__ r, ACC* __restrict__ t, Scalars* s,
+                         int cap, int init) {
     if (!init && s->done) return;
-    const int sub = threadIdx.x & (L - 1);
-    const int64_t g0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / L;
-    const int64_t ng = (static_cast<int64_t>(gridDim.x) * blockDim.x) / L;
-    const int64_t nloop = (n + ng - 1) / ng;
-    for (int64_t it = 0; it < nloop; ++it) {
-        const int64_t i = g0 + it * ng;
-        const double ti = row_dot_f64<L>(rowptr, col, val, r, i, n, sub);
-        if (i < n && sub == 0) t[i] = ti;
-    }
+    EpiStore<ACC, ACC> epi{t};
+    if (!tiled::spmv_rows<MODE, VT, double, ACC>(n, nnz, rowptr, col, val, r, cap, &s->err, epi)) abort_solve(s);
 }
 
-// ---- z = G^T t, rz' = r.z, beta (FP64 G) -----------------------------------
-template <int L>
-__global__ void k_spmv_Gt_dot_f64(int32_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                  const double* __restrict__ val, const double* __restrict__ t,
-                                  const double* __restrict__ r, double* __restrict__ z, Scalars* s, double* partials,
-                                  int init) {
+// ---- z = G^T t, rz' = r.z, beta -------------------------------------------
+template <int MODE, typename VT, typename ACC>
+__global__ void k_spmv_Gt_dot(int32_t n, int64_t nnz, const int32_t* __restrict__ rowptr,
+                              const int32_t* __restrict__ col, const VT* __restrict__ val, const ACC* __restrict__ t,
+                              const double* __restrict__ r, double* __restrict__ z, Scalars* s, double* partials,
+                              int cap, int init) {
     if (!init && s->done) return;
-    const int sub = threadIdx.x & (L - 1);
-    const int64_t g0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / L;
-    const int64_t ng = (static_cast<int64_t>(gridDim.x) * blockDim.x) / L;
-    const int64_t nloop = (n + ng - 1) / ng;
-    double v[1] = {0.0};
-    for (int64_t it = 0; it < nloop; ++it) {
-        const int64_t i = g0 + it * ng;
-        const double zi = row_dot_f64<L>(rowptr, col, val, t, i, n, sub);
-        if (i < n && sub == 0) {
-            z[i] = zi;
-            v[0] = fma(r[i], zi, v[0]);
-        }
+    EpiStoreDot<ACC> epi{z, r, 0.0};
+    if (!tiled::spmv_rows<MODE, VT, ACC, ACC>(n, nnz, rowptr, col, val, t, cap, &s->err, epi)) {
+        abort_solve(s);
+        return;
     }
-    if (grid_sum<1>(v, partials, &s->ticket[4]) && threadIdx.x == 0) {
-        if (init) {
-            s->rz = v[0];
-        } else {
-            s->beta = v[0] / s->rz;
-            s->rz = v[0];
-        }
-    }
-}
-
-// ---- reduced-precision G: t = G r (fp32 out), z = G^T t (fp64 out) ---------
-template <typename VT>
-__global__ void k_spmv_G_lowp(int32_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                              const VT* __restrict__ val, const double* __restrict__ r, float* __restrict__ t,
-                              const Scalars* s, int init) {
-    if (!init && s->done) return;
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int32_t b = rowptr[i], e = rowptr[i + 1];
-        float acc = 0.0f;
-        for (int32_t k = b; k < e; ++k) acc = fmaf(ld_f32(&val[k]), static_cast<float>(__ldg(&r[__ldg(&col[k])])), acc);
-        t[i] = acc;
-    }
-}
-
-template <typename VT>
-__global__ void k_spmv_Gt_dot_lowp(int32_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                   const VT* __restrict__ val, const float* __restrict__ t,
-                                   const double* __restrict__ r, double* __restrict__ z, Scalars* s,
-                                   double* partials, int init) {
-    if (!init && s->done) return;
-    double v[1] = {0.0};
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int32_t b = rowptr[i], e = rowptr[i + 1];
-        float acc = 0.0f;
-        for (int32_t k = b; k < e; ++k) acc = fmaf(ld_f32(&val[k]), __ldg(&t[__ldg(&col[k])]), acc);
-        const double zi = static_cast<double>(acc);
-        z[i] = zi;
-        v[0] = fma(r[i], zi, v[0]);
-    }
+    double v[1] = {epi.dot};
     if (grid_sum<1>(v, partials, &s->ticket[4]) && threadIdx.x == 0) {
         if (init) {
             s->rz = v[0];
@@ -328,22 +269,31 @@ __global__ void k_true_residual(int32_t n, const double* __restrict__ b, const d
     if (grid_sum<1>(v, partials, &s->ticket[5]) && threadIdx.x == 0) *out = v[0];
 }
 
-int group_for(int64_t n, int64_t nnz) {
-    static int forced = [] {
-        const char* e = std::getenv("AFSAI_SPMV_GROUP");
-        return e ? std::atoi(e) : 0;
-    }();
-    if (forced == 1 || forced == 2 || forced == 4 || forced == 8) return forced;
-    const double avg = n > 0 ? static_cast<double>(nnz) / n : 0.0;
-    if (avg <= 16.0) return 1;
-    if (avg <= 48.0) return 2;
-    return 4;
+// Vector kernels: a small persistent grid, so that each thread sums many
+// elements before the (FP64) block reduction.
+int vec_blocks(int64_t n) {
+    const int64_t need = (n + kThreads - 1) / kThreads;
+    const int64_t cap = static_cast<int64_t>(num_sms()) * 2;
+    return static_cast<int>(std::max<int64_t>(1, std::min(need, cap)));
 }
 
-int blocks_for(int64_t items) {
-    const int64_t need = (items + kThreads - 1) / kThreads;
-    const int64_t cap = static_cast<int64_t>(num_sms()) * (2048 / kThreads) * 2;
-    return static_cast<int>(std::max<int64_t>(1, std::min(need, cap)));
+template <typename K>
+void set_smem_attr(K kern, size_t smem) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+}
+
+// Calls f(std::integral_constant<int, MODE>) for the engine mode.
+template <typename F>
+bool with_mode(int mode, F f) {
+    switch (mode) {
+        case 1: f(std::integral_constant<int, 1>{}); return true;
+        case 2: f(std::integral_constant<int, 2>{}); return true;
+        case 4: f(std::integral_constant<int, 4>{}); return true;
+        case 8: f(std::integral_constant<int, 8>{}); return true;
+        case 101: f(std::integral_constant<int, 101>{}); return true;
+        case 102: f(std::integral_constant<int, 102>{}); return true;
+        default: return false;
+    }
 }
 
 struct Launcher {
@@ -355,72 +305,86 @@ struct Launcher {
     Scalars* s;
     double* partials;
     cudaStream_t st;
+    SpmvMode ma, mg, mt;
 
-    template <typename F>
-    afsai_status by_group(int L, F f) {
-        switch (L) {
-            case 1: f(std::integral_constant<int, 1>{}); break;
-            case 2: f(std::integral_constant<int, 2>{}); break;
-            case 4: f(std::integral_constant<int, 4>{}); break;
-            default: f(std::integral_constant<int, 8>{}); break;
+    // engine choice and shared-memory limits, before any stream capture
+    afsai_status plan() {
+        AFSAI_TRY(spmv_mode_for(ROLE_A, *A, st, &ma));
+        if (M) {
+            AFSAI_TRY(spmv_mode_for(ROLE_G, M->G, st, &mg));
+            AFSAI_TRY(spmv_mode_for(ROLE_GT, M->Gt, st, &mt));
         }
+        with_mode(ma.mode, [&](auto Mc) { set_smem_attr(k_spmv_A_dot<decltype(Mc)::value>, 200u * 1024u); });
+        if (M) {
+            const int vt = M->G.vtype;
+            with_mode(mg.mode, [&](auto Mc) {
+                constexpr int MD = decltype(Mc)::value;
+                if (vt == VAL_F64) set_smem_attr(k_spmv_G<MD, double, double>, 200u * 1024u);
+                if (vt == VAL_F32) set_smem_attr(k_spmv_G<MD, float, float>, 200u * 1024u);
+                if (vt == VAL_BF16) set_smem_attr(k_spmv_G<MD, __nv_bfloat16, float>, 200u * 1024u);
+            });
+            with_mode(mt.mode, [&](auto Mc) {
+                constexpr int MD = decltype(Mc)::value;
+                if (vt == VAL_F64) set_smem_attr(k_spmv_Gt_dot<MD, double, double>, 200u * 1024u);
+                if (vt == VAL_F32) set_smem_attr(k_spmv_Gt_dot<MD, float, float>, 200u * 1024u);
+                if (vt == VAL_BF16) set_smem_attr(k_spmv_Gt_dot<MD, __nv_bfloat16, float>, 200u * 1024u);
+            });
+        }
+        return AFSAI_OK;
+    }
+
+    afsai_status spmv_A_dot() {
+        const auto* v = static_cast<const double*>(A->val);
+        with_mode(ma.mode, [&](auto Mc) {
+            k_spmv_A_dot<decltype(Mc)::value><<<ma.blocks, ma.threads, ma.smem, st>>>(
+                A->n, A->nnz, A->rowptr, A->col, v, p, q, s, partials, ma.cap);
+        });
         AFSAI_CUDA_TRY(cudaGetLastError());
         count_launches(1);
         return AFSAI_OK;
     }
 
+    template <typename VT, typename ACC>
+    void launch_G_pair(const CsrDev& G, const CsrDev& Gt, int init) {
+        ACC* tt = reinterpret_cast<ACC*>(t);
+        with_mode(mg.mode, [&](auto Mc) {
+            k_spmv_G<decltype(Mc)::value, VT, ACC><<<mg.blocks, mg.threads, mg.smem, st>>>(
+                G.n, G.nnz, G.rowptr, G.col, static_cast<const VT*>(G.val), r, tt, s, mg.cap, init);
+        });
+        with_mode(mt.mode, [&](auto Mc) {
+            k_spmv_Gt_dot<decltype(Mc)::value, VT, ACC><<<mt.blocks, mt.threads, mt.smem, st>>>(
+                Gt.n, Gt.nnz, Gt.rowptr, Gt.col, static_cast<const VT*>(Gt.val), tt, r, z, s, partials, mt.cap, init);
+        });
+    }
+
     // z = M r and rz (init: rz only; else beta too)
     afsai_status precond_dot(int init) {
         if (!M) {
-            k_copy_dot<<<blocks_for(n), kThreads, 0, st>>>(n, r, z, s, partials, init);
+            k_copy_dot<<<vec_blocks(n), kThreads, 0, st>>>(n, r, z, s, partials, init);
             AFSAI_CUDA_TRY(cudaGetLastError());
             count_launches(1);
             return AFSAI_OK;
         }
         const CsrDev& G = M->G;
         const CsrDev& Gt = M->Gt;
-        if (G.vtype == VAL_F64) {
-            const int LG = group_for(G.n, G.nnz), LT = group_for(Gt.n, Gt.nnz);
-            AFSAI_TRY(by_group(LG, [&](auto Lc) {
-                constexpr int L = decltype(Lc)::value;
-                k_spmv_G_f64<L><<<blocks_for(int64_t(n) * L), kThreads, 0, st>>>(
-                    n, G.rowptr, G.col, static_cast<const double*>(G.val), r, t, s, init);
-            }));
-            return by_group(LT, [&](auto Lc) {
-                constexpr int L = decltype(Lc)::value;
-                k_spmv_Gt_dot_f64<L><<<blocks_for(int64_t(n) * L), kThreads, 0, st>>>(
-                    n, Gt.rowptr, Gt.col, static_cast<const double*>(Gt.val), t, r, z, s, partials, init);
-            });
-        }
-        float* tf = reinterpret_cast<float*>(t);
-        if (G.vtype == VAL_F32) {
-            k_spmv_G_lowp<float><<<blocks_for(n), kThreads, 0, st>>>(n, G.rowptr, G.col,
-                                                                     static_cast<const float*>(G.val), r, tf, s, init);
-            k_spmv_Gt_dot_lowp<float><<<blocks_for(n), kThreads, 0, st>>>(
-                n, Gt.rowptr, Gt.col, static_cast<const float*>(Gt.val), tf, r, z, s, partials, init);
-        } else {
-            k_spmv_G_lowp<__nv_bfloat16><<<blocks_for(n), kThreads, 0, st>>>(
-                n, G.rowptr, G.col, static_cast<const __nv_bfloat16*>(G.val), r, tf, s, init);
-            k_spmv_Gt_dot_lowp<__nv_bfloat16><<<blocks_for(n), kThreads, 0, st>>>(
-                n, Gt.rowptr, Gt.col, static_cast<const __nv_bfloat16*>(Gt.val), tf, r, z, s, partials, init);
-        }
+        if (G.vtype == VAL_F64)
+            launch_G_pair<double, double>(G, Gt, init);
+        else if (G.vtype == VAL_F32)
+            launch_G_pair<float, float>(G, Gt, init);
+        else
+            launch_G_pair<__nv_bfloat16, float>(G, Gt, init);
         AFSAI_CUDA_TRY(cudaGetLastError());
         count_launches(2);
         return AFSAI_OK;
     }
 
     afsai_status iteration() {
-        const int LA = group_for(A->n, A->nnz);
-        AFSAI_TRY(by_group(LA, [&](auto Lc) {
-            constexpr int L = decltype(Lc)::value;
-            k_spmv_A_dot<L><<<blocks_for(int64_t(n) * L), kThreads, 0, st>>>(
-                n, A->rowptr, A->col, static_cast<const double*>(A->val), p, q, s, partials);
-        }));
-        k_update_xr<<<blocks_for(n), kThreads, 0, st>>>(n, x, r, p, q, s, partials);
+        AFSAI_TRY(spmv_A_dot());
+        k_update_xr<<<vec_blocks(n), kThreads, 0, st>>>(n, x, r, p, q, s, partials);
         AFSAI_CUDA_TRY(cudaGetLastError());
         count_launches(1);
         AFSAI_TRY(precond_dot(0));
-        k_update_p<<<blocks_for(n), kThreads, 0, st>>>(n, z, p, s);
+        k_update_p<<<vec_blocks(n), kThreads, 0, st>>>(n, z, p, s);
         AFSAI_CUDA_TRY(cudaGetLastError());
         count_launches(1);
         return AFSAI_OK;
@@ -436,10 +400,6 @@ int iters_per_graph() {
     return v;
 }
 
-}  // namespace
-
-namespace {
-
 afsai_status pcg_body(const CsrDev& A, const afsai_precond* M, const double* b, double* x, double rtol,
                       int32_t maxit, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1, pcg_info* info) {
     const int32_t n = A.n;
@@ -449,7 +409,6 @@ afsai_status pcg_body(const CsrDev& A, const afsai_precond* M, const double* b, 
     AFSAI_TRY(partials.alloc(static_cast<size_t>(num_sms()) * 64, st));
     AFSAI_TRY(sc.alloc(1, st));
     AFSAI_TRY(trueres.alloc(1, st));
-    AFSAI_CUDA_TRY(cudaMemsetAsync(sc.p, 0, sizeof(Scalars), st));
     Scalars init_s{};
     init_s.maxit = maxit;
     AFSAI_CUDA_TRY(cudaMemcpyAsync(sc.p, &init_s, sizeof(Scalars), cudaMemcpyHostToDevice, st));
@@ -467,14 +426,18 @@ afsai_status pcg_body(const CsrDev& A, const afsai_precond* M, const double* b, 
     L.s = sc.p;
     L.partials = partials.p;
     L.st = st;
+    AFSAI_TRY(L.plan());
+    // partials hold one value per block of the largest grid (2 per block for K = 2)
+    if (std::max({L.ma.blocks, L.mg.blocks, L.mt.blocks, vec_blocks(n)}) * 2 > num_sms() * 64)
+        return fail(AFSAI_ENOTSUP, "reduction grid larger than the partials buffer");
 
     AFSAI_CUDA_TRY(cudaEventRecord(ev0, st));
     // r = b - A x ; z = M r ; p = z
     AFSAI_TRY(spmv_csr(A, x, L.q, st));
-    k_init_residual<<<blocks_for(n), kThreads, 0, st>>>(n, b, L.q, L.r, sc.p, partials.p, rtol);
+    k_init_residual<<<vec_blocks(n), kThreads, 0, st>>>(n, b, L.q, L.r, sc.p, partials.p, rtol);
     AFSAI_CUDA_TRY(cudaGetLastError());
     AFSAI_TRY(L.precond_dot(1));
-    k_init_p<<<blocks_for(n), kThreads, 0, st>>>(n, L.r, L.z, L.p, sc.p, partials.p);
+    k_init_p<<<vec_blocks(n), kThreads, 0, st>>>(n, L.r, L.z, L.p, sc.p, partials.p);
     AFSAI_CUDA_TRY(cudaGetLastError());
     count_launches(2);
 
@@ -517,7 +480,7 @@ afsai_status pcg_body(const CsrDev& A, const afsai_precond* M, const double* b, 
     AFSAI_CUDA_TRY(cudaEventRecord(ev1, st));
     // true residual
     AFSAI_TRY(spmv_csr(A, x, L.q, st));
-    k_true_residual<<<blocks_for(n), kThreads, 0, st>>>(n, b, L.q, sc.p, partials.p, trueres.p);
+    k_true_residual<<<vec_blocks(n), kThreads, 0, st>>>(n, b, L.q, sc.p, partials.p, trueres.p);
     AFSAI_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     Scalars hs{};
@@ -535,6 +498,7 @@ afsai_status pcg_body(const CsrDev& A, const afsai_precond* M, const double* b, 
         info->relres_true = bn > 0 ? std::sqrt(tr2) / bn : 0.0;
         info->solve_ms = ms;
     }
+    if (hs.done == 3 || hs.err) return fail(AFSAI_ETIMEOUT, "a bounded device wait ran out during PCG");
     if (hs.done == 2) return fail(AFSAI_ENOCONV, "PCG reached maxit without convergence");
     return AFSAI_OK;
 }

@@ -40,6 +40,7 @@
 // redone by a second launch that keeps the table in global memory.
 #include <algorithm>
 #include <climits>
+#include <cstdlib>
 #include <string>
 
 #include "afsai_internal.cuh"
@@ -175,23 +176,23 @@ __device__ __forceinline__ bool positive(float x) {
 // The trailing update of column c is spread over the lanes as (r, q) pairs
 // through the per-block table `pairs` (idx -> rr << 8 | qq, idx = rr(rr+1)/2
 // + qq).  Returns false (warp-uniform) on a non-positive pivot.
-template <typename T>
-__device__ bool warp_cholesky(T* M, int m, int lane, const uint16_t* pairs) {
+template <int GL, typename T>
+__device__ bool group_cholesky(T* M, int m, int sub, unsigned gmask, const uint16_t* pairs) {
     for (int c = 0; c < m; ++c) {
         const T piv = M[tri(c) + c];
         if (!positive(piv)) return false;
         const T d = sqrt(piv);
-        for (int r = c + 1 + lane; r < m; r += 32) M[tri(r) + c] = M[tri(r) + c] / d;
-        __syncwarp();
-        if (lane == 0) M[tri(c) + c] = d;
+        for (int r = c + 1 + sub; r < m; r += GL) M[tri(r) + c] = M[tri(r) + c] / d;
+        __syncwarp(gmask);
+        if (sub == 0) M[tri(c) + c] = d;
         const int w = m - c - 1;
         const int T_ = (w * (w + 1)) >> 1;
-        for (int idx = lane; idx < T_; idx += 32) {
+        for (int idx = sub; idx < T_; idx += GL) {
             const int pr = pairs[idx];
             const int r = c + 1 + (pr >> 8), q = c + 1 + (pr & 0xff);
             M[tri(r) + q] = fma(-M[tri(r) + c], M[tri(q) + c], M[tri(r) + q]);
         }
-        __syncwarp();
+        __syncwarp(gmask);
     }
     return true;
 }
@@ -200,34 +201,34 @@ __device__ bool warp_cholesky(T* M, int m, int lane, const uint16_t* pairs) {
 // oriented as in the plain definition: forward L z = rhs, back L^T x = z.
 // When `em` is true the right-hand side is e_m and the forward solve
 // reduces to z = e_m / L_mm.
-template <typename T>
-__device__ void warp_llt_solve(const T* L, T* x, int m, bool em, int lane) {
+template <int GL, typename T>
+__device__ void group_llt_solve(const T* L, T* x, int m, bool em, int sub, unsigned gmask) {
     if (em) {
-        for (int t = lane; t < m; t += 32) x[t] = T(0);
-        __syncwarp();
-        if (lane == 0) x[m - 1] = T(1) / L[tri(m - 1) + m - 1];
-        __syncwarp();
+        for (int t = sub; t < m; t += GL) x[t] = T(0);
+        __syncwarp(gmask);
+        if (sub == 0) x[m - 1] = T(1) / L[tri(m - 1) + m - 1];
+        __syncwarp(gmask);
     } else {
         for (int c = 0; c < m; ++c) {
             const T zc = x[c] / L[tri(c) + c];
-            __syncwarp();
-            if (lane == 0) x[c] = zc;
-            for (int r = c + 1 + lane; r < m; r += 32) x[r] = fma(-L[tri(r) + c], zc, x[r]);
-            __syncwarp();
+            __syncwarp(gmask);
+            if (sub == 0) x[c] = zc;
+            for (int r = c + 1 + sub; r < m; r += GL) x[r] = fma(-L[tri(r) + c], zc, x[r]);
+            __syncwarp(gmask);
         }
     }
     for (int c = m - 1; c >= 0; --c) {
         const T gc = x[c] / L[tri(c) + c];
-        __syncwarp();
-        if (lane == 0) x[c] = gc;
-        for (int r = lane; r < c; r += 32) x[r] = fma(-L[tri(c) + r], gc, x[r]);
-        __syncwarp();
+        __syncwarp(gmask);
+        if (sub == 0) x[c] = gc;
+        for (int r = sub; r < c; r += GL) x[r] = fma(-L[tri(c) + r], gc, x[r]);
+        __syncwarp(gmask);
     }
 }
 
-template <int MCAP, int HT, bool CHOL32>
+template <int GL, int MCAP, int HT, bool CHOL32>
 __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, int32_t* key, double* hv,
-                          int32_t* list, int log2, int lane, const uint16_t* pairs) {
+                          int32_t* list, int log2, int sub, unsigned gmask, const uint16_t* pairs) {
     const int ht = 1 << log2;
     const int32_t* __restrict__ colA = a.col;
     const double* __restrict__ valA = a.val;
@@ -236,15 +237,15 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
     {
         const int32_t e0 = a.rowptr[i], e1 = a.rowptr[i + 1];
         bool found = false;
-        for (int32_t e = e0 + lane; e < e1; e += 32)
+        for (int32_t e = e0 + sub; e < e1; e += GL)
             if (__ldg(&colA[e]) == i) {
                 aii = __ldg(&valA[e]);
                 found = true;
             }
-        const unsigned bal = __ballot_sync(kFull, found);
-        aii = __shfl_sync(kFull, aii, bal ? (__ffs(bal) - 1) : 0);
+        const unsigned bal = __ballot_sync(gmask, found) & gmask;
+        aii = __shfl_sync(gmask, aii, bal ? ((__ffs(bal) - 1) & (GL - 1)) : 0, GL);
         if (!bal) aii = 0.0;
-        if (lane == 0) {
+        if (sub == 0) {
             w.P[0] = i;
             w.g[0] = 1.0 / aii;
             w.Mraw[0] = aii;
@@ -252,7 +253,7 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
             w.re[0] = e1;
         }
     }
-    __syncwarp();
+    __syncwarp(gmask);
     int m = 1;
     const double psi0 = aii;
     double psi_prev = psi0;
@@ -261,37 +262,37 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
 
     for (int k = 1; k <= a.kiter && status == kRowOk; ++k) {
         // ---- Kaporin gradient over j < i (Eq. "grapsi") ----
-        for (int t = lane; t < ht; t += 32) {
+        for (int t = sub; t < ht; t += GL) {
             key[t] = -1;
             hv[t] = 0.0;
         }
-        if (lane == 0) w.nkeys = 0;
-        __syncwarp();
+        if (sub == 0) w.nkeys = 0;
+        __syncwarp(gmask);
         bool ovf = false;
         for (int t = 0; t < m; ++t) {
             const double gr = w.g[t];
             const int32_t e1 = w.re[t];
             // columns are sorted: stop at the first chunk with no j < i
-            for (int32_t e = w.rb[t] + lane;; e += 32) {
+            for (int32_t e = w.rb[t] + sub;; e += GL) {
                 const int32_t j = e < e1 ? __ldg(&colA[e]) : INT_MAX;
-                if (!__any_sync(kFull, j < i)) break;
+                if (!__any_sync(gmask, j < i)) break;
                 if (j < i) {
                     const int slot = table_insert(key, list, log2, j, &w.nkeys, ovf);
                     if (slot >= 0) hv[slot] = fma(__ldg(&valA[e]), gr, hv[slot]);
                 }
             }
-            __syncwarp();
+            __syncwarp(gmask);
         }
-        if (__any_sync(kFull, ovf)) {
+        if (__any_sync(gmask, ovf)) {
             status = kRowOverflow;
             break;
         }
         // members of P are not eligible: zero their accumulated gradient
-        for (int t = lane; t < m - 1; t += 32) {
+        for (int t = sub; t < m - 1; t += GL) {
             const int slot = table_find(key, log2, w.P[t]);
             if (slot >= 0) hv[slot] = 0.0;
         }
-        __syncwarp();
+        __syncwarp(gmask);
         const int nk = w.nkeys;
         // ---- select the s largest |gradient| (ties: smaller column) ----
         int npick = 0;
@@ -299,7 +300,7 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
             unsigned long long best = 0ull;
             int32_t bestj = INT_MAX;
             int bslot = -1;
-            for (int t = lane; t < nk; t += 32) {
+            for (int t = sub; t < nk; t += GL) {
                 const int sl = list[t];
                 const int32_t j = key[sl];
                 const unsigned long long ab =
@@ -312,10 +313,10 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
                 }
             }
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const unsigned long long ob = __shfl_xor_sync(kFull, best, off);
-                const int32_t oj = __shfl_xor_sync(kFull, bestj, off);
-                const int os = __shfl_xor_sync(kFull, bslot, off);
+            for (int off = GL / 2; off > 0; off >>= 1) {
+                const unsigned long long ob = __shfl_xor_sync(gmask, best, off, GL);
+                const int32_t oj = __shfl_xor_sync(gmask, bestj, off, GL);
+                const int os = __shfl_xor_sync(gmask, bslot, off, GL);
                 if (ob > best || (ob == best && oj < bestj)) {
                     best = ob;
                     bestj = oj;
@@ -323,12 +324,12 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
                 }
             }
             if (best == 0ull) break;
-            if (lane == 0) {
+            if (sub == 0) {
                 hv[bslot] = 0.0;
                 w.newj[npick] = bestj;
             }
             ++npick;
-            __syncwarp();
+            __syncwarp(gmask);
         }
         if (npick == 0) break;
 
@@ -339,9 +340,9 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
         // old triangle -> scratch (the hash table is dead from here on)
         double* scratch = w.u.f.L;
         const int told = tri(mold);
-        for (int t = lane; t < told; t += 32) scratch[t] = w.Mraw[t];
-        __syncwarp();
-        if (lane == 0) {
+        for (int t = sub; t < told; t += GL) scratch[t] = w.Mraw[t];
+        __syncwarp(gmask);
+        if (sub == 0) {
             for (int t = 0; t < m; ++t) w.isnew[t] = 0;
             for (int u = 0; u < npick; ++u) {
                 const int32_t j = w.newj[u];
@@ -359,27 +360,27 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
             for (int q = 0, cnt = 0; q < m; ++q)
                 if (!w.isnew[q]) w.opos[cnt++] = q;
         }
-        __syncwarp();
+        __syncwarp(gmask);
         const int tnew = tri(m);
-        for (int t = lane; t < tnew; t += 32) w.Mraw[t] = 0.0;
+        for (int t = sub; t < tnew; t += GL) w.Mraw[t] = 0.0;
         // row bounds of the new rows
-        for (int t = lane; t < m; t += 32)
+        for (int t = sub; t < m; t += GL)
             if (w.isnew[t]) {
                 w.rb[t] = a.rowptr[w.P[t]];
                 w.re[t] = a.rowptr[w.P[t] + 1];
             }
-        __syncwarp();
+        __syncwarp(gmask);
         // old entries to their new positions (the order of old indices is kept)
-        for (int t = lane; t < told; t += 32) {
+        for (int t = sub; t < told; t += GL) {
             const int pr = pairs[t];
             w.Mraw[tri(w.opos[pr >> 8]) + w.opos[pr & 0xff]] = scratch[t];
         }
-        __syncwarp();
+        __syncwarp(gmask);
         // ---- systems gather: rows of the new indices (A symmetric) ----
         for (int pj = 0; pj < m; ++pj) {
             if (!w.isnew[pj]) continue;
             const int32_t e0 = w.rb[pj], e1 = w.re[pj];
-            for (int32_t e = e0 + lane; e < e1; e += 32) {
+            for (int32_t e = e0 + sub; e < e1; e += GL) {
                 const int32_t c = __ldg(&colA[e]);
                 const int pc = find_sorted(w.P, m, c);
                 if (pc < 0) continue;
@@ -389,32 +390,32 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
                     w.Mraw[tri(pc) + pj] = __ldg(&valA[e]);
             }
         }
-        __syncwarp();
+        __syncwarp(gmask);
 
         // ---- dense solve A[P,P] g = e_m ----
         if (!CHOL32) {
             double* L = w.u.f.L;
-            for (int t = lane; t < tnew; t += 32) L[t] = w.Mraw[t];
-            __syncwarp();
-            if (!warp_cholesky<double>(L, m, lane, pairs)) {
+            for (int t = sub; t < tnew; t += GL) L[t] = w.Mraw[t];
+            __syncwarp(gmask);
+            if (!group_cholesky<GL, double>(L, m, sub, gmask, pairs)) {
                 status = kRowNotSpd;
                 break;
             }
-            warp_llt_solve<double>(L, w.g, m, true, lane);
+            group_llt_solve<GL, double>(L, w.g, m, true, sub, gmask);
         } else {
             float* Lf = w.u.f.Lf;
-            for (int t = lane; t < tnew; t += 32) Lf[t] = static_cast<float>(w.Mraw[t]);
-            __syncwarp();
-            if (!warp_cholesky<float>(Lf, m, lane, pairs)) {
+            for (int t = sub; t < tnew; t += GL) Lf[t] = static_cast<float>(w.Mraw[t]);
+            __syncwarp(gmask);
+            if (!group_cholesky<GL, float>(Lf, m, sub, gmask, pairs)) {
                 status = kRowNotSpd;
                 break;
             }
             float* xf = reinterpret_cast<float*>(w.newj);  // m floats of scratch
-            warp_llt_solve<float>(Lf, xf, m, true, lane);
-            for (int t = lane; t < m; t += 32) w.g[t] = static_cast<double>(xf[t]);
-            __syncwarp();
+            group_llt_solve<GL, float>(Lf, xf, m, true, sub, gmask);
+            for (int t = sub; t < m; t += GL) w.g[t] = static_cast<double>(xf[t]);
+            __syncwarp(gmask);
             // one FP64 refinement step: res = e_m - A[P,P] g (symmetric, lower stored)
-            for (int r = lane; r < m; r += 32) {
+            for (int r = sub; r < m; r += GL) {
                 double acc = (r == m - 1) ? 1.0 : 0.0;
                 for (int q = 0; q < m; ++q) {
                     const double arq = (q <= r) ? w.Mraw[tri(r) + q] : w.Mraw[tri(q) + r];
@@ -422,10 +423,10 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
                 }
                 xf[r] = static_cast<float>(acc);
             }
-            __syncwarp();
-            warp_llt_solve<float>(Lf, xf, m, false, lane);
-            for (int t = lane; t < m; t += 32) w.g[t] = w.g[t] + static_cast<double>(xf[t]);
-            __syncwarp();
+            __syncwarp(gmask);
+            group_llt_solve<GL, float>(Lf, xf, m, false, sub, gmask);
+            for (int t = sub; t < m; t += GL) w.g[t] = w.g[t] + static_cast<double>(xf[t]);
+            __syncwarp(gmask);
         }
         const double psi = 1.0 / w.g[m - 1];
         const bool stop = (a.exit_mode == 0) ? ((psi_prev - psi) < a.eps * psi_prev) : ((psi / psi0) <= a.eps);
@@ -436,17 +437,17 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
     if (status == kRowOk) {
         const double sq = sqrt(w.g[m - 1]);
         const int64_t o = static_cast<int64_t>(i) * a.mcap;
-        for (int t = lane; t < m; t += 32) {
+        for (int t = sub; t < m; t += GL) {
             a.out_col[o + t] = w.P[t];
             a.out_val[o + t] = w.g[t] / sq;
         }
-        if (lane == 0) {
+        if (sub == 0) {
             a.out_len[i] = m;
             a.psi[i] = psi_prev;
             a.steps[i] = steps;
             a.status[i] = kRowOk;
         }
-    } else if (lane == 0) {
+    } else if (sub == 0) {
         a.out_len[i] = 0;
         a.status[i] = status;
         if (status == kRowOverflow) {
@@ -456,20 +457,22 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
             atomicAdd(&a.counters[1], 1);
         }
     }
-    __syncwarp();
+    __syncwarp(gmask);
 }
 
-template <int MCAP, int HT, bool GTABLE, bool CHOL32>
+template <int GL, int MCAP, int HT, bool GTABLE, bool CHOL32>
 __global__ void __launch_bounds__(kSetupThreads) afsai_setup_kernel(SetupArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using WS = WarpWs<MCAP, HT>;
     constexpr int kPairs = MCAP * (MCAP + 1) / 2;
-    const int nwarp_blk = blockDim.x >> 5;
-    const int warp = threadIdx.x >> 5;
+    const int ngroup_blk = blockDim.x / GL;
+    const int group = threadIdx.x / GL;
     const int lane = threadIdx.x & 31;
+    const int sub = lane & (GL - 1);
+    const unsigned gmask = (GL == 32) ? 0xffffffffu : (((1u << GL) - 1u) << (lane & ~(GL - 1)));
     WS* ws = reinterpret_cast<WS*>(smem_raw);
-    uint16_t* pairs = reinterpret_cast<uint16_t*>(ws + nwarp_blk);
-    // (rr, qq) of the packed trailing triangle, shared by the block
+    uint16_t* pairs = reinterpret_cast<uint16_t*>(ws + ngroup_blk);
+    // (rr, qq) of a packed triangle, shared by the block
     for (int idx = threadIdx.x; idx < kPairs; idx += blockDim.x) {
         int r = static_cast<int>((sqrtf(8.0f * static_cast<float>(idx) + 1.0f) - 1.0f) * 0.5f);
         if (tri(r + 1) <= idx) ++r;
@@ -477,17 +480,17 @@ __global__ void __launch_bounds__(kSetupThreads) afsai_setup_kernel(SetupArgs a)
         pairs[idx] = static_cast<uint16_t>((r << 8) | (idx - tri(r)));
     }
     __syncthreads();
-    WS& w = ws[warp];
-    const int64_t gwarp = static_cast<int64_t>(blockIdx.x) * nwarp_blk + warp;
-    const int64_t nwarps = static_cast<int64_t>(gridDim.x) * nwarp_blk;
+    WS& w = ws[group];
+    const int64_t ggroup = static_cast<int64_t>(blockIdx.x) * ngroup_blk + group;
+    const int64_t ngroups = static_cast<int64_t>(gridDim.x) * ngroup_blk;
     int32_t* key;
     double* hv;
     int32_t* list;
     int log2;
     if (GTABLE) {
-        key = a.gkey + (gwarp << a.ght_log2);
-        hv = a.gval + (gwarp << a.ght_log2);
-        list = a.glist + (gwarp << a.ght_log2);
+        key = a.gkey + (ggroup << a.ght_log2);
+        hv = a.gval + (ggroup << a.ght_log2);
+        list = a.glist + (ggroup << a.ght_log2);
         log2 = a.ght_log2;
     } else {
         key = w.u.h.key;
@@ -496,9 +499,9 @@ __global__ void __launch_bounds__(kSetupThreads) afsai_setup_kernel(SetupArgs a)
         log2 = __ffs(HT) - 1;
     }
     const int64_t nrows = a.rows ? a.nrows : a.n;
-    for (int64_t t = gwarp; t < nrows; t += nwarps) {
+    for (int64_t t = ggroup; t < nrows; t += ngroups) {
         const int32_t i = a.rows ? a.rows[t] : static_cast<int32_t>(t);
-        afsai_row<MCAP, HT, CHOL32>(a, i, w, key, hv, list, log2, lane, pairs);
+        afsai_row<GL, MCAP, HT, CHOL32>(a, i, w, key, hv, list, log2, sub, gmask, pairs);
     }
 }
 
@@ -509,24 +512,35 @@ constexpr size_t ws_bytes() {
     return sizeof(WarpWs<MCAP, HT>);
 }
 
-template <int MCAP, int HT, bool GTABLE, bool CHOL32>
-afsai_status launch_setup(const SetupArgs& a, int64_t nrows, int64_t max_warps, cudaStream_t st) {
-    auto kern = afsai_setup_kernel<MCAP, HT, GTABLE, CHOL32>;
-    // as many warps per block as fit in ~200 KB of shared memory (max 8)
-    const size_t per_warp = ws_bytes<MCAP, HT>();
+template <int GL, int MCAP, int HT, bool GTABLE, bool CHOL32>
+afsai_status launch_setup(const SetupArgs& a, int64_t nrows, int64_t max_groups, cudaStream_t st) {
+    auto kern = afsai_setup_kernel<GL, MCAP, HT, GTABLE, CHOL32>;
+    // block size (whole warps, <= 256 threads) that maximises resident row
+    // groups per SM under the shared-memory budget
+    const size_t per_group = ws_bytes<MCAP, HT>();
     const size_t pairs_bytes = (sizeof(uint16_t) * (MCAP * (MCAP + 1) / 2) + 15) / 16 * 16;
-    const int warps_per_block =
-        static_cast<int>(std::max<size_t>(1, std::min<size_t>(8, (200u * 1024u - pairs_bytes) / per_warp)));
-    const int threads = warps_per_block * 32;
-    const size_t smem = per_warp * warps_per_block + pairs_bytes;
+    const size_t sm_budget = 227u * 1024u;
+    int groups_blk = 32 / GL;
+    int best_total = 0;
+    for (int gb = 32 / GL; gb <= kSetupThreads / GL; gb += 32 / GL) {
+        const size_t blk = per_group * gb + pairs_bytes + 1024;  // + reserved per block
+        if (blk > sm_budget) break;
+        const int per = static_cast<int>(std::min<size_t>(sm_budget / blk, 2048 / (gb * GL)));
+        if (per * gb > best_total) {
+            best_total = per * gb;
+            groups_blk = gb;
+        }
+    }
+    const int threads = groups_blk * GL;
+    const size_t smem = per_group * groups_blk + pairs_bytes;
     AFSAI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
     int per_sm = 0;
     AFSAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     if (per_sm < 1) return fail(AFSAI_ENOTSUP, "set-up workspace does not fit in shared memory");
     int64_t blocks = static_cast<int64_t>(per_sm) * num_sms();
-    const int64_t need = (nrows + warps_per_block - 1) / warps_per_block;
+    const int64_t need = (nrows + groups_blk - 1) / groups_blk;
     if (blocks > need) blocks = need;
-    if (blocks * warps_per_block > max_warps) blocks = max_warps / warps_per_block;  // global table capacity
+    if (blocks * groups_blk > max_groups) blocks = max_groups / groups_blk;  // global table capacity
     if (blocks < 1) blocks = 1;
     kern<<<static_cast<unsigned>(blocks), threads, smem, st>>>(a);
     AFSAI_CUDA_TRY(cudaGetLastError());
@@ -534,29 +548,39 @@ afsai_status launch_setup(const SetupArgs& a, int64_t nrows, int64_t max_warps, 
     return AFSAI_OK;
 }
 
-template <int MCAP, int HT>
-afsai_status dispatch_chol(const SetupArgs& a, int64_t nrows, int64_t max_warps, bool gtable, bool chol32,
+template <int GL, int MCAP, int HT>
+afsai_status dispatch_chol(const SetupArgs& a, int64_t nrows, int64_t max_groups, bool gtable, bool chol32,
                           cudaStream_t st) {
     if (gtable)
-        return chol32 ? launch_setup<MCAP, HT, true, true>(a, nrows, max_warps, st)
-                      : launch_setup<MCAP, HT, true, false>(a, nrows, max_warps, st);
-    return chol32 ? launch_setup<MCAP, HT, false, true>(a, nrows, max_warps, st)
-                  : launch_setup<MCAP, HT, false, false>(a, nrows, max_warps, st);
+        return chol32 ? launch_setup<GL, MCAP, HT, true, true>(a, nrows, max_groups, st)
+                      : launch_setup<GL, MCAP, HT, true, false>(a, nrows, max_groups, st);
+    return chol32 ? launch_setup<GL, MCAP, HT, false, true>(a, nrows, max_groups, st)
+                  : launch_setup<GL, MCAP, HT, false, false>(a, nrows, max_groups, st);
 }
 
-afsai_status dispatch(int mcap_t, int ht, const SetupArgs& a, int64_t nrows, int64_t max_warps, bool gtable,
+// Lanes per row.  The row code is written for groups of GL lanes, but only
+// whole warps are instantiated: groups packed into one warp diverge and
+// lose more than the shared square roots and divisions gain.
+template <int MCAP, int HT>
+afsai_status dispatch_gl(int gl, const SetupArgs& a, int64_t nrows, int64_t max_groups, bool gtable, bool chol32,
+                         cudaStream_t st) {
+    (void)gl;  // one warp per row (packing rows into a warp measured slower: the groups diverge)
+    return dispatch_chol<32, MCAP, HT>(a, nrows, max_groups, gtable, chol32, st);
+}
+
+afsai_status dispatch(int mcap_t, int ht, int gl, const SetupArgs& a, int64_t nrows, int64_t max_groups, bool gtable,
                       bool chol32, cudaStream_t st) {
     switch (mcap_t) {
         case 16:
-            return ht == 256 ? dispatch_chol<16, 256>(a, nrows, max_warps, gtable, chol32, st)
-                             : dispatch_chol<16, 512>(a, nrows, max_warps, gtable, chol32, st);
+            return ht == 256 ? dispatch_gl<16, 256>(gl, a, nrows, max_groups, gtable, chol32, st)
+                             : dispatch_gl<16, 512>(gl, a, nrows, max_groups, gtable, chol32, st);
         case 32:
-            return ht == 256 ? dispatch_chol<32, 256>(a, nrows, max_warps, gtable, chol32, st)
-                             : dispatch_chol<32, 512>(a, nrows, max_warps, gtable, chol32, st);
+            return ht == 256 ? dispatch_gl<32, 256>(gl, a, nrows, max_groups, gtable, chol32, st)
+                             : dispatch_gl<32, 512>(gl, a, nrows, max_groups, gtable, chol32, st);
         case 64:
-            return dispatch_chol<64, 512>(a, nrows, max_warps, gtable, chol32, st);
+            return dispatch_chol<32, 64, 512>(a, nrows, max_groups, gtable, chol32, st);
         case 128:
-            return dispatch_chol<128, 512>(a, nrows, max_warps, gtable, chol32, st);
+            return dispatch_chol<32, 128, 512>(a, nrows, max_groups, gtable, chol32, st);
         default:
             return fail(AFSAI_ENOTSUP, "pattern capacity above 128");
     }
@@ -587,6 +611,12 @@ __global__ void compact_rows_kernel(int32_t n, int64_t mcap, const int32_t* __re
     if (lane == 0 && localmax > 0) atomicMax(maxrow, localmax);
 }
 
+int lanes_per_row(int mcap_t, bool chol32) {
+    (void)mcap_t;
+    (void)chol32;
+    return 32;
+}
+
 }  // namespace
 
 afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_row_nnz, cudaStream_t st,
@@ -602,6 +632,7 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
     int ht = 512;
     if (mcap_t <= 32 && cand_bound * 8 <= 256 * 7) ht = 256;
     const bool chol32 = p->chol_prec == 1;
+    const int gl = lanes_per_row(mcap_t, chol32);
 
     cudaEvent_t ev0, ev1;
     AFSAI_CUDA_TRY(cudaEventCreate(&ev0));
@@ -644,7 +675,7 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
     AFSAI_CUDA_TRY(cudaEventCreate(&evk0));
     AFSAI_CUDA_TRY(cudaEventCreate(&evk1));
     AFSAI_CUDA_TRY(cudaEventRecord(evk0, st));
-    AFSAI_TRY(dispatch(mcap_t, ht, a, n, INT64_MAX, false, chol32, st));
+    AFSAI_TRY(dispatch(mcap_t, ht, gl, a, n, INT64_MAX, false, chol32, st));
     AFSAI_CUDA_TRY(cudaEventRecord(evk1, st));
 
     int32_t hc[4];
@@ -679,7 +710,7 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
         b.gval = gval.p;
         b.glist = glist.p;
         b.ght_log2 = log2;
-        AFSAI_TRY(dispatch(mcap_t, ht, b, nretry, warps, true, chol32, st));
+        AFSAI_TRY(dispatch(mcap_t, ht, gl, b, nretry, warps, true, chol32, st));
         int32_t hc2[4];
         AFSAI_CUDA_TRY(cudaMemcpyAsync(hc2, counters2.p, sizeof(hc2), cudaMemcpyDeviceToHost, st));
         AFSAI_CUDA_TRY(cudaStreamSynchronize(st));

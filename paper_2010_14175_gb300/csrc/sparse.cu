@@ -10,8 +10,15 @@
 #include <algorithm>
 #include <climits>
 #include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include <cmath>
 
 #include "afsai_internal.cuh"
+#include "spmv_tiled.cuh"
 
 namespace afsai {
 namespace {
@@ -172,83 +179,17 @@ __global__ void sort_rows_rank(int32_t n, const int32_t* __restrict__ rowptr, co
 }
 
 // ---------------------------------------------------------------------------
-// SpMV kernels
+// SpMV kernels (row engines in spmv_tiled.cuh)
 // ---------------------------------------------------------------------------
-template <typename VT>
-__device__ __forceinline__ double as_f64(VT v) {
-    return static_cast<double>(v);
-}
-template <>
-__device__ __forceinline__ double as_f64<__nv_bfloat16>(__nv_bfloat16 v) {
-    return static_cast<double>(__bfloat162float(v));
-}
-template <typename VT>
-__device__ __forceinline__ float as_f32(VT v) {
-    return static_cast<float>(v);
-}
-template <>
-__device__ __forceinline__ float as_f32<__nv_bfloat16>(__nv_bfloat16 v) {
-    return __bfloat162float(v);
-}
-
-// FP64 values and vectors: one lane per row, fma in CSR order.
-__global__ void spmv_f64_scalar(int32_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y) {
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int32_t b = rowptr[i], e = rowptr[i + 1];
-        double acc = 0.0;
-        for (int32_t k = b; k < e; ++k) acc = fma(__ldg(&val[k]), __ldg(&x[__ldg(&col[k])]), acc);
-        y[i] = acc;
-    }
-}
-
-// FP64: L lanes per row, lanes stride the row, shuffle reduction.
-template <int L>
-__global__ void spmv_f64_group(int32_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                               const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y) {
-    const int sub = threadIdx.x & (L - 1);
-    const int64_t g0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / L;
-    const int64_t ng = (static_cast<int64_t>(gridDim.x) * blockDim.x) / L;
-    const int64_t nloop = (n + ng - 1) / ng;  // uniform trip count keeps the shuffles convergent
-    for (int64_t it = 0; it < nloop; ++it) {
-        const int64_t i = g0 + it * ng;
-        double acc = 0.0;
-        if (i < n) {
-            const int32_t b = rowptr[i], e = rowptr[i + 1];
-            for (int32_t k = b + sub; k < e; k += L) acc = fma(__ldg(&val[k]), __ldg(&x[__ldg(&col[k])]), acc);
-        }
-#pragma unroll
-        for (int o = L >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o, L);
-        if (i < n && sub == 0) y[i] = acc;
-    }
-}
-
-// Reduced-precision G / G^T (fp32 or bf16 values): fp32 arithmetic, x read
-// as XT (double or float), y written as YT.
-template <typename VT, typename XT, typename YT>
-__global__ void spmv_lowp_scalar(int32_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                 const VT* __restrict__ val, const XT* __restrict__ x, YT* __restrict__ y) {
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int32_t b = rowptr[i], e = rowptr[i + 1];
-        float acc = 0.0f;
-        for (int32_t k = b; k < e; ++k)
-            acc = fmaf(as_f32<VT>(__ldg(&val[k])), static_cast<float>(__ldg(&x[__ldg(&col[k])])), acc);
-        y[i] = static_cast<YT>(acc);
-    }
-}
-
-int spmv_group_for(int64_t n, int64_t nnz) {
-    static int forced = [] {
-        const char* s = std::getenv("AFSAI_SPMV_GROUP");
-        return s ? std::atoi(s) : 0;
-    }();
-    if (forced == 1 || forced == 2 || forced == 4 || forced == 8 || forced == 16 || forced == 32) return forced;
-    const double avg = n > 0 ? static_cast<double>(nnz) / n : 0.0;
-    if (avg <= 16.0) return 1;
-    if (avg <= 48.0) return 2;
-    return 4;
+template <int MODE, typename VT, typename XT, typename ACC, typename YT>
+__global__ void spmv_plain(int32_t n, int64_t nnz, const int32_t* __restrict__ rowptr,
+                           const int32_t* __restrict__ col, const VT* __restrict__ val, const XT* __restrict__ x,
+                           YT* __restrict__ y, int cap, int32_t* errflag) {
+    struct Epi {
+        YT* y;
+        __device__ void row(int64_t i, ACC a) { y[i] = static_cast<YT>(a); }
+    } epi{y};
+    tiled::spmv_rows<MODE, VT, XT, ACC>(n, nnz, rowptr, col, val, x, cap, errflag, epi);
 }
 
 int grid_for(int64_t work_items, int threads) {
@@ -267,6 +208,24 @@ int num_sms() {
         return v > 0 ? v : 1;
     }();
     return sms;
+}
+
+// Device flag raised by a bounded device-side wait that ran out.  It is a
+// module variable (no allocation); its address is looked up once per device.
+__device__ int32_t g_wait_error_flag;
+
+int32_t* error_flag() {
+    static std::mutex mu;
+    static int32_t* ptr[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_wait_error_flag) == cudaSuccess) ptr[dev] = static_cast<int32_t*>(p);
+    }
+    return ptr[dev];
 }
 
 afsai_status exclusive_scan_i32(const int32_t* in, int32_t* out, int32_t n, cudaStream_t st, int64_t* total_host) {
@@ -343,62 +302,182 @@ afsai_status build_transpose(const CsrDev& G, CsrDev* Gt, cudaStream_t st) {
     return AFSAI_OK;
 }
 
-afsai_status spmv_csr(const CsrDev& A, const double* x, double* y, cudaStream_t st) {
-    if (A.vtype != VAL_F64) return fail(AFSAI_EINVAL, "spmv_csr expects FP64 values");
-    const int threads = 256;
-    const int L = spmv_group_for(A.n, A.nnz);
-    const auto* v = static_cast<const double*>(A.val);
-    switch (L) {
-        case 1:
-            spmv_f64_scalar<<<grid_for(A.n, threads), threads, 0, st>>>(A.n, A.rowptr, A.col, v, x, y);
-            break;
-        case 2:
-            spmv_f64_group<2><<<grid_for(int64_t(A.n) * 2, threads), threads, 0, st>>>(A.n, A.rowptr, A.col, v, x, y);
-            break;
-        case 4:
-            spmv_f64_group<4><<<grid_for(int64_t(A.n) * 4, threads), threads, 0, st>>>(A.n, A.rowptr, A.col, v, x, y);
-            break;
-        case 8:
-            spmv_f64_group<8><<<grid_for(int64_t(A.n) * 8, threads), threads, 0, st>>>(A.n, A.rowptr, A.col, v, x, y);
-            break;
-        case 16:
-            spmv_f64_group<16><<<grid_for(int64_t(A.n) * 16, threads), threads, 0, st>>>(A.n, A.rowptr, A.col, v, x, y);
-            break;
-        default:
-            spmv_f64_group<32><<<grid_for(int64_t(A.n) * 32, threads), threads, 0, st>>>(A.n, A.rowptr, A.col, v, x, y);
-            break;
+TiledPlan plan_tiled(int32_t n, int64_t nnz, int32_t max_row, size_t val_size, const void* col, const void* val,
+                     int tpr) {
+    TiledPlan p;
+    if (n <= 0 || nnz <= 0) return p;
+    if ((reinterpret_cast<uintptr_t>(col) & 15u) || (reinterpret_cast<uintptr_t>(val) & 15u)) return p;
+    const double avg = static_cast<double>(nnz) / n;
+    p.tpr = (tpr == 1 || tpr == 2) ? tpr : (avg > 48.0 ? 2 : 1);
+    const size_t budget = 74u * 1024u;
+    for (int threads = 256; threads >= 64; threads /= 2) {
+        const int rows = threads / p.tpr;
+        const int64_t cap = static_cast<int64_t>(rows) * static_cast<int64_t>(std::ceil(avg * 1.25)) +
+                            std::max<int64_t>(max_row, 32) + 32;
+        const size_t bytes = 128 + (static_cast<size_t>(cap) * 4 + 127) / 128 * 128 +
+                             (static_cast<size_t>(cap) * val_size + 127) / 128 * 128;
+        p.threads = threads;
+        p.cap = static_cast<int>(cap);
+        p.smem = bytes;
+        if (bytes <= budget) break;
     }
+    if (p.smem > 200u * 1024u) return p;
+    const int per_sm = static_cast<int>(std::max<size_t>(
+        1, std::min<size_t>((227u * 1024u) / (p.smem + 1024u), static_cast<size_t>(2048 / p.threads))));
+    p.blocks = num_sms() * per_sm;
+    p.ok = true;
+    return p;
+}
+
+namespace {
+
+bool make_mode(int mode, const CsrDev& C, SpmvMode* m) {
+    m->mode = mode;
+    if (mode > 100) {
+        const TiledPlan pl = plan_tiled(C.n, C.nnz, C.max_row, val_bytes(C.vtype), C.col, C.val, mode - 100);
+        if (!pl.ok) return false;
+        m->threads = pl.threads;
+        m->blocks = pl.blocks;
+        m->smem = pl.smem;
+        m->cap = pl.cap;
+        return true;
+    }
+    m->threads = 256;
+    m->blocks = grid_for(static_cast<int64_t>(C.n) * mode, 256);
+    m->smem = 0;
+    m->cap = 0;
+    return true;
+}
+
+template <int MODE, typename VT, typename XT, typename ACC, typename YT>
+afsai_status launch_plain_mode(const SpmvMode& m, const CsrDev& C, const XT* x, YT* y, cudaStream_t st) {
+    auto k = spmv_plain<MODE, VT, XT, ACC, YT>;
+    if (m.smem > 0)
+        AFSAI_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(m.smem)));
+    k<<<m.blocks, m.threads, m.smem, st>>>(C.n, C.nnz, C.rowptr, C.col, static_cast<const VT*>(C.val), x, y, m.cap,
+                                           error_flag());
     AFSAI_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     return AFSAI_OK;
 }
 
+template <typename VT, typename XT, typename ACC, typename YT>
+afsai_status launch_plain(const SpmvMode& m, const CsrDev& C, const XT* x, YT* y, cudaStream_t st) {
+    switch (m.mode) {
+        case 1: return launch_plain_mode<1, VT, XT, ACC, YT>(m, C, x, y, st);
+        case 2: return launch_plain_mode<2, VT, XT, ACC, YT>(m, C, x, y, st);
+        case 4: return launch_plain_mode<4, VT, XT, ACC, YT>(m, C, x, y, st);
+        case 8: return launch_plain_mode<8, VT, XT, ACC, YT>(m, C, x, y, st);
+        case 101: return launch_plain_mode<101, VT, XT, ACC, YT>(m, C, x, y, st);
+        case 102: return launch_plain_mode<102, VT, XT, ACC, YT>(m, C, x, y, st);
+        default: return fail(AFSAI_EINVAL, "unknown SpMV mode");
+    }
+}
+
+// y = C x with the types of the role: A and FP64 G/G^T in FP64; reduced
+// precision G: x double -> y float (G), x float -> y double (G^T).
+afsai_status launch_role(int role, const SpmvMode& m, const CsrDev& C, const void* x, void* y, cudaStream_t st) {
+    if (C.vtype == VAL_F64)
+        return launch_plain<double, double, double, double>(m, C, static_cast<const double*>(x),
+                                                            static_cast<double*>(y), st);
+    if (C.vtype == VAL_F32) {
+        if (role == ROLE_G)
+            return launch_plain<float, double, float, float>(m, C, static_cast<const double*>(x),
+                                                             static_cast<float*>(y), st);
+        return launch_plain<float, float, float, double>(m, C, static_cast<const float*>(x), static_cast<double*>(y),
+                                                         st);
+    }
+    if (role == ROLE_G)
+        return launch_plain<__nv_bfloat16, double, float, float>(m, C, static_cast<const double*>(x),
+                                                                 static_cast<float*>(y), st);
+    return launch_plain<__nv_bfloat16, float, float, double>(m, C, static_cast<const float*>(x),
+                                                             static_cast<double*>(y), st);
+}
+
+struct ModeKey {
+    int dev, role, vtype;
+    int32_t n;
+    int64_t nnz;
+    bool operator<(const ModeKey& o) const {
+        return std::tie(dev, role, vtype, n, nnz) < std::tie(o.dev, o.role, o.vtype, o.n, o.nnz);
+    }
+};
+
+}  // namespace
+
+afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode* out) {
+    static std::mutex mu;
+    static std::map<ModeKey, int> cache;
+    static const int forced = [] {
+        const char* e = std::getenv("AFSAI_SPMV_MODE");
+        return e ? std::atoi(e) : 0;
+    }();
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const ModeKey key{dev, role, C.vtype, C.n, C.nnz};
+    if (forced && make_mode(forced, C, out)) return AFSAI_OK;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end() && make_mode(it->second, C, out)) return AFSAI_OK;
+    }
+    // time the candidates on this matrix
+    const double avg = C.n > 0 ? static_cast<double>(C.nnz) / C.n : 0.0;
+    std::vector<int> cand = {2, 4, 8, 101, 102};
+    if (avg <= 16.0) cand.insert(cand.begin(), 1);
+    DevBuf<double> xb, yb;
+    AFSAI_TRY(xb.alloc(static_cast<size_t>(C.n), st));
+    AFSAI_TRY(yb.alloc(static_cast<size_t>(C.n), st));
+    AFSAI_CUDA_TRY(cudaMemsetAsync(xb.p, 0, sizeof(double) * C.n, st));
+    cudaEvent_t e0, e1;
+    AFSAI_CUDA_TRY(cudaEventCreate(&e0));
+    AFSAI_CUDA_TRY(cudaEventCreate(&e1));
+    const int64_t launches_before = launches_so_far();
+    int best = -1;
+    float best_ms = 0.f;
+    for (int mode : cand) {
+        SpmvMode m;
+        if (!make_mode(mode, C, &m)) continue;
+        if (launch_role(role, m, C, xb.p, yb.p, st) != AFSAI_OK) continue;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; ++r) launch_role(role, m, C, xb.p, yb.p, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best < 0 || ms < best_ms) {
+            best = mode;
+            best_ms = ms;
+        }
+    }
+    set_launches(launches_before);  // tuning launches are not part of the solve
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    AFSAI_CUDA_TRY(cudaGetLastError());
+    if (best < 0) best = 4;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        cache[key] = best;
+    }
+    make_mode(best, C, out);
+    return AFSAI_OK;
+}
+
+afsai_status spmv_csr(const CsrDev& A, const double* x, double* y, cudaStream_t st) {
+    if (A.vtype != VAL_F64) return fail(AFSAI_EINVAL, "spmv_csr expects FP64 values");
+    SpmvMode m;
+    AFSAI_TRY(spmv_mode_for(ROLE_A, A, st, &m));
+    return launch_role(ROLE_A, m, A, x, y, st);
+}
+
 // t = G r ; z = G^T t.  For fp32/bf16 G the intermediate t is fp32 (t
 // points to n doubles of scratch, used as n floats).
 afsai_status apply_precond(const afsai_precond* M, const double* r, double* t, double* z, cudaStream_t st) {
-    const CsrDev& G = M->G;
-    const CsrDev& Gt = M->Gt;
-    if (G.vtype == VAL_F64) {
-        AFSAI_TRY(spmv_csr(G, r, t, st));
-        AFSAI_TRY(spmv_csr(Gt, t, z, st));
-        return AFSAI_OK;
-    }
-    const int threads = 256;
-    float* tf = reinterpret_cast<float*>(t);
-    if (G.vtype == VAL_F32) {
-        spmv_lowp_scalar<float, double, float><<<grid_for(G.n, threads), threads, 0, st>>>(
-            G.n, G.rowptr, G.col, static_cast<const float*>(G.val), r, tf);
-        spmv_lowp_scalar<float, float, double><<<grid_for(G.n, threads), threads, 0, st>>>(
-            Gt.n, Gt.rowptr, Gt.col, static_cast<const float*>(Gt.val), tf, z);
-    } else {
-        spmv_lowp_scalar<__nv_bfloat16, double, float><<<grid_for(G.n, threads), threads, 0, st>>>(
-            G.n, G.rowptr, G.col, static_cast<const __nv_bfloat16*>(G.val), r, tf);
-        spmv_lowp_scalar<__nv_bfloat16, float, double><<<grid_for(G.n, threads), threads, 0, st>>>(
-            Gt.n, Gt.rowptr, Gt.col, static_cast<const __nv_bfloat16*>(Gt.val), tf, z);
-    }
-    AFSAI_CUDA_TRY(cudaGetLastError());
-    count_launches(2);
-    return AFSAI_OK;
+    SpmvMode mg, mt;
+    AFSAI_TRY(spmv_mode_for(ROLE_G, M->G, st, &mg));
+    AFSAI_TRY(spmv_mode_for(ROLE_GT, M->Gt, st, &mt));
+    AFSAI_TRY(launch_role(ROLE_G, mg, M->G, r, t, st));
+    return launch_role(ROLE_GT, mt, M->Gt, t, z, st);
 }
 
 void free_csr(CsrDev* A, cudaStream_t st) {
