@@ -135,6 +135,26 @@ AFSAI_API afsai_status afsai_setup(const afsai_csr* A, const afsai_params* param
  * r, z: device vectors of n doubles (must not overlap).  Asynchronous. */
 AFSAI_API afsai_status afsai_apply(const afsai_precond* M, const double* r, double* z, void* stream);
 
+/* Same result as afsai_apply, for callers that cannot allocate device
+ * memory: code whose device memory is owned by another allocator (a
+ * framework's caching allocator that has reserved the free memory), and
+ * code on a latency-critical path where cudaMalloc / cudaFree may
+ * synchronise the device.  The paper has no counterpart; this is a service
+ * entry point of the library.
+ *   - Allocates nothing: the intermediate G r is kept in a fixed device
+ *     array of 2^20 doubles (8 MiB) that every GPU which loads the library
+ *     holds until the process exits.  n > 2^20 returns AFSAI_EINVAL.
+ *   - The first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress) with the device current; make this first call
+ *     before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents;
+ *     calls that overlap on the GPU (different streams, no ordering) race
+ *     on it and give wrong results.  Calls on one stream are safe.
+ *   - The SpMV engines are the ones already chosen for this matrix shape
+ *     by afsai_apply / pcg_solve, else a default; nothing is timed.
+ * r, z: device vectors of n doubles (must not overlap).  Asynchronous. */
+AFSAI_API afsai_status afsai_apply_static(const afsai_precond* M, const double* r, double* z, void* stream);
+
 /* y = A x (CSR SpMV, FP64).  A, x, y device pointers.  Asynchronous. */
 AFSAI_API afsai_status afsai_spmv(const afsai_csr* A, const double* x, double* y, void* stream);
 

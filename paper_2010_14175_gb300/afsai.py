@@ -30,7 +30,7 @@ OK, EINVAL, ENOMEM, ENOTSPD, ENOCONV, ECUDA, ETIMEOUT, EAGAIN, EBUSY, ENOTSUP = 
 EXPORTS = (
     "afsai_setup", "afsai_apply", "afsai_spmv", "pcg_solve", "afsai_solve_host", "afsai_get_info",
     "afsai_export_G", "afsai_export_Gt", "afsai_export_rows", "afsai_destroy", "afsai_last_error", "afsai_version",
-    "afsai_kernel_launches",
+    "afsai_kernel_launches", "afsai_apply_static",
 )
 
 
@@ -87,6 +87,8 @@ def load(build_if_missing: bool = True):
         lib.afsai_setup.restype = st
         lib.afsai_apply.argtypes = [P, P, P, P]
         lib.afsai_apply.restype = st
+        lib.afsai_apply_static.argtypes = [P, P, P, P]
+        lib.afsai_apply_static.restype = st
         lib.afsai_spmv.argtypes = [ctypes.POINTER(Csr), P, P, P]
         lib.afsai_spmv.restype = st
         lib.pcg_solve.argtypes = [ctypes.POINTER(Csr), P, P, P, ctypes.c_double, ctypes.c_int32, P,
@@ -218,6 +220,11 @@ def afsai_setup(A: DeviceCSR, prm: Params, stream=None) -> Precond:
 
 def afsai_apply(M: Precond, r, z, stream=None):
     _check(load().afsai_apply(M.handle, _ptr(r), _ptr(z), _stream(stream)))
+
+
+def afsai_apply_static(M: Precond, r, z, stream=None):
+    """z = G^T (G r) without any device allocation (n <= 2^20)."""
+    _check(load().afsai_apply_static(M.handle, _ptr(r), _ptr(z), _stream(stream)))
 
 
 def afsai_spmv(A: DeviceCSR, x, y, stream=None):

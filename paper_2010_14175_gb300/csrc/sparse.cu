@@ -405,7 +405,11 @@ struct ModeKey {
 
 }  // namespace
 
-afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode* out) {
+afsai_status spmv_launch_role(int role, const SpmvMode& m, const CsrDev& C, const void* x, void* y, cudaStream_t st) {
+    return launch_role(role, m, C, x, y, st);
+}
+
+afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode* out, bool allow_tuning) {
     static std::mutex mu;
     static std::map<ModeKey, int> cache;
     static const int forced = [] {
@@ -421,8 +425,12 @@ afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode*
         auto it = cache.find(key);
         if (it != cache.end() && make_mode(it->second, C, out)) return AFSAI_OK;
     }
-    // time the candidates on this matrix
     const double avg = C.n > 0 ? static_cast<double>(C.nnz) / C.n : 0.0;
+    if (!allow_tuning) {
+        make_mode(avg <= 16.0 ? 1 : 4, C, out);
+        return AFSAI_OK;
+    }
+    // time the candidates on this matrix
     std::vector<int> cand = {2, 4, 8, 101, 102};
     if (avg <= 16.0) cand.insert(cand.begin(), 1);
     DevBuf<double> xb, yb;

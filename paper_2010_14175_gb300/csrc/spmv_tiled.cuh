@@ -276,8 +276,13 @@ enum SpmvRole : int { ROLE_A = 0, ROLE_G = 1, ROLE_GT = 2 };
 
 // Engine for a matrix: timed once per (role, shape, value type) among the
 // candidate engines on the given stream, then cached.  Must not be called
-// during stream capture.
-afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode* out);
+// during stream capture.  With allow_tuning = false nothing is timed or
+// allocated: the cached engine is used if there is one, else a default
+// chosen from the average row length.
+afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode* out, bool allow_tuning = true);
+
+// y = C x with the engine `m` and the value/vector types of `role`.
+afsai_status spmv_launch_role(int role, const SpmvMode& m, const CsrDev& C, const void* x, void* y, cudaStream_t st);
 
 // Host-side launch plan of a tiled SpMV.
 struct TiledPlan {
