@@ -43,7 +43,39 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "aFSAI set-up+PCG s/solve to relres 1e-8 (FP64; mixed reported beside)"
-WORKLOAD = "elasticity_hex48_fp64"
+WORKLOAD_NAMES = {"elast48": "elasticity_hex48", "hetero256": "hetero_diffusion7_256", "poisson20": "poisson7_20"}
+# precision forms: storage/arithmetic of G and of the row Cholesky solves
+FORMS = {
+    "fp64": dict(g_prec=0, chol_prec=0, desc="FP64 G, FP64 Cholesky"),
+    "mixed": dict(g_prec=1, chol_prec=1, desc="FP32 G, FP32 Cholesky + one FP64 refinement step"),
+    "g32": dict(g_prec=1, chol_prec=0, desc="FP32 G, FP64 Cholesky"),
+    "bf16": dict(g_prec=2, chol_prec=1, desc="BF16 G, FP32 Cholesky + one FP64 refinement step"),
+}
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def source_digest(paths):
+    import hashlib
+
+    h = hashlib.sha256()
+    for rel in paths:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel_key, units):
+    """DRAM bytes per launch of `kernel_key` from the committed ncu record,
+    scaled to `units` rows; None if absent or the kernel source changed."""
+    try:
+        rec = json.load(open(TRAFFIC_FILE))[kernel_key]
+    except Exception:
+        return None, "no ncu record"
+    if rec.get("source_digest") != source_digest(rec["sources"]):
+        return None, "kernel changed since the ncu capture"
+    per_unit = rec["dram_bytes"] / rec["units"]
+    return per_unit * units, f"ncu {rec['capture']}: {rec['dram_bytes']:.4g} B over {rec['units']} rows, scaled"
+
 
 
 def parse():
@@ -55,7 +87,11 @@ def parse():
     ap.add_argument("--scale", type=int, default=None, help="grid size override (testing only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the other precision forms")
+    ap.add_argument("--workload", default="elast48", choices=["elast48", "hetero256", "poisson20"])
+    ap.add_argument("--form", default="fp64", choices=list(FORMS), help="precision form of the timed line")
+    ap.add_argument("--extra-forms", default=None,
+                    help="comma list of other forms reported beside (default: mixed; hetero256: g32,bf16,mixed)")
     return ap.parse_args()
 
 
@@ -153,16 +189,50 @@ def setup_flops(rowptr_G, steps, s, nnz_row_avg):
     return total
 
 
+def setup_touched_bytes(rowptr_G, steps, s, nnz_row_avg):
+    """Bytes the set-up touches without cache reuse: per row and step the
+    rows of A read by the gradient (|P_{k-1}| of them) and by the gather
+    (the s new ones), 12 B per entry plus 8 B of row pointers, plus the
+    written row of G (12 B per entry)."""
+    m_final = np.diff(rowptr_G).astype(np.float64)
+    total = float(np.sum(m_final)) * 12.0
+    kmax = int(steps.max()) if steps.size else 0
+    for k in range(1, kmax + 1):
+        act = steps >= k
+        mprev = np.minimum(1 + (k - 1) * s, m_final[act])
+        mk = np.minimum(1 + k * s, m_final[act])
+        total += float(np.sum((mprev + (mk - mprev)) * (12.0 * nnz_row_avg + 8.0)))
+    return total
+
+
+def pcg_iteration_bytes(A, sinfo, form):
+    """Algorithmic bytes of one PCG iteration: A (12 B/entry + row
+    pointers), G and G^T ((4 + w) B/entry + row pointers, w the G value
+    size) and ~140 B per row of vector traffic."""
+    w = {0: 8, 1: 4, 2: 2}[FORMS[form]["g_prec"]]
+    return 12 * A.nnz + 2 * (4 + w) * sinfo["nnz_G"] + 12 * A.n + 140 * A.n
+
+
+def _measured_hbm():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        return 6800.0  # fallback figure of the pool
+
+
+MEASURED_HBM_GBS = _measured_hbm()
+
+
 def spmv_bytes(n, nnz, val_bytes=8, x_bytes=8, y_bytes=8):
     """Compulsory bytes of y = A x: values, columns, row pointers, x once,
     y once."""
     return nnz * (val_bytes + 4) + 4 * (n + 1) + n * x_bytes + n * y_bytes
 
 
-def make_workload(scale):
+def make_workload(name, scale):
     from paper_2010_14175_gb300 import matgen as mg
 
-    A, b, xs, p = mg.workload("elast48", scale=scale)
+    A, b, xs, p = mg.workload(name, scale=scale)
     return A, b, p
 
 
@@ -189,7 +259,7 @@ def run_reference(args, rank, world):
         return
     import oracle
 
-    A, b, p = make_workload(args.scale)
+    A, b, p = make_workload(args.workload, args.scale)
     # iteration count of the oracle's own full solve (measured once)
     G = oracle.afsai_setup(A, p["kiter"], p["s"], p["eps"])
     _, iters, _, rt = oracle.pcg(A, G, b, rtol=1e-8, maxit=20000)
@@ -205,8 +275,9 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s/solve", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
-        "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "kiter": p["kiter"], "s": p["s"],
-                   "eps": p["eps"], "rtol": 1e-8, "oracle_iters": iters, "oracle_relres_true": rt},
+        "config": {"workload": WORKLOAD_NAMES[args.workload] + "_fp64", "n": A.n, "nnz": A.nnz,
+                   "kiter": p["kiter"], "s": p["s"], "eps": p["eps"], "rtol": 1e-8, "oracle_iters": iters,
+                   "oracle_relres_true": rt},
         "cpu_baseline": {"value": value, "unit": "s/solve", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "s/solve", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -226,22 +297,24 @@ def main():
     assert torch.cuda.is_available(), "bench needs a GPU"
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    lib = afsai.load()
-    A, b, p = make_workload(args.scale)
+    afsai.load()
+    A, b, p = make_workload(args.workload, args.scale)
     Ad = afsai.DeviceCSR.from_host(A, device=dev)
     bd = torch.from_numpy(b).to(dev)
     x = torch.zeros_like(bd)
     stream = torch.cuda.current_stream(dev)
-    prm = afsai.params(p["kiter"], p["s"], p["eps"])
-    prm_mixed = afsai.params(p["kiter"], p["s"], p["eps"], 0, 1, 1)
+
+    def prm_of(form):
+        f = FORMS[form]
+        return afsai.params(p["kiter"], p["s"], p["eps"], 0, f["g_prec"], f["chol_prec"])
 
     def one_solve(prm_):
         x.zero_()
         M = afsai.afsai_setup(Ad, prm_, stream)
         info = afsai.pcg_solve(Ad, M, bd, x, rtol=1e-8, maxit=20000, stream=stream)
-        sinfo = M.info()
-        return M, sinfo, info
+        return M, M.info(), info
 
+    prm = prm_of(args.form)
     for _ in range(args.warmup):
         M, sinfo, pinfo = one_solve(prm)
         M.close()
@@ -280,30 +353,46 @@ def main():
     rp, ci, va = M.export()
     psi, steps = M.rows()
     flops = setup_flops(rp, steps, p["s"], A.nnz / A.n)
-    fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12  # TFLOP/s: SMs x DFMA/clk x 2 x max clock
-    roof = {"kernel": "afsai_setup_kernel", "bound": "alu", "achieved": flops / (kern_ms * 1e-3) / 1e12,
-            "peak": fp64_peak, "unit": "TFLOP/s", "frac": None, "traffic": None,
-            "kernel_ms": kern_ms, "algorithmic_flops": flops,
-            "peak_source": "FP64: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived, not measured)"}
+    kkey = f"afsai_setup_kernel/{args.form}"
+    traffic, traffic_note = measured_traffic(kkey, A.n)
+    if FORMS[args.form]["chol_prec"] == 0:
+        fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12  # TFLOP/s: SMs x DFMA/clk x 2 x max clock
+        roof = {"kernel": kkey, "bound": "alu", "achieved": flops / (kern_ms * 1e-3) / 1e12, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": None, "traffic": traffic, "traffic_note": traffic_note,
+                "kernel_ms": kern_ms, "algorithmic_flops": flops,
+                "peak_source": "FP64 ALU: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived from unit counts)"}
+    else:
+        # reduced-precision factorisation: the set-up's roof is the bytes it
+        # must touch, against the measured HBM copy bandwidth
+        touched = setup_touched_bytes(rp, steps, p["s"], A.nnz / A.n)
+        roof = {"kernel": kkey, "bound": "hbm", "achieved": touched / (kern_ms * 1e-3) / 1e9,
+                "peak": MEASURED_HBM_GBS, "unit": "GB/s", "frac": None, "traffic": traffic,
+                "traffic_note": traffic_note, "kernel_ms": kern_ms, "algorithmic_bytes": touched,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     M.close()
 
-    mixed = None
+    extra = {}
     if not args.no_mixed:
-        for _ in range(2):
-            Mm, sm_, pm_ = one_solve(prm_mixed)
-            Mm.close()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            Mm, sm_, pm_ = one_solve(prm_mixed)
-            Mm.close()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        mixed = {"value": e0.elapsed_time(e1) / 1e3 / args.steps, "unit": "s/solve", "iters": pm_["iters"],
-                 "relres_true": pm_["relres_true"], "g_prec": "fp32", "chol_prec": "fp32+fp64 refinement",
-                 "setup_ms": sm_["setup_ms"], "solve_ms": pm_["solve_ms"]}
+        names = args.extra_forms.split(",") if args.extra_forms else (
+            ["g32", "bf16", "mixed"] if args.workload == "hetero256" else ["mixed"])
+        for form in [f for f in names if f and f != args.form]:
+            pf = prm_of(form)
+            for _ in range(2):
+                Mm, sm_, pm_ = one_solve(pf)
+                Mm.close()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                Mm, sm_, pm_ = one_solve(pf)
+                Mm.close()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            extra[form] = {"value": e0.elapsed_time(e1) / 1e3 / args.steps, "unit": "s/solve", "iters": pm_["iters"],
+                           "relres_true": pm_["relres_true"], "desc": FORMS[form]["desc"],
+                           "setup_ms": sm_["setup_ms"], "solve_ms": pm_["solve_ms"],
+                           "iters_vs_fp64": pm_["iters"] / max(1, int(np.median(iters)))}
 
     e2e = None
     if not args.no_e2e:
@@ -312,6 +401,7 @@ def main():
         bh = pin(b).numpy()
         xh = torch.zeros(A.n, dtype=torch.float64).pin_memory().numpy()
         afsai.afsai_solve_host(Ah, prm, bh, xh, rtol=1e-8, maxit=20000, stream=stream)
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             afsai.afsai_solve_host(Ah, prm, bh, xh, rtol=1e-8, maxit=20000, stream=stream)
@@ -326,16 +416,22 @@ def main():
         cpu = {"value": v, "unit": "s/solve", "cores": cores, "kind": "oracle", "sample": sample}
 
     if rank == 0:
+        n_it = int(np.median(iters))
         line = {
             "metric": METRIC, "value": value, "unit": "s/solve", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
-            "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "kiter": p["kiter"], "s": p["s"],
-                       "eps": p["eps"], "rtol": 1e-8, "l2": "inputs larger than L2 (A is %.0f MB)" % (A.nnz * 12e-6),
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.form == "fp64" else "f64+f32",
+            "data": "synthetic (seeded generator)",
+            "config": {"workload": WORKLOAD_NAMES[args.workload] + "_" + args.form, "n": A.n, "nnz": A.nnz,
+                       "kiter": p["kiter"], "s": p["s"], "eps": p["eps"], "rtol": 1e-8,
+                       "form": FORMS[args.form]["desc"],
+                       "l2": "inputs larger than L2 (A is %.0f MB)" % (A.nnz * 12e-6),
                        "parallelism": f"replicas x{world}"},
-            "setup_ms": float(np.median(setup_ms)), "solve_ms": float(np.median(solve_ms)),
-            "pcg_iters": int(np.median(iters)), "relres_true": pinfo["relres_true"], "nnz_G": sinfo["nnz_G"],
-            "gpu_launches": int(launches), "roofline": roof, "mixed": mixed, "e2e": e2e, "cpu_baseline": cpu,
+            "setup_ms": float(np.median(setup_ms)), "solve_ms": float(np.median(solve_ms)), "pcg_iters": n_it,
+            "relres_true": pinfo["relres_true"], "nnz_G": sinfo["nnz_G"],
+            "setup_rows_per_s": A.n / (float(np.median(setup_ms)) * 1e-3),
+            "solve_gbs": pcg_iteration_bytes(A, sinfo, args.form) * n_it / (float(np.median(solve_ms)) * 1e-3) / 1e9,
+            "gpu_launches": int(launches), "roofline": roof, "forms": extra, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

@@ -169,6 +169,36 @@ AFSAI_API afsai_status afsai_spmv(const afsai_csr* A, const double* x, double* y
 AFSAI_API afsai_status pcg_solve(const afsai_csr* A, const afsai_precond* M, const double* b, double* x, double rtol,
                        int32_t maxit, void* stream, pcg_info* info);
 
+/* Outcome of a batched solve (host struct). */
+typedef struct {
+    int32_t nsys;          /* systems in the batch */
+    int32_t converged;     /* systems that reached rtol */
+    int32_t max_iters;     /* largest PCG iteration count of the batch */
+    int32_t graph_launches;/* graph launches of the PCG loop */
+    int64_t total_rows;    /* sum of n */
+    int64_t nnz_G;         /* sum of the entries of the G factors */
+    double setup_ms;       /* device time of the packed set-up */
+    double solve_ms;       /* device time of the batched PCG */
+} afsai_batch_info;
+
+/* Solves nsys independent SPD systems A_k x_k = b_k with aFSAI-PCG in one
+ * batch (Section 2 set-up, Section 5.2 stopping rule): one fused set-up
+ * launch over the rows of all systems (packed block-diagonally, so each
+ * G_k equals the G of system k alone), then graph-captured PCG iterations
+ * that advance every unconverged system per launch; each system keeps its
+ * own alpha, beta and convergence test, and its result does not depend on
+ * the other systems of the batch.
+ *   A       host array of nsys CSR descriptors with DEVICE pointers.
+ *   params  one parameter set for all systems (host).
+ *   b, x    host arrays of nsys DEVICE pointers; x_k is the initial guess
+ *           on entry and the solution on exit.
+ *   info    host array of nsys pcg_info (may be NULL); binfo may be NULL.
+ * Synchronises `stream`.  Returns OK, ENOCONV (some system reached maxit),
+ * EINVAL, ENOTSPD, ENOTSUP, ENOMEM, ECUDA. */
+AFSAI_API afsai_status afsai_batch_solve(int32_t nsys, const afsai_csr* A, const afsai_params* params,
+                                         const double* const* b, double* const* x, double rtol, int32_t maxit,
+                                         void* stream, pcg_info* info, afsai_batch_info* binfo);
+
 /* End-to-end solve from HOST buffers: copies A and b to the device, builds
  * the preconditioner, runs PCG from x = 0 and copies x back (x_host: n
  * doubles).  Device memory is allocated and freed inside the call.

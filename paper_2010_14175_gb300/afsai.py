@@ -30,7 +30,7 @@ OK, EINVAL, ENOMEM, ENOTSPD, ENOCONV, ECUDA, ETIMEOUT, EAGAIN, EBUSY, ENOTSUP = 
 EXPORTS = (
     "afsai_setup", "afsai_apply", "afsai_spmv", "pcg_solve", "afsai_solve_host", "afsai_get_info",
     "afsai_export_G", "afsai_export_Gt", "afsai_export_rows", "afsai_destroy", "afsai_last_error", "afsai_version",
-    "afsai_kernel_launches", "afsai_apply_static",
+    "afsai_kernel_launches", "afsai_apply_static", "afsai_batch_solve",
 )
 
 
@@ -54,6 +54,12 @@ class Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("nnz_G", ctypes.c_int64), ("max_row", ctypes.c_int32),
                 ("g_prec", ctypes.c_int32), ("n_retry", ctypes.c_int32), ("setup_ms", ctypes.c_double),
                 ("kernel_ms", ctypes.c_double)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("nsys", ctypes.c_int32), ("converged", ctypes.c_int32), ("max_iters", ctypes.c_int32),
+                ("graph_launches", ctypes.c_int32), ("total_rows", ctypes.c_int64), ("nnz_G", ctypes.c_int64),
+                ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double)]
 
 
 class PcgInfo(ctypes.Structure):
@@ -110,6 +116,9 @@ def load(build_if_missing: bool = True):
         lib.afsai_last_error.restype = ctypes.c_char_p
         lib.afsai_version.argtypes = []
         lib.afsai_version.restype = ctypes.c_char_p
+        lib.afsai_batch_solve.argtypes = [ctypes.c_int32, P, ctypes.POINTER(Params), P, P, ctypes.c_double,
+                                          ctypes.c_int32, P, P, ctypes.POINTER(BatchInfo)]
+        lib.afsai_batch_solve.restype = st
         lib.afsai_kernel_launches.argtypes = []
         lib.afsai_kernel_launches.restype = ctypes.c_int64
         _lib = lib
@@ -242,6 +251,24 @@ def pcg_solve(A: DeviceCSR, M, b, x, rtol=1e-8, maxit=10000, stream=None, raise_
     out = _as_dict(inf)
     out["status"] = st
     return out
+
+
+def afsai_batch_solve(As, prm: Params, bs, xs, rtol=1e-8, maxit=10000, stream=None, raise_on_noconv=True):
+    """Batched aFSAI-PCG over independent systems (lists of DeviceCSR and
+    device vectors; xs hold the initial guesses and receive the solutions).
+    Returns (list of per-system info dicts, batch info dict)."""
+    n = len(As)
+    csrs = (Csr * n)(*[A.c() for A in As])
+    bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
+    xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    infos = (PcgInfo * n)()
+    binfo = BatchInfo()
+    st = load().afsai_batch_solve(n, ctypes.cast(csrs, ctypes.c_void_p), ctypes.byref(prm),
+                                  ctypes.cast(bp, ctypes.c_void_p), ctypes.cast(xp, ctypes.c_void_p), float(rtol),
+                                  int(maxit), _stream(stream), ctypes.cast(infos, ctypes.c_void_p), ctypes.byref(binfo))
+    if st != OK and not (st == ENOCONV and not raise_on_noconv):
+        _check(st)
+    return [_as_dict(i) for i in infos], dict(_as_dict(binfo), status=st)
 
 
 def afsai_solve_host(A, prm: Params, b: np.ndarray, x: np.ndarray, rtol=1e-8, maxit=10000, stream=None):

@@ -1,0 +1,715 @@
+// Batched aFSAI-PCG: many independent SPD systems of uneven size solved in
+// one set-up launch and one stream of graph-captured PCG iterations.
+//
+// Set-up.  The systems' CSRs are packed into one block-diagonal matrix and
+// the fused set-up kernel runs once over all rows.  Rows are independent
+// and a row only sees columns of its own block, so each system's G is
+// exactly the G of that system alone.  G and G^T stay packed; their column
+// indices are made local to each system afterwards.
+//
+// PCG.  Every system keeps its own vectors and scalars (rz, alpha, beta,
+// rr, convergence).  Work is cut into chunks of up to kChunk rows of one
+// system; a block handles one chunk at a time, one thread per row.  The SpMV
+// of a row is the plain sequential sum in CSR order, and every per-system
+// dot product is reduced over the system's own chunks in a fixed order
+// (fixed tree inside a chunk, chunks in order), so the result of a system
+// does not depend on which other systems share the batch.  A system that
+// has converged stops touching its vectors; the batch ends when the device
+// counter of active systems reaches zero, which the host polls between
+// launches of a graph of several iterations.
+//
+// The descriptor and chunk tables live in device memory with a fixed
+// capacity and their counts are read on the device, so a captured graph
+// stays valid when the tables are rewritten between launches (the solve
+// server relies on this).
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <string>
+#include <vector>
+
+#include "afsai_batch.cuh"
+
+namespace afsai {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Sum over the block of one value per thread (fixed tree); result in
+// thread 0.  blockDim.x == kChunk.
+__device__ __forceinline__ double chunk_sum(double v, double* sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (warp == 0) {
+        t = lane < (kChunk >> 5) ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(kFull, t, o);
+    }
+    __syncthreads();
+    return t;
+}
+
+// Records the chunk partial; returns true in the block that completes the
+// system's last chunk, which then holds the system total in `total`
+// (thread 0): the chunk partials of the system summed in chunk order.
+__device__ bool system_sum(double part, const BSys& sy, int32_t c, double* partials, unsigned* ticket,
+                           double* total) {
+    __shared__ bool last;
+    __shared__ double sh[32];
+    if (threadIdx.x == 0) {
+        partials[c] = part;
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == static_cast<unsigned>(sy.nchunks - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double acc = 0.0;
+    for (int32_t k = threadIdx.x; k < sy.nchunks; k += blockDim.x)
+        acc += reinterpret_cast<volatile double*>(partials)[sy.chunk0 + k];
+    const double t = chunk_sum(acc, sh);
+    if (threadIdx.x == 0) {
+        *total = t;
+        *ticket = 0u;
+    }
+    return true;
+}
+
+template <typename VT>
+__device__ __forceinline__ float vf(VT v) {
+    return static_cast<float>(v);
+}
+template <>
+__device__ __forceinline__ float vf<__nv_bfloat16>(__nv_bfloat16 v) {
+    return __bfloat162float(v);
+}
+
+// Row i of a CSR times x, sequential in CSR order (FP64).
+__device__ __forceinline__ double row_f64(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                          const double* __restrict__ val, const double* __restrict__ x, int32_t i) {
+    double acc = 0.0;
+    const int32_t e = rp[i + 1];
+    for (int32_t k = rp[i]; k < e; ++k) acc = fma(__ldg(&val[k]), __ldg(&x[__ldg(&col[k])]), acc);
+    return acc;
+}
+
+// ---- init: r = b - A x, bb, rr ------------------------------------------
+__global__ void kb_init(const BSys* __restrict__ sys, BScal* sc, const BChunk* __restrict__ chunks,
+                        const int32_t* nchunks, double* partials, double* partials2) {
+    __shared__ double sh[32];
+    for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
+        const BChunk ch = chunks[c];
+        const BSys& sy = sys[ch.sys];
+        BScal* s = &sc[ch.sys];
+        const int32_t i = ch.row0 + threadIdx.x;
+        double rr = 0.0, bb = 0.0;
+        if (i < ch.row1) {
+            const double ri = sy.b[i] - row_f64(sy.Arp, sy.Acol, sy.Aval, sy.x, i);
+            sy.r[i] = ri;
+            rr = ri * ri;
+            bb = sy.b[i] * sy.b[i];
+        }
+        const double trr = chunk_sum(rr, sh);
+        const double tbb = chunk_sum(bb, sh);
+        if (threadIdx.x == 0) partials2[c] = tbb;
+        double tot;
+        if (system_sum(trr, sy, c, partials, &s->ticket[0], &tot) && threadIdx.x == 0) {
+            double b2 = 0.0;
+            for (int32_t k = 0; k < sy.nchunks; ++k) b2 += reinterpret_cast<volatile double*>(partials2)[sy.chunk0 + k];
+            s->rr = tot;
+            s->bb = b2;
+            s->tol2 = s->rtol * s->rtol * b2;
+            s->iters = 0;
+            if (tot <= s->tol2) {
+                s->done = 1;
+                atomicSub(s->active, 1);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---- t = G r --------------------------------------------------------------
+template <typename VT, typename TT>
+__device__ __forceinline__ TT row_G(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                    const VT* __restrict__ val, const double* __restrict__ x, int32_t i) {
+    if constexpr (sizeof(TT) == 8) {
+        double acc = 0.0;
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k)
+            acc = fma(static_cast<double>(__ldg(&val[k])), __ldg(&x[__ldg(&col[k])]), acc);
+        return acc;
+    } else {
+        float acc = 0.0f;
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k)
+            acc = fmaf(vf<VT>(val[k]), static_cast<float>(__ldg(&x[__ldg(&col[k])])), acc);
+        return acc;
+    }
+}
+
+template <typename VT, typename TT>
+__device__ __forceinline__ TT row_Gt(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                     const VT* __restrict__ val, const TT* __restrict__ t, int32_t i) {
+    TT acc = TT(0);
+    for (int32_t k = rp[i]; k < rp[i + 1]; ++k) {
+        if constexpr (sizeof(TT) == 8)
+            acc = fma(static_cast<double>(__ldg(&val[k])), __ldg(&t[__ldg(&col[k])]), acc);
+        else
+            acc = fmaf(vf<VT>(val[k]), __ldg(&t[__ldg(&col[k])]), acc);
+    }
+    return acc;
+}
+
+template <typename VT, typename TT>
+__global__ void kb_G(const BSys* __restrict__ sys, const BScal* sc, const BChunk* __restrict__ chunks,
+                     const int32_t* nchunks, int init) {
+    for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
+        const BChunk ch = chunks[c];
+        if (!init && sc[ch.sys].done) continue;
+        const BSys& sy = sys[ch.sys];
+        const int32_t i = ch.row0 + threadIdx.x;
+        if (i < ch.row1)
+            static_cast<TT*>(sy.t)[i] = row_G<VT, TT>(sy.Grp, sy.Gcol, static_cast<const VT*>(sy.Gval), sy.r, i);
+    }
+}
+
+// ---- z = G^T t, rz' = r.z, beta -------------------------------------------
+template <typename VT, typename TT>
+__global__ void kb_Gt_dot(const BSys* __restrict__ sys, BScal* sc, const BChunk* __restrict__ chunks,
+                          const int32_t* nchunks, double* partials, int init) {
+    __shared__ double sh[32];
+    for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
+        const BChunk ch = chunks[c];
+        BScal* s = &sc[ch.sys];
+        if (!init && s->done) continue;
+        const BSys& sy = sys[ch.sys];
+        const int32_t i = ch.row0 + threadIdx.x;
+        double part = 0.0;
+        if (i < ch.row1) {
+            const double zi = static_cast<double>(
+                row_Gt<VT, TT>(sy.Trp, sy.Tcol, static_cast<const VT*>(sy.Tval), static_cast<const TT*>(sy.t), i));
+            sy.z[i] = zi;
+            part = sy.r[i] * zi;
+        }
+        const double tp = chunk_sum(part, sh);
+        double tot;
+        if (system_sum(tp, sy, c, partials, &s->ticket[1], &tot) && threadIdx.x == 0) {
+            if (init) {
+                s->rz = tot;
+            } else {
+                s->beta = tot / s->rz;
+                s->rz = tot;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---- p = z (init) ---------------------------------------------------------
+__global__ void kb_init_p(const BSys* __restrict__ sys, const BChunk* __restrict__ chunks, const int32_t* nchunks) {
+    for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
+        const BChunk ch = chunks[c];
+        const BSys& sy = sys[ch.sys];
+        const int32_t i = ch.row0 + threadIdx.x;
+        if (i < ch.row1) sy.p[i] = sy.z[i];
+    }
+}
+
+// ---- q = A p, pq, alpha ---------------------------------------------------
+__global__ void kb_A_dot(const BSys* __restrict__ sys, BScal* sc, const BChunk* __restrict__ chunks,
+                         const int32_t* nchunks, double* partials) {
+    __shared__ double sh[32];
+    for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
+        const BChunk ch = chunks[c];
+        BScal* s = &sc[ch.sys];
+        if (s->done) continue;
+        const BSys& sy = sys[ch.sys];
+        const int32_t i = ch.row0 + threadIdx.x;
+        double part = 0.0;
+        if (i < ch.row1) {
+            const double qi = row_f64(sy.Arp, sy.Acol, sy.Aval, sy.p, i);
+            sy.q[i] = qi;
+            part = sy.p[i] * qi;
+        }
+        const double tp = chunk_sum(part, sh);
+        double tot;
+        if (system_sum(tp, sy, c, partials, &s->ticket[2], &tot) && threadIdx.x == 0) s->alpha = s->rz / tot;
+        __syncthreads();
+    }
+}
+
+// ---- x += alpha p, r -= alpha q, rr, convergence --------------------------
+__global__ void kb_update_xr(const BSys* __restrict__ sys, BScal* sc, const BChunk* __restrict__ chunks,
+                             const int32_t* nchunks, double* partials) {
+    __shared__ double sh[32];
+    for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
+        const BChunk ch = chunks[c];
+        BScal* s = &sc[ch.sys];
+        if (s->done) continue;
+        const BSys& sy = sys[ch.sys];
+        const double alpha = s->alpha;
+        const int32_t i = ch.row0 + threadIdx.x;
+        double part = 0.0;
+        if (i < ch.row1) {
+            sy.x[i] = fma(alpha, sy.p[i], sy.x[i]);
+            const double ri = fma(-alpha, sy.q[i], sy.r[i]);
+            sy.r[i] = ri;
+            part = ri * ri;
+        }
+        const double tp = chunk_sum(part, sh);
+        double tot;
+        if (system_sum(tp, sy, c, partials, &s->ticket[3], &tot) && threadIdx.x == 0) {
+            s->rr = tot;
+            s->iters += 1;
+            if (tot <= s->tol2) {
+                s->done = 1;
+                atomicSub(s->active, 1);
+            } else if (s->iters >= s->maxit) {
+                s->done = 2;
+                atomicSub(s->active, 1);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---- p = z + beta p --------------------------------------------------------
+__global__ void kb_update_p(const BSys* __restrict__ sys, const BScal* sc, const BChunk* __restrict__ chunks,
+                            const int32_t* nchunks) {
+    for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
+        const BChunk ch = chunks[c];
+        const BScal* s = &sc[ch.sys];
+        if (s->done) continue;
+        const BSys& sy = sys[ch.sys];
+        const int32_t i = ch.row0 + threadIdx.x;
+        if (i < ch.row1) sy.p[i] = fma(s->beta, sy.p[i], sy.z[i]);
+    }
+}
+
+// ---- true residual ||b - A x||^2 per system -------------------------------
+__global__ void kb_true_residual(const BSys* __restrict__ sys, BScal* sc, const BChunk* __restrict__ chunks,
+                                 const int32_t* nchunks, double* partials) {
+    __shared__ double sh[32];
+    for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
+        const BChunk ch = chunks[c];
+        BScal* s = &sc[ch.sys];
+        const BSys& sy = sys[ch.sys];
+        const int32_t i = ch.row0 + threadIdx.x;
+        double part = 0.0;
+        if (i < ch.row1) {
+            const double d = sy.b[i] - row_f64(sy.Arp, sy.Acol, sy.Aval, sy.x, i);
+            part = d * d;
+        }
+        const double tp = chunk_sum(part, sh);
+        double tot;
+        if (system_sum(tp, sy, c, partials, &s->ticket[4], &tot) && threadIdx.x == 0) s->true_rr = tot;
+        __syncthreads();
+    }
+}
+
+// ---- packing of many CSRs into one block-diagonal CSR ---------------------
+__global__ void kb_pack(int32_t nsys, const PackSrc* __restrict__ src, const int64_t* __restrict__ row_off,
+                        int64_t nrows, int32_t* __restrict__ rowptr, int32_t* __restrict__ col,
+                        double* __restrict__ val, int32_t* __restrict__ bad) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t g = gw; g < nrows; g += nw) {
+        int lo = 0, hi = nsys - 1;  // system of row g: last s with row_off[s] <= g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (row_off[mid] <= g)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const PackSrc& s = src[lo];
+        const int32_t i = static_cast<int32_t>(g - row_off[lo]);
+        const int32_t b = s.rowptr[i], e = s.rowptr[i + 1];
+        if (b < 0 || e < b || e > s.nnz) {
+            if (lane == 0) atomicOr(bad, 1);
+            if (lane == 0) rowptr[g] = static_cast<int32_t>(s.nnz_off);
+            continue;
+        }
+        if (lane == 0) rowptr[g] = static_cast<int32_t>(s.nnz_off + b);
+        for (int32_t k = b + lane; k < e; k += 32) {
+            const int32_t c = s.col[k];
+            col[s.nnz_off + k] = (c >= 0 && c < s.n) ? c + static_cast<int32_t>(row_off[lo]) : -1;
+            val[s.nnz_off + k] = s.val[k];
+        }
+    }
+}
+
+// columns of the packed G / G^T back to system-local indices
+__global__ void kb_localize(int32_t nsys, const int64_t* __restrict__ row_off, const int32_t* __restrict__ rowptr,
+                            int64_t nrows, int32_t* __restrict__ col) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t g = gw; g < nrows; g += nw) {
+        int lo = 0, hi = nsys - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (row_off[mid] <= g)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const int32_t off = static_cast<int32_t>(row_off[lo]);
+        for (int32_t k = rowptr[g] + lane; k < rowptr[g + 1]; k += 32) col[k] -= off;
+    }
+}
+
+int grid_blocks() { return num_sms() * (2048 / kChunk); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// BatchEngine
+// ---------------------------------------------------------------------------
+afsai_status BatchEngine::reserve(int32_t max_sys, int64_t max_chunks, cudaStream_t st) {
+    if (max_sys <= cap_sys && max_chunks <= cap_chunks) return AFSAI_OK;
+    release(st);
+    cap_sys = std::max<int32_t>(max_sys, 1);
+    cap_chunks = std::max<int64_t>(max_chunks, 1);
+    AFSAI_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_sys), sizeof(BSys) * cap_sys, st));
+    AFSAI_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_sc), sizeof(BScal) * cap_sys, st));
+    AFSAI_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_chunks), sizeof(BChunk) * cap_chunks, st));
+    AFSAI_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_partials), sizeof(double) * cap_chunks, st));
+    AFSAI_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_partials2), sizeof(double) * cap_chunks, st));
+    AFSAI_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_counts), sizeof(int32_t) * 4, st));
+    AFSAI_CUDA_TRY(cudaMemsetAsync(d_counts, 0, sizeof(int32_t) * 4, st));
+    AFSAI_CUDA_TRY(cudaMallocHost(reinterpret_cast<void**>(&h_counts), sizeof(int32_t) * 4));
+    return AFSAI_OK;
+}
+
+void BatchEngine::release(cudaStream_t st) {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    if (d_sys) cudaFreeAsync(d_sys, st);
+    if (d_sc) cudaFreeAsync(d_sc, st);
+    if (d_chunks) cudaFreeAsync(d_chunks, st);
+    if (d_partials) cudaFreeAsync(d_partials, st);
+    if (d_partials2) cudaFreeAsync(d_partials2, st);
+    if (d_counts) cudaFreeAsync(d_counts, st);
+    if (h_counts) cudaFreeHost(h_counts);
+    d_sys = nullptr;
+    d_sc = nullptr;
+    d_chunks = nullptr;
+    d_partials = nullptr;
+    d_partials2 = nullptr;
+    d_counts = nullptr;
+    h_counts = nullptr;
+    cap_sys = 0;
+    cap_chunks = 0;
+}
+
+// Host tables -> device.  Systems get consecutive chunk ranges.
+afsai_status BatchEngine::upload(const std::vector<BSys>& sys_in, const std::vector<BScal>& sc_in, cudaStream_t st) {
+    std::vector<BSys> sys = sys_in;
+    chunks_h.clear();
+    for (size_t s = 0; s < sys.size(); ++s) {
+        sys[s].chunk0 = static_cast<int32_t>(chunks_h.size());
+        const int32_t nc = (sys[s].n + kChunk - 1) / kChunk;
+        sys[s].nchunks = nc;
+        for (int32_t c = 0; c < nc; ++c)
+            chunks_h.push_back(BChunk{static_cast<int32_t>(s), c * kChunk, std::min(sys[s].n, (c + 1) * kChunk)});
+    }
+    AFSAI_TRY(reserve(static_cast<int32_t>(sys.size()), static_cast<int64_t>(chunks_h.size()), st));
+    std::vector<BScal> sc = sc_in;
+    for (auto& v : sc) v.active = d_counts;
+    if (!sys.empty()) {
+        AFSAI_CUDA_TRY(cudaMemcpyAsync(d_sys, sys.data(), sizeof(BSys) * sys.size(), cudaMemcpyHostToDevice, st));
+        AFSAI_CUDA_TRY(cudaMemcpyAsync(d_sc, sc.data(), sizeof(BScal) * sc.size(), cudaMemcpyHostToDevice, st));
+        AFSAI_CUDA_TRY(cudaMemcpyAsync(d_chunks, chunks_h.data(), sizeof(BChunk) * chunks_h.size(),
+                                       cudaMemcpyHostToDevice, st));
+    }
+    int32_t counts[4] = {static_cast<int32_t>(sys.size()), static_cast<int32_t>(chunks_h.size()), 0, 0};
+    AFSAI_CUDA_TRY(cudaMemcpyAsync(d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice, st));
+    // the host array is pageable: wait for the copies before it goes away
+    AFSAI_CUDA_TRY(cudaStreamSynchronize(st));
+    return AFSAI_OK;
+}
+
+template <typename VT, typename TT>
+afsai_status launch_precond(BatchEngine& E, int init, cudaStream_t st) {
+    const int gb = grid_blocks();
+    kb_G<VT, TT><<<gb, kChunk, 0, st>>>(E.d_sys, E.d_sc, E.d_chunks, E.d_counts + 1, init);
+    kb_Gt_dot<VT, TT><<<gb, kChunk, 0, st>>>(E.d_sys, E.d_sc, E.d_chunks, E.d_counts + 1, E.d_partials, init);
+    AFSAI_CUDA_TRY(cudaGetLastError());
+    count_launches(2);
+    return AFSAI_OK;
+}
+
+afsai_status BatchEngine::precond(int init, cudaStream_t st) {
+    if (vtype == VAL_F64) return launch_precond<double, double>(*this, init, st);
+    if (vtype == VAL_F32) return launch_precond<float, float>(*this, init, st);
+    return launch_precond<__nv_bfloat16, float>(*this, init, st);
+}
+
+afsai_status BatchEngine::start(cudaStream_t st) {
+    const int gb = grid_blocks();
+    kb_init<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, d_counts + 1, d_partials, d_partials2);
+    AFSAI_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    AFSAI_TRY(precond(1, st));
+    kb_init_p<<<gb, kChunk, 0, st>>>(d_sys, d_chunks, d_counts + 1);
+    AFSAI_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return AFSAI_OK;
+}
+
+afsai_status BatchEngine::iteration(cudaStream_t st) {
+    const int gb = grid_blocks();
+    kb_A_dot<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, d_counts + 1, d_partials);
+    kb_update_xr<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, d_counts + 1, d_partials);
+    AFSAI_CUDA_TRY(cudaGetLastError());
+    count_launches(2);
+    AFSAI_TRY(precond(0, st));
+    kb_update_p<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, d_counts + 1);
+    AFSAI_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return AFSAI_OK;
+}
+
+afsai_status BatchEngine::capture(int iters_per_graph, cudaStream_t st) {
+    if (exec) {
+        cudaGraphExecDestroy(exec);
+        exec = nullptr;
+    }
+    graph_iters = iters_per_graph;
+    cudaGraph_t graph = nullptr;
+    AFSAI_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const int64_t before = launches_so_far();
+    afsai_status cap = AFSAI_OK;
+    for (int k = 0; k < iters_per_graph && cap == AFSAI_OK; ++k) cap = iteration(st);
+    const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    per_graph = launches_so_far() - before;
+    set_launches(before);
+    if (cap != AFSAI_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return cap;
+    }
+    AFSAI_CUDA_TRY(ce);
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    AFSAI_CUDA_TRY(ie);
+    return AFSAI_OK;
+}
+
+afsai_status BatchEngine::launch_graph(cudaStream_t st) {
+    AFSAI_CUDA_TRY(cudaGraphLaunch(exec, st));
+    count_launches(per_graph);
+    return AFSAI_OK;
+}
+
+afsai_status BatchEngine::read_active(cudaStream_t st, int32_t* active) {
+    AFSAI_CUDA_TRY(cudaMemcpyAsync(h_counts, d_counts, sizeof(int32_t) * 4, cudaMemcpyDeviceToHost, st));
+    AFSAI_CUDA_TRY(cudaStreamSynchronize(st));
+    *active = h_counts[0];
+    return AFSAI_OK;
+}
+
+afsai_status BatchEngine::finish(cudaStream_t st) {
+    kb_true_residual<<<grid_blocks(), kChunk, 0, st>>>(d_sys, d_sc, d_chunks, d_counts + 1, d_partials);
+    AFSAI_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return AFSAI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Packed set-up of many systems
+// ---------------------------------------------------------------------------
+afsai_status batch_setup(int32_t nsys, const afsai_csr* A, const afsai_params* p, cudaStream_t st,
+                         afsai_precond** out, std::vector<int64_t>* row_off_h) {
+    row_off_h->assign(nsys + 1, 0);
+    std::vector<PackSrc> src(nsys);
+    int64_t nnz_total = 0;
+    for (int32_t s = 0; s < nsys; ++s) {
+        if (!A[s].rowptr || !A[s].col || !A[s].val || A[s].n <= 0 || A[s].nnz < A[s].n)
+            return fail(AFSAI_EINVAL, "system " + std::to_string(s) + ": invalid CSR descriptor");
+        src[s] = PackSrc{A[s].n, A[s].nnz, nnz_total, A[s].rowptr, A[s].col, A[s].val};
+        (*row_off_h)[s + 1] = (*row_off_h)[s] + A[s].n;
+        nnz_total += A[s].nnz;
+    }
+    const int64_t nrows = (*row_off_h)[nsys];
+    if (nrows >= INT32_MAX || nnz_total >= INT32_MAX) return fail(AFSAI_ENOTSUP, "batch larger than 2^31 rows/entries");
+    DevBuf<PackSrc> dsrc;
+    DevBuf<int64_t> droff;
+    DevBuf<int32_t> bad, prp, pcol;
+    DevBuf<double> pval;
+    AFSAI_TRY(dsrc.alloc(nsys, st));
+    AFSAI_TRY(droff.alloc(nsys + 1, st));
+    AFSAI_TRY(bad.alloc(1, st));
+    AFSAI_TRY(prp.alloc(nrows + 1, st));
+    AFSAI_TRY(pcol.alloc(nnz_total, st));
+    AFSAI_TRY(pval.alloc(nnz_total, st));
+    AFSAI_CUDA_TRY(cudaMemcpyAsync(dsrc.p, src.data(), sizeof(PackSrc) * nsys, cudaMemcpyHostToDevice, st));
+    AFSAI_CUDA_TRY(cudaMemcpyAsync(droff.p, row_off_h->data(), sizeof(int64_t) * (nsys + 1), cudaMemcpyHostToDevice, st));
+    AFSAI_CUDA_TRY(cudaMemsetAsync(bad.p, 0, sizeof(int32_t), st));
+    const int32_t tot32 = static_cast<int32_t>(nnz_total);
+    AFSAI_CUDA_TRY(cudaMemcpyAsync(prp.p + nrows, &tot32, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    const int blocks = std::max(1, std::min(ceil_div(nrows * 32, 256), num_sms() * 16));
+    kb_pack<<<blocks, 256, 0, st>>>(nsys, dsrc.p, droff.p, nrows, prp.p, pcol.p, pval.p, bad.p);
+    AFSAI_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    int32_t hbad = 0;
+    AFSAI_CUDA_TRY(cudaMemcpyAsync(&hbad, bad.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    AFSAI_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hbad) return fail(AFSAI_EINVAL, "a system has malformed row pointers");
+    afsai_csr packed{static_cast<int32_t>(nrows), nnz_total, prp.p, pcol.p, pval.p};
+    afsai_precond* M = nullptr;
+    AFSAI_TRY(afsai_setup(&packed, p, st, &M));
+    kb_localize<<<blocks, 256, 0, st>>>(nsys, droff.p, M->G.rowptr, nrows, M->G.col);
+    kb_localize<<<blocks, 256, 0, st>>>(nsys, droff.p, M->Gt.rowptr, nrows, M->Gt.col);
+    AFSAI_CUDA_TRY(cudaGetLastError());
+    count_launches(2);
+    AFSAI_CUDA_TRY(cudaStreamSynchronize(st));
+    *out = M;
+    return AFSAI_OK;
+}
+
+}  // namespace afsai
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+using namespace afsai;
+
+namespace {
+
+afsai_status batch_solve_impl(int32_t nsys, const afsai_csr* A, const afsai_params* params, const double* const* b,
+                              double* const* x, double rtol, int32_t maxit, cudaStream_t st, pcg_info* info,
+                              afsai_batch_info* binfo) {
+    cudaEvent_t e0, e1, e2;
+    AFSAI_CUDA_TRY(cudaEventCreate(&e0));
+    AFSAI_CUDA_TRY(cudaEventCreate(&e1));
+    AFSAI_CUDA_TRY(cudaEventCreate(&e2));
+    AFSAI_CUDA_TRY(cudaEventRecord(e0, st));
+    afsai_precond* M = nullptr;
+    std::vector<int64_t> row_off;
+    AFSAI_TRY(batch_setup(nsys, A, params, st, &M, &row_off));
+    AFSAI_CUDA_TRY(cudaEventRecord(e1, st));
+    const int64_t ntot = row_off[nsys];
+    DevBuf<double> vec;
+    afsai_status s = vec.alloc(static_cast<size_t>(ntot) * 5, st);
+    BatchEngine E;
+    if (s == AFSAI_OK) {
+        std::vector<BSys> sys(nsys);
+        std::vector<BScal> sc(nsys);
+        for (int32_t k = 0; k < nsys; ++k) {
+            BSys& y = sys[k];
+            const int64_t o = row_off[k];
+            y.n = A[k].n;
+            y.Arp = A[k].rowptr;
+            y.Acol = A[k].col;
+            y.Aval = A[k].val;
+            y.Grp = M->G.rowptr + o;
+            y.Gcol = M->G.col;
+            y.Gval = M->G.val;
+            y.Trp = M->Gt.rowptr + o;
+            y.Tcol = M->Gt.col;
+            y.Tval = M->Gt.val;
+            y.b = b[k];
+            y.x = x[k];
+            y.r = vec.p + o;
+            y.p = vec.p + ntot + o;
+            y.q = vec.p + 2 * ntot + o;
+            y.z = vec.p + 3 * ntot + o;
+            y.t = vec.p + 4 * ntot + o;
+            BScal& c = sc[k];
+            c = BScal{};
+            c.rtol = rtol;
+            c.maxit = maxit;
+        }
+        E.vtype = M->G.vtype;
+        s = E.upload(sys, sc, st);
+        if (s == AFSAI_OK) s = E.start(st);
+        const int K = 8;
+        if (s == AFSAI_OK) s = E.capture(K, st);
+        int32_t active = nsys;
+        int64_t launches = 0;
+        const int64_t max_launches = maxit > 0 ? (static_cast<int64_t>(maxit) + K - 1) / K + 1 : 0;
+        if (s == AFSAI_OK) s = E.read_active(st, &active);
+        while (s == AFSAI_OK && active > 0 && launches < max_launches) {
+            s = E.launch_graph(st);
+            ++launches;
+            if (s == AFSAI_OK) s = E.read_active(st, &active);
+        }
+        if (s == AFSAI_OK) s = E.finish(st);
+        if (s == AFSAI_OK && cudaEventRecord(e2, st) != cudaSuccess) s = fail(AFSAI_ECUDA, "cudaEventRecord");
+        std::vector<BScal> out(nsys);
+        if (s == AFSAI_OK) {
+            if (cudaMemcpyAsync(out.data(), E.d_sc, sizeof(BScal) * nsys, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                s = fail(AFSAI_ECUDA, "reading batch results");
+        }
+        if (s == AFSAI_OK) {
+            float ms_setup = 0.f, ms_solve = 0.f;
+            cudaEventElapsedTime(&ms_setup, e0, e1);
+            cudaEventElapsedTime(&ms_solve, e1, e2);
+            int32_t maxi = 0, nconv = 0;
+            for (int32_t k = 0; k < nsys; ++k) {
+                const double bn = std::sqrt(out[k].bb);
+                if (info) {
+                    info[k].iters = out[k].iters;
+                    info[k].converged = out[k].done == 1 ? 1 : 0;
+                    info[k].relres_rec = bn > 0 ? std::sqrt(out[k].rr) / bn : 0.0;
+                    info[k].relres_true = bn > 0 ? std::sqrt(out[k].true_rr) / bn : 0.0;
+                    info[k].solve_ms = ms_solve;
+                }
+                maxi = std::max(maxi, out[k].iters);
+                nconv += out[k].done == 1 ? 1 : 0;
+            }
+            if (binfo) {
+                binfo->nsys = nsys;
+                binfo->total_rows = ntot;
+                binfo->nnz_G = M->info.nnz_G;
+                binfo->setup_ms = ms_setup;
+                binfo->solve_ms = ms_solve;
+                binfo->graph_launches = static_cast<int32_t>(launches);
+                binfo->max_iters = maxi;
+                binfo->converged = nconv;
+            }
+            if (nconv < nsys) s = fail(AFSAI_ENOCONV, std::to_string(nsys - nconv) + " system(s) reached maxit");
+        }
+    }
+    E.release(st);
+    vec.release();
+    cudaStreamSynchronize(st);
+    afsai_destroy(M);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    return s;
+}
+
+}  // namespace
+
+extern "C" afsai_status afsai_batch_solve(int32_t nsys, const afsai_csr* A, const afsai_params* params,
+                                          const double* const* b, double* const* x, double rtol, int32_t maxit,
+                                          void* stream, pcg_info* info, afsai_batch_info* binfo) {
+    if (nsys <= 0 || !A || !params || !b || !x) return fail(AFSAI_EINVAL, "invalid batch arguments");
+    if (maxit < 0 || !(rtol >= 0.0)) return fail(AFSAI_EINVAL, "invalid rtol or maxit");
+    for (int32_t k = 0; k < nsys; ++k)
+        if (!b[k] || !x[k]) return fail(AFSAI_EINVAL, "NULL vector of system " + std::to_string(k));
+    // the packed set-up uses a private non-blocking stream (graph capture
+    // needs one), ordered after and joined back to the caller's stream
+    cudaStream_t user = static_cast<cudaStream_t>(stream);
+    cudaStream_t st;
+    AFSAI_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    cudaEvent_t join;
+    AFSAI_CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+    cudaEventRecord(join, user);
+    cudaStreamWaitEvent(st, join, 0);
+    const afsai_status s = batch_solve_impl(nsys, A, params, b, x, rtol, maxit, st, info, binfo);
+    cudaEventRecord(join, st);
+    cudaStreamWaitEvent(user, join, 0);
+    cudaStreamSynchronize(st);
+    cudaEventDestroy(join);
+    cudaStreamDestroy(st);
+    return s;
+}

@@ -424,3 +424,35 @@ def workload(name: str, scale: int | None = None):
     _, kiter, s, eps = WORKLOADS[name]
     b, xs = rhs(A, seed + 1000)
     return A, b, xs, dict(kiter=kiter, s=s, eps=eps)
+
+
+# --------------------------------------------------------------------------
+# Batch of uneven systems (the batched and served forms)
+# --------------------------------------------------------------------------
+
+def batch_system(k: int, seed: int, nmin: float = 2e3, nmax: float = 2e5):
+    """System k of the uneven batch: n ~ log-uniform[nmin, nmax], type
+    uniform over {2D 5-point, 3D 7-point, 3D 27-point (Q1 FE)}, anisotropy
+    rho ~ log-uniform[1, 1e3] on the last axis, Dirichlet boundary; the
+    grid side is round(n^(1/d)).  Returns (A, type name)."""
+    rng = np.random.Generator(np.random.PCG64([seed, k]))
+    n_target = math.exp(rng.uniform(math.log(nmin), math.log(nmax)))
+    kind = int(rng.integers(0, 3))
+    rho = math.exp(rng.uniform(0.0, math.log(1e3)))
+    if kind == 0:
+        side = max(2, int(round(n_target ** 0.5)))
+        return poisson5_2d(side, side, scale=(1.0, rho)), "5pt2d"
+    side = max(2, int(round(n_target ** (1.0 / 3.0))))
+    if kind == 1:
+        return poisson7(side, side, side, scale=(1.0, 1.0, rho)), "7pt3d"
+    return stencil27_fe(side, side, side, scale=(1.0, 1.0, rho)), "27pt3d"
+
+
+def batch_workload(nsys: int, seed: int = BASE_SEED + 3, nmin: float = 2e3, nmax: float = 2e5):
+    """nsys systems of the uneven batch with seeded right-hand sides."""
+    out = []
+    for k in range(nsys):
+        A, kind = batch_system(k, seed, nmin, nmax)
+        b, _ = rhs(A, seed * 1000 + k)
+        out.append((A, b, kind))
+    return out
