@@ -43,7 +43,8 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "aFSAI set-up+PCG s/solve to relres 1e-8 (FP64; mixed reported beside)"
-WORKLOAD_NAMES = {"elast48": "elasticity_hex48", "hetero256": "hetero_diffusion7_256", "poisson20": "poisson7_20"}
+WORKLOAD_NAMES = {"elast48": "elasticity_hex48", "hetero256": "hetero_diffusion7_256", "poisson20": "poisson7_20",
+                  "batch512": "batch_uneven"}
 # precision forms: storage/arithmetic of G and of the row Cholesky solves
 FORMS = {
     "fp64": dict(g_prec=0, chol_prec=0, desc="FP64 G, FP64 Cholesky"),
@@ -88,7 +89,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the other precision forms")
-    ap.add_argument("--workload", default="elast48", choices=["elast48", "hetero256", "poisson20"])
+    ap.add_argument("--workload", default="elast48", choices=["elast48", "hetero256", "poisson20", "batch512"])
+    ap.add_argument("--nsys", type=int, default=512, help="systems of the batch512 workload")
     ap.add_argument("--form", default="fp64", choices=list(FORMS), help="precision form of the timed line")
     ap.add_argument("--extra-forms", default=None,
                     help="comma list of other forms reported beside (default: mixed; hetero256: g32,bf16,mixed)")
@@ -284,11 +286,129 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, rank, world, local):
+    """Batched form: nsys uneven systems (2D 5-point, 3D 7-point, 3D 27-point,
+    anisotropy up to 1e3, n log-uniform in [2e3, 2e5]) solved by one
+    afsai_batch_solve per step; value = seconds per system solve.  Reported
+    beside: the same batch in FP64, and the plain FP64 GPU path solving the
+    systems one after another (afsai_setup + pcg_solve each)."""
+    import torch
+
+    from paper_2010_14175_gb300 import afsai, matgen as mg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    afsai.load()
+    systems = mg.batch_workload(args.nsys)
+    As = [afsai.DeviceCSR.from_host(A, device=dev) for A, _, _ in systems]
+    bs = [torch.from_numpy(b).to(dev) for _, b, _ in systems]
+    xs = [torch.zeros_like(b) for b in bs]
+    stream = torch.cuda.current_stream(dev)
+    kiter, s_, eps = 8, 2, 1e-3
+    form = args.form if args.form != "fp64" or args.extra_forms == "none" else "mixed"
+
+    def prm_of(f):
+        return afsai.params(kiter, s_, eps, 0, FORMS[f]["g_prec"], FORMS[f]["chol_prec"])
+
+    def batch_once(f):
+        for x in xs:
+            x.zero_()
+        return afsai.afsai_batch_solve(As, prm_of(f), bs, xs, rtol=1e-8, maxit=20000, stream=stream)
+
+    for _ in range(args.warmup):
+        batch_once(form)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = afsai.kernel_launches()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    binfos = []
+    for _ in range(args.steps):
+        infos, binfo = batch_once(form)
+        binfos.append(binfo)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = afsai.kernel_launches() - launches0
+    clk = clocks.stop()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev) / args.steps
+    nsys = len(systems)
+    value = ms / 1e3 / (nsys * world)
+    iters = np.array([i["iters"] for i in infos])
+    worst = max(i["relres_true"] for i in infos)
+    ntot = sum(A.n for A, _, _ in systems)
+    nnz = sum(A.nnz for A, _, _ in systems)
+    w = {0: 8, 1: 4, 2: 2}[FORMS[form]["g_prec"]]
+    nnzg = binfos[-1]["nnz_G"]
+    # batched PCG bytes: every system's iterations x its per-iteration bytes
+    by = 0.0
+    for (A, _, _), it in zip(systems, iters):
+        by += it * (12 * A.nnz + 2 * (4 + w) * nnzg * A.n / ntot + 152 * A.n)
+    solve_ms = float(np.median([b["solve_ms"] for b in binfos]))
+    setup_ms = float(np.median([b["setup_ms"] for b in binfos]))
+    roof = {"kernel": "batched PCG (kb_* kernels)", "bound": "hbm", "achieved": by / (solve_ms * 1e-3) / 1e9,
+            "peak": MEASURED_HBM_GBS, "unit": "GB/s", "frac": None, "traffic": None,
+            "traffic_note": "no ncu record for the batched kernels", "algorithmic_bytes": by,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    extra = {}
+    if args.extra_forms != "none":
+        # the same batch in FP64
+        batch_once("fp64")
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        inf64, b64 = batch_once("fp64")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        extra["batched_fp64"] = {"value": e0.elapsed_time(e1) / 1e3 / nsys, "unit": "s/solve",
+                                 "max_iters": b64["max_iters"], "setup_ms": b64["setup_ms"],
+                                 "solve_ms": b64["solve_ms"]}
+        it64 = np.array([i["iters"] for i in inf64])
+        extra["iters_vs_fp64_max_ratio"] = float(np.max(iters / np.maximum(it64, 1)))
+        # plain FP64 GPU path, one system after another (engines tuned in a first pass)
+        def sequential():
+            for A, b, x in zip(As, bs, xs):
+                x.zero_()
+                M = afsai.afsai_setup(A, prm_of("fp64"), stream)
+                afsai.pcg_solve(A, M, b, x, rtol=1e-8, maxit=20000, stream=stream)
+                M.close()
+        sequential()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sequential()
+        torch.cuda.synchronize()
+        extra["sequential_fp64"] = {"value": (time.perf_counter() - t0) / nsys, "unit": "s/solve",
+                                    "desc": "afsai_setup + pcg_solve per system, FP64, one after another"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "s/solve", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if form == "fp64" else "f64+f32", "data": "synthetic (seeded generator)",
+            "config": {"workload": f"batch_uneven_{nsys}_{form}", "nsys": nsys, "total_rows": ntot, "total_nnz": nnz,
+                       "kiter": kiter, "s": s_, "eps": eps, "rtol": 1e-8, "form": FORMS[form]["desc"],
+                       "l2": "inputs larger than L2", "parallelism": f"replicas x{world}"},
+            "setup_ms": setup_ms, "solve_ms": solve_ms, "pcg_iters_max": int(iters.max()),
+            "pcg_iters_median": float(np.median(iters)), "relres_true_max": worst,
+            "converged": binfos[-1]["converged"], "graph_launches": binfos[-1]["graph_launches"],
+            "setup_rows_per_s": ntot / (setup_ms * 1e-3), "gpu_launches": int(launches), "roofline": roof,
+            "forms": extra, "e2e": None, "cpu_baseline": None, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batch512":
+        run_batch(args, rank, world, local)
         return
     import torch
 

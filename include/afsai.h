@@ -199,6 +199,54 @@ AFSAI_API afsai_status afsai_batch_solve(int32_t nsys, const afsai_csr* A, const
                                          const double* const* b, double* const* x, double rtol, int32_t maxit,
                                          void* stream, pcg_info* info, afsai_batch_info* binfo);
 
+/* ---- Solve server (continuous batching; no counterpart in the paper, which
+ * solves one system at a time).  Registered matrices stay on the device;
+ * the set-up of a matrix runs at its first request and its G is reused.
+ * Requests (1..k right-hand sides each) are admitted in arrival order as
+ * slots and device memory (the budget covers matrices, preconditioners and
+ * vectors) free up; every server step advances all running systems by a
+ * few PCG iterations in one graph launch, whatever their sizes; finished
+ * systems leave and free their slot.  A system's result does not depend on
+ * which other systems were running with it. */
+typedef struct afsai_server afsai_server;
+
+typedef struct {
+    int32_t nrhs;            /* right-hand sides of the request */
+    int32_t max_iters;       /* largest PCG iteration count among them */
+    int32_t converged;       /* 1 if all reached their rtol */
+    int32_t pad;
+    double max_relres_true;  /* largest ||b - A x|| / ||b|| */
+    double queue_ms;         /* submit -> admission */
+    double setup_ms;         /* set-up time paid by this request (0 if G was reused) */
+    double latency_ms;       /* submit -> completion */
+} serve_result;
+
+typedef struct {
+    int64_t requests_submitted, requests_done, solves, steps;
+    int64_t peak_mem_bytes, mem_used_bytes, queued, running;
+} serve_stats;
+
+/* Starts a server thread on the current device.  mem_budget_bytes bounds
+ * the device memory of matrices + preconditioners + vectors; max_slots
+ * bounds the systems on the GPU at once; params applies to every matrix;
+ * iters_per_step = PCG iterations per server step (<= 0: 4). */
+AFSAI_API afsai_status serve_create(size_t mem_budget_bytes, int32_t max_slots, const afsai_params* params,
+                                    int32_t maxit, int32_t iters_per_step, afsai_server** out);
+/* Copies A (host or device CSR) to the device; *matrix_id names it in
+ * later requests.  EBUSY if it does not fit the budget. */
+AFSAI_API afsai_status serve_register(afsai_server* S, const afsai_csr* A, int32_t* matrix_id);
+/* Queues a request: b = n * nrhs HOST doubles (right-hand side k at offset
+ * k n), copied before return.  Returns at once with a ticket. */
+AFSAI_API afsai_status serve_submit(afsai_server* S, int32_t matrix_id, const double* b, int32_t nrhs, double rtol,
+                                    int64_t* ticket);
+/* AFSAI_EAGAIN while the request runs; then copies x (n * nrhs HOST
+ * doubles), per-rhs info (nrhs entries) and the summary (each may be NULL)
+ * and releases the ticket.  ENOCONV if a right-hand side hit maxit. */
+AFSAI_API afsai_status serve_poll(afsai_server* S, int64_t ticket, double* x, pcg_info* info, serve_result* res);
+AFSAI_API afsai_status serve_get_stats(afsai_server* S, serve_stats* out);
+/* Stops the server thread and frees everything (pending requests are dropped). */
+AFSAI_API void serve_destroy(afsai_server* S);
+
 /* End-to-end solve from HOST buffers: copies A and b to the device, builds
  * the preconditioner, runs PCG from x = 0 and copies x back (x_host: n
  * doubles).  Device memory is allocated and freed inside the call.

@@ -30,7 +30,8 @@ OK, EINVAL, ENOMEM, ENOTSPD, ENOCONV, ECUDA, ETIMEOUT, EAGAIN, EBUSY, ENOTSUP = 
 EXPORTS = (
     "afsai_setup", "afsai_apply", "afsai_spmv", "pcg_solve", "afsai_solve_host", "afsai_get_info",
     "afsai_export_G", "afsai_export_Gt", "afsai_export_rows", "afsai_destroy", "afsai_last_error", "afsai_version",
-    "afsai_kernel_launches", "afsai_apply_static", "afsai_batch_solve",
+    "afsai_kernel_launches", "afsai_apply_static", "afsai_batch_solve", "serve_create", "serve_register",
+    "serve_submit", "serve_poll", "serve_get_stats", "serve_destroy",
 )
 
 
@@ -60,6 +61,17 @@ class BatchInfo(ctypes.Structure):
     _fields_ = [("nsys", ctypes.c_int32), ("converged", ctypes.c_int32), ("max_iters", ctypes.c_int32),
                 ("graph_launches", ctypes.c_int32), ("total_rows", ctypes.c_int64), ("nnz_G", ctypes.c_int64),
                 ("setup_ms", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+
+
+class ServeResult(ctypes.Structure):
+    _fields_ = [("nrhs", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("max_relres_true", ctypes.c_double), ("queue_ms", ctypes.c_double),
+                ("setup_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("requests_submitted", "requests_done", "solves", "steps",
+                                              "peak_mem_bytes", "mem_used_bytes", "queued", "running")]
 
 
 class PcgInfo(ctypes.Structure):
@@ -119,6 +131,20 @@ def load(build_if_missing: bool = True):
         lib.afsai_batch_solve.argtypes = [ctypes.c_int32, P, ctypes.POINTER(Params), P, P, ctypes.c_double,
                                           ctypes.c_int32, P, P, ctypes.POINTER(BatchInfo)]
         lib.afsai_batch_solve.restype = st
+        lib.serve_create.argtypes = [ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(Params), ctypes.c_int32,
+                                     ctypes.c_int32, ctypes.POINTER(P)]
+        lib.serve_create.restype = st
+        lib.serve_register.argtypes = [P, ctypes.POINTER(Csr), ctypes.POINTER(ctypes.c_int32)]
+        lib.serve_register.restype = st
+        lib.serve_submit.argtypes = [P, ctypes.c_int32, P, ctypes.c_int32, ctypes.c_double,
+                                     ctypes.POINTER(ctypes.c_int64)]
+        lib.serve_submit.restype = st
+        lib.serve_poll.argtypes = [P, ctypes.c_int64, P, P, ctypes.POINTER(ServeResult)]
+        lib.serve_poll.restype = st
+        lib.serve_get_stats.argtypes = [P, ctypes.POINTER(ServeStats)]
+        lib.serve_get_stats.restype = st
+        lib.serve_destroy.argtypes = [P]
+        lib.serve_destroy.restype = None
         lib.afsai_kernel_launches.argtypes = []
         lib.afsai_kernel_launches.restype = ctypes.c_int64
         _lib = lib
@@ -269,6 +295,84 @@ def afsai_batch_solve(As, prm: Params, bs, xs, rtol=1e-8, maxit=10000, stream=No
     if st != OK and not (st == ENOCONV and not raise_on_noconv):
         _check(st)
     return [_as_dict(i) for i in infos], dict(_as_dict(binfo), status=st)
+
+
+class Server:
+    """Solve server (continuous batching) on the current device."""
+
+    def __init__(self, mem_budget_bytes, max_slots, prm: Params, maxit=10000, iters_per_step=4):
+        h = ctypes.c_void_p()
+        _check(load().serve_create(int(mem_budget_bytes), int(max_slots), ctypes.byref(prm), int(maxit),
+                                   int(iters_per_step), ctypes.byref(h)))
+        self._h = h
+        self._n = {}
+
+    def register(self, A) -> int:
+        """A: host CSR (n, rowptr, col, val numpy arrays) or DeviceCSR."""
+        if isinstance(A, DeviceCSR):
+            csr = A.c()
+        else:
+            self._keep = getattr(self, "_keep", [])
+            arrs = (np.ascontiguousarray(A.rowptr, dtype=np.int32), np.ascontiguousarray(A.col, dtype=np.int32),
+                    np.ascontiguousarray(A.val, dtype=np.float64))
+            self._keep.append(arrs)
+            csr = Csr(A.n, int(arrs[1].size), arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data)
+        mid = ctypes.c_int32()
+        _check(load().serve_register(self._h, ctypes.byref(csr), ctypes.byref(mid)))
+        self._n[mid.value] = A.n
+        return mid.value
+
+    def submit(self, matrix_id, b: np.ndarray, rtol=1e-8) -> int:
+        """b: (n,) or (nrhs, n) float64 host array."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        nrhs = 1 if b.ndim == 1 else b.shape[0]
+        t = ctypes.c_int64()
+        _check(load().serve_submit(self._h, int(matrix_id), b.ctypes.data_as(ctypes.c_void_p), nrhs, float(rtol),
+                                   ctypes.byref(t)))
+        return t.value, matrix_id, nrhs
+
+    def poll(self, ticket):
+        """None while running, else (x (nrhs, n), [info dicts], result dict)."""
+        t, mid, nrhs = ticket
+        n = self._n[mid]
+        x = np.zeros((nrhs, n))
+        infos = (PcgInfo * nrhs)()
+        res = ServeResult()
+        st = load().serve_poll(self._h, t, x.ctypes.data_as(ctypes.c_void_p), ctypes.cast(infos, ctypes.c_void_p),
+                               ctypes.byref(res))
+        if st == EAGAIN:
+            return None
+        if st not in (OK, ENOCONV):
+            _check(st)
+        return x, [_as_dict(i) for i in infos], _as_dict(res)
+
+    def wait(self, ticket, timeout_s=120.0, sleep_s=0.0005):
+        import time
+
+        t0 = time.time()
+        while True:
+            r = self.poll(ticket)
+            if r is not None:
+                return r
+            if time.time() - t0 > timeout_s:
+                raise TimeoutError("request did not finish")
+            time.sleep(sleep_s)
+
+    def stats(self):
+        s = ServeStats()
+        _check(load().serve_get_stats(self._h, ctypes.byref(s)))
+        return _as_dict(s)
+
+    def close(self):
+        if self._h:
+            load().serve_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def afsai_solve_host(A, prm: Params, b: np.ndarray, x: np.ndarray, rtol=1e-8, maxit=10000, stream=None):

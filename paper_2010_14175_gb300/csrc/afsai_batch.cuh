@@ -40,7 +40,7 @@ struct BScal {
     int32_t done;   // 0 running, 1 converged, 2 maxit reached
     int32_t iters;
     int32_t maxit;
-    int32_t pad;
+    int32_t fresh;  // 1: not initialised yet (the start kernels act on fresh systems only)
     int32_t* active;  // device counter of running systems
     unsigned ticket[6];
 };
@@ -78,13 +78,19 @@ struct BatchEngine {
     afsai_status reserve(int32_t max_sys, int64_t max_chunks, cudaStream_t st);
     void release(cudaStream_t st);
     afsai_status upload(const std::vector<BSys>& sys, const std::vector<BScal>& sc, cudaStream_t st);
+    // Slot-indexed tables: rewrites every descriptor (n = 0 marks a free
+    // slot), rebuilds the chunk table over slots with running systems, and
+    // sets the device count of running systems.  Scalars are not touched.
+    afsai_status set_tables(const std::vector<BSys>& sys, const std::vector<char>& running, int32_t nrunning,
+                            cudaStream_t st);
+    afsai_status set_scalars(int32_t slot, const BScal& sc, cudaStream_t st);
     afsai_status start(cudaStream_t st);  // r = b - A x, z = M r, p = z
     afsai_status iteration(cudaStream_t st);
     afsai_status precond(int init, cudaStream_t st);
     afsai_status capture(int iters_per_graph, cudaStream_t st);
     afsai_status launch_graph(cudaStream_t st);
     afsai_status read_active(cudaStream_t st, int32_t* active);
-    afsai_status finish(cudaStream_t st);  // true residuals
+    afsai_status finish(cudaStream_t st, int only_done = 0);  // true residuals (of finished systems only)
 };
 
 // Packs the systems into one block-diagonal CSR and runs the set-up on it.

@@ -103,8 +103,9 @@ __global__ void kb_init(const BSys* __restrict__ sys, BScal* sc, const BChunk* _
     __shared__ double sh[32];
     for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
         const BChunk ch = chunks[c];
-        const BSys& sy = sys[ch.sys];
         BScal* s = &sc[ch.sys];
+        if (!s->fresh) continue;
+        const BSys& sy = sys[ch.sys];
         const int32_t i = ch.row0 + threadIdx.x;
         double rr = 0.0, bb = 0.0;
         if (i < ch.row1) {
@@ -168,7 +169,7 @@ __global__ void kb_G(const BSys* __restrict__ sys, const BScal* sc, const BChunk
                      const int32_t* nchunks, int init) {
     for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
         const BChunk ch = chunks[c];
-        if (!init && sc[ch.sys].done) continue;
+        if (init ? !sc[ch.sys].fresh : (sc[ch.sys].done != 0)) continue;
         const BSys& sy = sys[ch.sys];
         const int32_t i = ch.row0 + threadIdx.x;
         if (i < ch.row1)
@@ -184,7 +185,7 @@ __global__ void kb_Gt_dot(const BSys* __restrict__ sys, BScal* sc, const BChunk*
     for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
         const BChunk ch = chunks[c];
         BScal* s = &sc[ch.sys];
-        if (!init && s->done) continue;
+        if (init ? !s->fresh : (s->done != 0)) continue;
         const BSys& sy = sys[ch.sys];
         const int32_t i = ch.row0 + threadIdx.x;
         double part = 0.0;
@@ -209,13 +210,20 @@ __global__ void kb_Gt_dot(const BSys* __restrict__ sys, BScal* sc, const BChunk*
 }
 
 // ---- p = z (init) ---------------------------------------------------------
-__global__ void kb_init_p(const BSys* __restrict__ sys, const BChunk* __restrict__ chunks, const int32_t* nchunks) {
+__global__ void kb_init_p(const BSys* __restrict__ sys, const BScal* sc, const BChunk* __restrict__ chunks,
+                          const int32_t* nchunks) {
     for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
         const BChunk ch = chunks[c];
+        if (!sc[ch.sys].fresh) continue;
         const BSys& sy = sys[ch.sys];
         const int32_t i = ch.row0 + threadIdx.x;
         if (i < ch.row1) sy.p[i] = sy.z[i];
     }
+}
+
+// ---- end of the start sequence: systems are no longer fresh ---------------
+__global__ void kb_clear_fresh(BScal* sc, int32_t nslots) {
+    for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nslots; k += gridDim.x * blockDim.x) sc[k].fresh = 0;
 }
 
 // ---- q = A p, pq, alpha ---------------------------------------------------
@@ -225,7 +233,7 @@ __global__ void kb_A_dot(const BSys* __restrict__ sys, BScal* sc, const BChunk* 
     for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
         const BChunk ch = chunks[c];
         BScal* s = &sc[ch.sys];
-        if (s->done) continue;
+        if (s->done || s->fresh) continue;
         const BSys& sy = sys[ch.sys];
         const int32_t i = ch.row0 + threadIdx.x;
         double part = 0.0;
@@ -248,7 +256,7 @@ __global__ void kb_update_xr(const BSys* __restrict__ sys, BScal* sc, const BChu
     for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
         const BChunk ch = chunks[c];
         BScal* s = &sc[ch.sys];
-        if (s->done) continue;
+        if (s->done || s->fresh) continue;
         const BSys& sy = sys[ch.sys];
         const double alpha = s->alpha;
         const int32_t i = ch.row0 + threadIdx.x;
@@ -282,7 +290,7 @@ __global__ void kb_update_p(const BSys* __restrict__ sys, const BScal* sc, const
     for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
         const BChunk ch = chunks[c];
         const BScal* s = &sc[ch.sys];
-        if (s->done) continue;
+        if (s->done || s->fresh) continue;
         const BSys& sy = sys[ch.sys];
         const int32_t i = ch.row0 + threadIdx.x;
         if (i < ch.row1) sy.p[i] = fma(s->beta, sy.p[i], sy.z[i]);
@@ -291,11 +299,12 @@ __global__ void kb_update_p(const BSys* __restrict__ sys, const BScal* sc, const
 
 // ---- true residual ||b - A x||^2 per system -------------------------------
 __global__ void kb_true_residual(const BSys* __restrict__ sys, BScal* sc, const BChunk* __restrict__ chunks,
-                                 const int32_t* nchunks, double* partials) {
+                                 const int32_t* nchunks, double* partials, int only_done) {
     __shared__ double sh[32];
     for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
         const BChunk ch = chunks[c];
         BScal* s = &sc[ch.sys];
+        if (only_done && s->done == 0) continue;
         const BSys& sy = sys[ch.sys];
         const int32_t i = ch.row0 + threadIdx.x;
         double part = 0.0;
@@ -420,7 +429,10 @@ afsai_status BatchEngine::upload(const std::vector<BSys>& sys_in, const std::vec
     }
     AFSAI_TRY(reserve(static_cast<int32_t>(sys.size()), static_cast<int64_t>(chunks_h.size()), st));
     std::vector<BScal> sc = sc_in;
-    for (auto& v : sc) v.active = d_counts;
+    for (auto& v : sc) {
+        v.active = d_counts;
+        v.fresh = 1;
+    }
     if (!sys.empty()) {
         AFSAI_CUDA_TRY(cudaMemcpyAsync(d_sys, sys.data(), sizeof(BSys) * sys.size(), cudaMemcpyHostToDevice, st));
         AFSAI_CUDA_TRY(cudaMemcpyAsync(d_sc, sc.data(), sizeof(BScal) * sc.size(), cudaMemcpyHostToDevice, st));
@@ -456,9 +468,46 @@ afsai_status BatchEngine::start(cudaStream_t st) {
     AFSAI_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     AFSAI_TRY(precond(1, st));
-    kb_init_p<<<gb, kChunk, 0, st>>>(d_sys, d_chunks, d_counts + 1);
+    kb_init_p<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, d_counts + 1);
+    kb_clear_fresh<<<std::max(1, std::min(ceil_div(cap_sys, 256), 64)), 256, 0, st>>>(d_sc, cap_sys);
     AFSAI_CUDA_TRY(cudaGetLastError());
-    count_launches(1);
+    count_launches(2);
+    return AFSAI_OK;
+}
+
+afsai_status BatchEngine::set_tables(const std::vector<BSys>& sys_in, const std::vector<char>& running,
+                                     int32_t nrunning, cudaStream_t st) {
+    std::vector<BSys> sys = sys_in;
+    chunks_h.clear();
+    for (size_t s = 0; s < sys.size(); ++s) {
+        sys[s].chunk0 = static_cast<int32_t>(chunks_h.size());
+        sys[s].nchunks = 0;
+        if (!running[s] || sys[s].n <= 0) continue;
+        const int32_t nc = (sys[s].n + kChunk - 1) / kChunk;
+        sys[s].nchunks = nc;
+        for (int32_t c = 0; c < nc; ++c)
+            chunks_h.push_back(BChunk{static_cast<int32_t>(s), c * kChunk, std::min(sys[s].n, (c + 1) * kChunk)});
+    }
+    if (static_cast<int32_t>(sys.size()) > cap_sys || static_cast<int64_t>(chunks_h.size()) > cap_chunks)
+        return fail(AFSAI_ENOTSUP, "batch tables above their reserved capacity");
+    if (!sys.empty())
+        AFSAI_CUDA_TRY(cudaMemcpyAsync(d_sys, sys.data(), sizeof(BSys) * sys.size(), cudaMemcpyHostToDevice, st));
+    if (!chunks_h.empty())
+        AFSAI_CUDA_TRY(cudaMemcpyAsync(d_chunks, chunks_h.data(), sizeof(BChunk) * chunks_h.size(),
+                                       cudaMemcpyHostToDevice, st));
+    h_counts[0] = nrunning;
+    h_counts[1] = static_cast<int32_t>(chunks_h.size());
+    AFSAI_CUDA_TRY(cudaMemcpyAsync(d_counts, h_counts, sizeof(int32_t) * 2, cudaMemcpyHostToDevice, st));
+    AFSAI_CUDA_TRY(cudaStreamSynchronize(st));
+    return AFSAI_OK;
+}
+
+afsai_status BatchEngine::set_scalars(int32_t slot, const BScal& sc_in, cudaStream_t st) {
+    if (slot < 0 || slot >= cap_sys) return fail(AFSAI_EINVAL, "slot out of range");
+    BScal sc = sc_in;
+    sc.active = d_counts;
+    AFSAI_CUDA_TRY(cudaMemcpyAsync(d_sc + slot, &sc, sizeof(BScal), cudaMemcpyHostToDevice, st));
+    AFSAI_CUDA_TRY(cudaStreamSynchronize(st));
     return AFSAI_OK;
 }
 
@@ -513,8 +562,8 @@ afsai_status BatchEngine::read_active(cudaStream_t st, int32_t* active) {
     return AFSAI_OK;
 }
 
-afsai_status BatchEngine::finish(cudaStream_t st) {
-    kb_true_residual<<<grid_blocks(), kChunk, 0, st>>>(d_sys, d_sc, d_chunks, d_counts + 1, d_partials);
+afsai_status BatchEngine::finish(cudaStream_t st, int only_done) {
+    kb_true_residual<<<grid_blocks(), kChunk, 0, st>>>(d_sys, d_sc, d_chunks, d_counts + 1, d_partials, only_done);
     AFSAI_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     return AFSAI_OK;

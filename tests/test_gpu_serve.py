@@ -1,0 +1,101 @@
+"""Serving form: continuous batching of solve requests (serve_* C ABI).
+
+Bars: every request converges to the true residual 1e-8 with the oracle's
+iteration count +-1; requests submitted while others run overlap on the
+device (the server runs several at once); each result is bit-for-bit the
+same alone and in the mix; the preconditioner of a matrix is built once and
+reused; a small memory budget queues requests instead of failing them."""
+import numpy as np
+import pytest
+
+from paper_2010_14175_gb300 import matgen as mg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2010_14175_gb300 import afsai
+
+    afsai.load()
+    return afsai
+
+
+@pytest.fixture(scope="module")
+def pool():
+    return [A for A, _, _ in mg.batch_workload(6, seed=mg.BASE_SEED + 9, nmin=300, nmax=4000)]
+
+
+def _rhs(A, k, nrhs):
+    rng = np.random.default_rng(1000 + k)
+    return rng.uniform(-1, 1, size=(nrhs, A.n))
+
+
+def test_server_mix_matches_alone_and_oracle(gpu, oracle_mod, pool):
+    afsai = gpu
+    prm = afsai.params(8, 2, 1e-3)
+    # alone: one server, one request at a time
+    alone = {}
+    S = afsai.Server(2 << 30, 64, prm)
+    ids = [S.register(A) for A in pool]
+    for k in range(8):
+        m = k % len(pool)
+        b = _rhs(pool[m], k, 1 + k % 3)
+        x, infos, res = S.wait(S.submit(ids[m], b))
+        alone[k] = x
+    S.close()
+    # mix: all submitted at once to a fresh server
+    S = afsai.Server(2 << 30, 64, prm)
+    ids = [S.register(A) for A in pool]
+    tickets = {}
+    for k in range(8):
+        m = k % len(pool)
+        tickets[k] = (m, S.submit(ids[m], _rhs(pool[m], k, 1 + k % 3)))
+    results = {k: S.wait(t) for k, (m, t) in tickets.items()}
+    st = S.stats()
+    S.close()
+    assert st["requests_done"] == 8 and st["solves"] == sum(1 + k % 3 for k in range(8))
+    for k, (m, _) in tickets.items():
+        x, infos, res = results[k]
+        assert res["converged"] == 1 and res["max_relres_true"] <= 1.05e-8
+        assert np.array_equal(x, alone[k]), f"request {k}: mix differs from alone"
+        A = pool[m]
+        G = oracle_mod.afsai_setup(A, 8, 2, 1e-3)
+        b = _rhs(A, k, 1 + k % 3)
+        for j in range(b.shape[0]):
+            xo, it_o, _, _ = oracle_mod.pcg(A, G, b[j], rtol=1e-8)
+            assert abs(infos[j]["iters"] - it_o) <= 1
+            assert np.linalg.norm(x[j] - xo) <= 1e-6 * np.linalg.norm(xo)
+
+
+def test_server_overlap_reuse_and_budget(gpu, pool):
+    afsai = gpu
+    prm = afsai.params(8, 2, 1e-3)
+    # budget just above the matrices + one preconditioner + a few vectors:
+    # requests must queue and still complete
+    need = sum(4 * (A.n + 1) + 12 * A.nnz for A in pool)
+    nmax = max(A.n for A in pool)
+    budget = need + 2 * (nmax * 17 * 12 * 2 + 24 * nmax) + 3 * 7 * 8 * nmax
+    S = afsai.Server(budget, 16, prm)
+    ids = [S.register(A) for A in pool]
+    ts = [S.submit(ids[k % len(pool)], _rhs(pool[k % len(pool)], k, 1)) for k in range(12)]
+    out = [S.wait(t) for t in ts]
+    st = S.stats()
+    S.close()
+    assert all(r[2]["converged"] == 1 for r in out)
+    assert st["peak_mem_bytes"] <= budget
+    # set-up paid once per matrix while it stayed resident: some requests reused G
+    assert sum(1 for r in out if r[2]["setup_ms"] == 0.0) >= 1
+    # plenty of memory: later requests of a matrix reuse its G, and requests overlap
+    S = afsai.Server(4 << 30, 64, prm)
+    ids = [S.register(A) for A in pool]
+    ts = [S.submit(ids[k % len(pool)], _rhs(pool[k % len(pool)], k, 2)) for k in range(18)]
+    out = [S.wait(t) for t in ts]
+    st = S.stats()
+    S.close()
+    paid = [r[2]["setup_ms"] > 0 for r in out]
+    assert sum(paid) == len(pool)  # one set-up per matrix
+    assert st["steps"] < sum(r[2]["max_iters"] for r in out) / 4  # requests shared steps
