@@ -44,7 +44,7 @@ if ROOT not in sys.path:
 
 METRIC = "aFSAI set-up+PCG s/solve to relres 1e-8 (FP64; mixed reported beside)"
 WORKLOAD_NAMES = {"elast48": "elasticity_hex48", "hetero256": "hetero_diffusion7_256", "poisson20": "poisson7_20",
-                  "batch512": "batch_uneven"}
+                  "batch512": "batch_uneven", "serve": "serve_poisson_arrivals"}
 # precision forms: storage/arithmetic of G and of the row Cholesky solves
 FORMS = {
     "fp64": dict(g_prec=0, chol_prec=0, desc="FP64 G, FP64 Cholesky"),
@@ -89,7 +89,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the other precision forms")
-    ap.add_argument("--workload", default="elast48", choices=["elast48", "hetero256", "poisson20", "batch512"])
+    ap.add_argument("--workload", default="elast48",
+                    choices=["elast48", "hetero256", "poisson20", "batch512", "serve"])
+    ap.add_argument("--requests", type=int, default=2000, help="timed requests of the serve workload")
+    ap.add_argument("--warm-requests", type=int, default=200)
     ap.add_argument("--nsys", type=int, default=512, help="systems of the batch512 workload")
     ap.add_argument("--form", default="fp64", choices=list(FORMS), help="precision form of the timed line")
     ap.add_argument("--extra-forms", default=None,
@@ -401,6 +404,139 @@ def run_batch(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_serve(args, rank, world, local):
+    """Serving form: a pool of 64 matrices from the uneven-batch
+    distribution; requests pick a matrix uniformly and bring 1..8
+    right-hand sides; arrivals are a Poisson process at 70% of the
+    server's measured capacity (solves/s when saturated); G is built at a
+    matrix's first request and reused.  Reports p50/p99 latency (submit ->
+    completion, measured by the server) and solves/s, beside the plain FP64
+    path serving the same requests one at a time."""
+    import torch
+
+    from paper_2010_14175_gb300 import afsai, matgen as mg
+
+    torch.cuda.set_device(local)
+    afsai.load()
+    rng = np.random.Generator(np.random.PCG64(mg.BASE_SEED + 5))
+    pool = [A for A, _, _ in mg.batch_workload(64, seed=mg.BASE_SEED + 4)]
+    form = args.form if args.form != "fp64" else "mixed"
+    f = FORMS[form]
+    prm = afsai.params(8, 2, 1e-3, 0, f["g_prec"], f["chol_prec"])
+    S = afsai.Server(150 << 30, 512, prm, maxit=20000, iters_per_step=4)
+    ids = [S.register(A) for A in pool]
+
+    def make_request():
+        m = int(rng.integers(0, len(pool)))
+        nrhs = int(rng.integers(1, 9))
+        return m, rng.uniform(-1, 1, size=(nrhs, pool[m].n))
+
+    def drain(tickets):
+        done = []
+        while tickets:
+            keep = []
+            for t in tickets:
+                r = S.poll(t)
+                if r is None:
+                    keep.append(t)
+                else:
+                    done.append(r)
+            tickets = keep
+            if tickets:
+                time.sleep(0.0005)
+        return done
+
+    # capacity: saturate the server (all matrices' G built by a first pass)
+    drain([S.submit(ids[m], np.ones(pool[m].n)) for m in range(len(pool))])
+    burst = [make_request() for _ in range(256)]
+    t0 = time.perf_counter()
+    res = drain([S.submit(ids[m], b) for m, b in burst])
+    cap_s = time.perf_counter() - t0
+    capacity = sum(b.shape[0] for _, b in burst) / cap_s  # solves/s
+    mean_rhs = 4.5
+    lam = 0.7 * capacity / mean_rhs  # requests/s
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = afsai.kernel_launches()
+
+    def poisson_run(nreq):
+        outstanding, done = [], []
+        t_next = time.perf_counter()
+        start = t_next
+        for _ in range(nreq):
+            t_next += rng.exponential(1.0 / lam)
+            m, b = make_request()
+            while True:
+                now = time.perf_counter()
+                if now >= t_next:
+                    break
+                keep = []
+                for t in outstanding:
+                    r = S.poll(t)
+                    if r is None:
+                        keep.append(t)
+                    else:
+                        done.append(r)
+                outstanding = keep
+                if t_next - now > 0.0005:
+                    time.sleep(min(0.0005, t_next - now))
+            outstanding.append(S.submit(ids[m], b))
+        done += drain(outstanding)
+        return done, time.perf_counter() - start
+
+    poisson_run(args.warm_requests)
+    done, wall = poisson_run(args.requests)
+    launches = afsai.kernel_launches() - launches0
+    clk = clocks.stop()
+    st = S.stats()
+    S.close()
+    lat = np.array([r[2]["latency_ms"] for r in done])
+    solves = sum(r[2]["nrhs"] for r in done)
+    worst = max(r[2]["max_relres_true"] for r in done)
+    conv = all(r[2]["converged"] == 1 for r in done)
+    # plain FP64 path, one request at a time (G cached per matrix), on a sample
+    nseq = min(100, args.requests)
+    Ad = [afsai.DeviceCSR.from_host(A) for A in pool]
+    Ms = {}
+    seq = [make_request() for _ in range(nseq)]
+    for m in set(m for m, _ in seq):
+        Ms[m] = afsai.afsai_setup(Ad[m], afsai.params(8, 2, 1e-3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat_seq = []
+    for m, b in seq:
+        t1 = time.perf_counter()
+        for j in range(b.shape[0]):
+            bd = torch.from_numpy(b[j]).cuda()
+            x = torch.zeros_like(bd)
+            afsai.pcg_solve(Ad[m], Ms[m], bd, x, rtol=1e-8, maxit=20000)
+            x.cpu()
+        lat_seq.append((time.perf_counter() - t1) * 1e3)
+    seq_wall = time.perf_counter() - t0
+    seq_solves = sum(b.shape[0] for _, b in seq) / seq_wall
+    if rank == 0:
+        line = {
+            "metric": METRIC + "; serve p50/p99 ms", "value": float(np.percentile(lat, 50)) / 1e3, "unit": "s/request",
+            "n_gpus": world, "steps": args.requests, "warmup": args.warm_requests,
+            "ms_per_step": float(np.percentile(lat, 50)), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic (seeded generator, Poisson arrivals)",
+            "config": {"workload": f"serve_pool64_{form}", "arrival_rate_req_s": lam, "capacity_solves_s": capacity,
+                       "load": 0.7, "nrhs": "U{1..8}", "pool": 64, "budget_gb": 150, "iters_per_step": 4,
+                       "form": FORMS[form]["desc"], "parallelism": f"replicas x{world}"},
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "solves_per_s": solves / wall, "requests": len(done),
+            "all_converged": conv, "relres_true_max": worst, "server_steps": st["steps"],
+            "peak_mem_gb": st["peak_mem_bytes"] / 2 ** 30, "gpu_launches": int(launches),
+            "sequential_fp64": {"solves_per_s": seq_solves, "p50_ms": float(np.percentile(lat_seq, 50)),
+                                "p99_ms": float(np.percentile(lat_seq, 99)), "requests": nseq,
+                                "desc": "pcg_solve per right-hand side, one request after another, G cached"},
+            "roofline": None, "e2e": {"value": float(np.percentile(lat, 50)) / 1e3, "unit": "s/request",
+                                      "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
+            "cpu_baseline": None, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_init(args)
@@ -409,6 +545,9 @@ def main():
         return
     if args.workload == "batch512":
         run_batch(args, rank, world, local)
+        return
+    if args.workload == "serve":
+        run_serve(args, rank, world, local)
         return
     import torch
 
