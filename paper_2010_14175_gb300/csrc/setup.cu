@@ -90,6 +90,9 @@ struct WarpWs {
     int32_t re[MCAP];
     int32_t isnew[MCAP];                   // 1 for positions inserted this step
     int32_t opos[MCAP];                    // new position of each old position
+    int32_t Pn[MCAP];                      // merge buffers
+    int32_t rbn[MCAP];
+    int32_t ren[MCAP];
     int32_t nkeys;                         // keys in the candidate table this step
     int32_t pad_;
     union {
@@ -226,6 +229,54 @@ __device__ void group_llt_solve(const T* L, T* x, int m, bool em, int sub, unsig
     }
 }
 
+// Entries of one row of A held in registers: chunk q covers the entries
+// rb + sub + q*GL (up to NPF chunks; longer rows continue directly).  NPF is
+// 1 for short rows (small candidate tables), 4 otherwise, to keep the
+// register budget of short-row kernels low.
+template <int NPF>
+struct RowPref {
+    int32_t c[NPF];
+    double v[NPF];
+};
+
+template <int GL, int NPF>
+__device__ __forceinline__ void prefetch_row(RowPref<NPF>& R, const int32_t* __restrict__ colA,
+                                             const double* __restrict__ valA, int32_t rb, int32_t re, int sub) {
+#pragma unroll
+    for (int q = 0; q < NPF; ++q) {
+        const int32_t e = rb + sub + q * GL;
+        R.c[q] = e < re ? __ldg(&colA[e]) : INT_MAX;
+        R.v[q] = e < re ? __ldg(&valA[e]) : 0.0;
+    }
+}
+
+// Accumulates one row r of A (weight gr = g_r) into the candidate table:
+// acc_j = fma(a_rj, g_r, acc_j) for the row's columns j < i, in CSR order.
+template <int GL, int NPF>
+__device__ __forceinline__ void accumulate_row(const RowPref<NPF>& R, const int32_t* __restrict__ colA,
+                                               const double* __restrict__ valA, int32_t rb, int32_t re, int32_t i,
+                                               double gr, int32_t* key, double* hv, int32_t* list, int log2,
+                                               int32_t* nkeys, bool& ovf, int sub, unsigned gmask) {
+#pragma unroll
+    for (int q = 0; q < NPF; ++q) {
+        const int32_t j = R.c[q];
+        if (!__any_sync(gmask, j < i)) return;  // columns are sorted
+        if (j < i) {
+            const int slot = table_insert(key, list, log2, j, nkeys, ovf);
+            if (slot >= 0) hv[slot] = fma(R.v[q], gr, hv[slot]);
+        }
+    }
+    for (int32_t e = rb + sub + NPF * GL;; e += GL) {
+        const int32_t j = e < re ? __ldg(&colA[e]) : INT_MAX;
+        const double v = e < re ? __ldg(&valA[e]) : 0.0;
+        if (!__any_sync(gmask, j < i)) return;
+        if (j < i) {
+            const int slot = table_insert(key, list, log2, j, nkeys, ovf);
+            if (slot >= 0) hv[slot] = fma(v, gr, hv[slot]);
+        }
+    }
+}
+
 template <int GL, int MCAP, int HT, bool CHOL32>
 __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, int32_t* key, double* hv,
                           int32_t* list, int log2, int sub, unsigned gmask, const uint16_t* pairs) {
@@ -269,19 +320,24 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
         if (sub == 0) w.nkeys = 0;
         __syncwarp(gmask);
         bool ovf = false;
-        for (int t = 0; t < m; ++t) {
-            const double gr = w.g[t];
-            const int32_t e1 = w.re[t];
-            // columns are sorted: stop at the first chunk with no j < i
-            for (int32_t e = w.rb[t] + sub;; e += GL) {
-                const int32_t j = e < e1 ? __ldg(&colA[e]) : INT_MAX;
-                if (!__any_sync(gmask, j < i)) break;
-                if (j < i) {
-                    const int slot = table_insert(key, list, log2, j, &w.nkeys, ovf);
-                    if (slot >= 0) hv[slot] = fma(__ldg(&valA[e]), gr, hv[slot]);
+        {
+            // rows r in P ascending; the next row's entries are loaded while
+            // the current one is accumulated
+            constexpr int NPF = HT <= 256 ? 1 : 4;
+            RowPref<NPF> RA, RB;
+            prefetch_row<GL, NPF>(RA, colA, valA, w.rb[0], w.re[0], sub);
+            for (int t = 0; t < m; t += 2) {
+                if (t + 1 < m) prefetch_row<GL, NPF>(RB, colA, valA, w.rb[t + 1], w.re[t + 1], sub);
+                accumulate_row<GL, NPF>(RA, colA, valA, w.rb[t], w.re[t], i, w.g[t], key, hv, list, log2, &w.nkeys, ovf,
+                                   sub, gmask);
+                __syncwarp(gmask);
+                if (t + 1 < m) {
+                    if (t + 2 < m) prefetch_row<GL, NPF>(RA, colA, valA, w.rb[t + 2], w.re[t + 2], sub);
+                    accumulate_row<GL, NPF>(RB, colA, valA, w.rb[t + 1], w.re[t + 1], i, w.g[t + 1], key, hv, list, log2,
+                                       &w.nkeys, ovf, sub, gmask);
+                    __syncwarp(gmask);
                 }
             }
-            __syncwarp(gmask);
         }
         if (__any_sync(gmask, ovf)) {
             status = kRowOverflow;
@@ -342,23 +398,38 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
         const int told = tri(mold);
         for (int t = sub; t < told; t += GL) scratch[t] = w.Mraw[t];
         __syncwarp(gmask);
-        if (sub == 0) {
-            for (int t = 0; t < m; ++t) w.isnew[t] = 0;
-            for (int u = 0; u < npick; ++u) {
-                const int32_t j = w.newj[u];
-                int pos = mold + u;
-                while (pos > 0 && w.P[pos - 1] > j) {
-                    w.P[pos] = w.P[pos - 1];
-                    w.rb[pos] = w.rb[pos - 1];
-                    w.re[pos] = w.re[pos - 1];
-                    w.isnew[pos] = w.isnew[pos - 1];
-                    --pos;
-                }
-                w.P[pos] = j;
-                w.isnew[pos] = 1;
+        // new positions: an old entry moves up by the number of picks below
+        // it; a pick lands after the old entries and the picks below it
+        for (int t = sub; t < mold; t += GL) {
+            const int32_t pt = w.P[t];
+            int up = 0;
+            for (int u = 0; u < npick; ++u) up += w.newj[u] < pt;
+            w.opos[t] = t + up;
+            w.Pn[t + up] = pt;
+            w.rbn[t + up] = w.rb[t];
+            w.ren[t + up] = w.re[t];
+        }
+        for (int u = sub; u < npick; u += GL) {
+            const int32_t j = w.newj[u];
+            int below = 0;
+            for (int q = 0; q < npick; ++q) below += w.newj[q] < j;
+            int lo = 0, hi = mold;  // old entries below j
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (w.P[mid] < j)
+                    lo = mid + 1;
+                else
+                    hi = mid;
             }
-            for (int q = 0, cnt = 0; q < m; ++q)
-                if (!w.isnew[q]) w.opos[cnt++] = q;
+            w.Pn[lo + below] = j;
+            w.rbn[lo + below] = -1;  // marks a new position
+        }
+        __syncwarp(gmask);
+        for (int t = sub; t < m; t += GL) {
+            w.P[t] = w.Pn[t];
+            w.isnew[t] = w.rbn[t] < 0 ? 1 : 0;
+            w.rb[t] = w.rbn[t];
+            w.re[t] = w.ren[t];
         }
         __syncwarp(gmask);
         const int tnew = tri(m);
@@ -382,12 +453,13 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
             const int32_t e0 = w.rb[pj], e1 = w.re[pj];
             for (int32_t e = e0 + sub; e < e1; e += GL) {
                 const int32_t c = __ldg(&colA[e]);
+                const double v = __ldg(&valA[e]);
                 const int pc = find_sorted(w.P, m, c);
                 if (pc < 0) continue;
                 if (pc <= pj)
-                    w.Mraw[tri(pj) + pc] = __ldg(&valA[e]);
+                    w.Mraw[tri(pj) + pc] = v;
                 else if (!w.isnew[pc])
-                    w.Mraw[tri(pc) + pj] = __ldg(&valA[e]);
+                    w.Mraw[tri(pc) + pj] = v;
             }
         }
         __syncwarp(gmask);
