@@ -51,6 +51,9 @@ FORMS = {
     "mixed": dict(g_prec=1, chol_prec=1, desc="FP32 G, FP32 Cholesky + one FP64 refinement step"),
     "g32": dict(g_prec=1, chol_prec=0, desc="FP32 G, FP64 Cholesky"),
     "bf16": dict(g_prec=2, chol_prec=1, desc="BF16 G, FP32 Cholesky + one FP64 refinement step"),
+    # the paper's comparison preconditioner (Section 5.2): kiter = 0 keeps
+    # the diagonal pattern, G^T G = diag(A)^{-1}
+    "jacobi": dict(g_prec=0, chol_prec=0, kiter=0, desc="Jacobi (aFSAI with kiter = 0), FP64"),
 }
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -565,7 +568,7 @@ def main():
 
     def prm_of(form):
         f = FORMS[form]
-        return afsai.params(p["kiter"], p["s"], p["eps"], 0, f["g_prec"], f["chol_prec"])
+        return afsai.params(f.get("kiter", p["kiter"]), p["s"], p["eps"], 0, f["g_prec"], f["chol_prec"])
 
     def one_solve(prm_):
         x.zero_()
@@ -634,7 +637,7 @@ def main():
     extra = {}
     if not args.no_mixed:
         names = args.extra_forms.split(",") if args.extra_forms else (
-            ["g32", "bf16", "mixed"] if args.workload == "hetero256" else ["mixed"])
+            ["g32", "bf16", "mixed", "jacobi"] if args.workload == "hetero256" else ["mixed", "jacobi"])
         for form in [f for f in names if f and f != args.form]:
             pf = prm_of(form)
             for _ in range(2):

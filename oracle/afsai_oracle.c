@@ -310,6 +310,8 @@ int oracle_afsai_rows(int32_t n, const int32_t* rowptr, const int32_t* col, cons
     int64_t candcap = mcap * (int64_t)max_row_nnz(&A) + 1;
     int status = ORC_OK;
 #ifdef _OPENMP
+    /* thread count of this call only (the default is restored after) */
+    const int nt_before = omp_get_max_threads();
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel
 #endif
@@ -340,6 +342,9 @@ int oracle_afsai_rows(int32_t n, const int32_t* rowptr, const int32_t* col, cons
         }
         ws_free(&w);
     }
+#ifdef _OPENMP
+    omp_set_num_threads(nt_before);
+#endif
     return status;
 }
 

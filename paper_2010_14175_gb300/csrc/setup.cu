@@ -646,6 +646,9 @@ afsai_status dispatch(int mcap_t, int ht, int gl, const SetupArgs& a, int64_t nr
         case 16:
             return ht == 256 ? dispatch_gl<16, 256>(gl, a, nrows, max_groups, gtable, chol32, st)
                              : dispatch_gl<16, 512>(gl, a, nrows, max_groups, gtable, chol32, st);
+        case 20:
+            return ht == 256 ? dispatch_gl<20, 256>(gl, a, nrows, max_groups, gtable, chol32, st)
+                             : dispatch_gl<20, 512>(gl, a, nrows, max_groups, gtable, chol32, st);
         case 32:
             return ht == 256 ? dispatch_gl<32, 256>(gl, a, nrows, max_groups, gtable, chol32, st)
                              : dispatch_gl<32, 512>(gl, a, nrows, max_groups, gtable, chol32, st);
@@ -683,6 +686,470 @@ __global__ void compact_rows_kernel(int32_t n, int64_t mcap, const int32_t* __re
     if (lane == 0 && localmax > 0) atomicMax(maxrow, localmax);
 }
 
+// ---------------------------------------------------------------------------
+// Stepwise set-up for small patterns (1 + kiter s <= 20).
+//
+// With few entries per row, the fused kernel spends its FP64 issue slots on
+// square roots and divisions with one useful lane.  Here every step k runs
+// as two kernels, the structure of the paper's Section 3 (gradient +
+// selection + systems gather, then batched Cholesky):
+//   A  one warp per active row: Kaporin gradient, top-s selection, merge,
+//      full gather of A[P,P] into a per-row slot in global memory;
+//   B  one LANE per row: the row's Cholesky, triangular solves, psi and the
+//      exit test, in the exact sequential order of the plain definition, so
+//      each FP64 warp instruction serves 32 rows.
+// Row state (P, g, psi, step count, status) lives in global memory between
+// the kernels.  Results are bit-identical to the fused kernel.
+// ---------------------------------------------------------------------------
+constexpr int32_t kStActive = 0;   // in the loop, no system pending
+constexpr int32_t kStSolve = 1;    // system gathered, solve pending
+constexpr int32_t kStStop = 2;     // finished (exit test or no candidates)
+
+struct StepArgs {
+    int32_t n;
+    const int32_t* __restrict__ rowptr;
+    const int32_t* __restrict__ col;
+    const double* __restrict__ val;
+    int32_t s;
+    int32_t exit_mode;
+    double eps;
+    int32_t mc;   // row stride of P and g
+    int32_t tmc;  // row stride of the gathered triangle
+    int32_t* P;
+    double* g;
+    double* M;
+    int32_t* m;
+    int32_t* steps;
+    int32_t* st;
+    double* psi;
+    double* psi0;
+};
+
+__global__ void step_init(StepArgs a) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < a.n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        double aii = 0.0;
+        for (int32_t e = a.rowptr[i]; e < a.rowptr[i + 1]; ++e)
+            if (a.col[e] == i) aii = a.val[e];
+        a.P[i * a.mc] = static_cast<int32_t>(i);
+        a.g[i * a.mc] = 1.0 / aii;
+        a.m[i] = 1;
+        a.steps[i] = 0;
+        a.psi[i] = aii;
+        a.psi0[i] = aii;
+        a.st[i] = positive(aii) ? kStActive : kRowNotSpd;
+    }
+}
+
+template <int MC, int HT>
+struct GatherWs {
+    double g[MC];
+    double Mw[MC * (MC + 1) / 2];
+    int32_t P[MC];
+    int32_t newj[MC];
+    int32_t Pn[MC];
+    int32_t rb[MC];
+    int32_t re[MC];
+    int32_t nkeys;
+    int32_t pad_;
+    double val[HT];
+    int32_t key[HT];
+    int32_t list[HT];
+};
+
+template <int MC, int HT>
+__global__ void __launch_bounds__(256) step_gather(StepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    using WS = GatherWs<MC, HT>;
+    constexpr int GL = 32;
+    const int warp = threadIdx.x >> 5;
+    const int sub = threadIdx.x & 31;
+    const unsigned gmask = 0xffffffffu;
+    WS& w = reinterpret_cast<WS*>(smem_raw)[warp];
+    constexpr int log2 = (HT == 256) ? 8 : 9;
+    const int64_t gw = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + warp;
+    const int64_t nw = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t ii = gw; ii < a.n; ii += nw) {
+        if (a.st[ii] != kStActive) continue;
+        const int32_t i = static_cast<int32_t>(ii);
+        int m = a.m[i];
+        for (int t = sub; t < m; t += GL) {
+            w.P[t] = a.P[ii * a.mc + t];
+            w.g[t] = a.g[ii * a.mc + t];
+            w.rb[t] = a.rowptr[w.P[t]];
+            w.re[t] = a.rowptr[w.P[t] + 1];
+        }
+        for (int t = sub; t < HT; t += GL) {
+            w.key[t] = -1;
+            w.val[t] = 0.0;
+        }
+        if (sub == 0) w.nkeys = 0;
+        __syncwarp();
+        // ---- Kaporin gradient over j < i (Eq. "grapsi") ----
+        bool ovf = false;
+        {
+            constexpr int NPF = HT <= 256 ? 1 : 4;
+            RowPref<NPF> RA, RB;
+            prefetch_row<GL, NPF>(RA, a.col, a.val, w.rb[0], w.re[0], sub);
+            for (int t = 0; t < m; t += 2) {
+                if (t + 1 < m) prefetch_row<GL, NPF>(RB, a.col, a.val, w.rb[t + 1], w.re[t + 1], sub);
+                accumulate_row<GL, NPF>(RA, a.col, a.val, w.rb[t], w.re[t], i, w.g[t], w.key, w.val, w.list, log2,
+                                        &w.nkeys, ovf, sub, gmask);
+                __syncwarp();
+                if (t + 1 < m) {
+                    if (t + 2 < m) prefetch_row<GL, NPF>(RA, a.col, a.val, w.rb[t + 2], w.re[t + 2], sub);
+                    accumulate_row<GL, NPF>(RB, a.col, a.val, w.rb[t + 1], w.re[t + 1], i, w.g[t + 1], w.key, w.val,
+                                            w.list, log2, &w.nkeys, ovf, sub, gmask);
+                    __syncwarp();
+                }
+            }
+        }
+        if (__any_sync(gmask, ovf)) {
+            if (sub == 0) a.st[i] = kRowOverflow;
+            __syncwarp();
+            continue;
+        }
+        for (int t = sub; t < m - 1; t += GL) {
+            const int slot = table_find(w.key, log2, w.P[t]);
+            if (slot >= 0) w.val[slot] = 0.0;
+        }
+        __syncwarp();
+        // ---- select the s largest |gradient| (ties: smaller column) ----
+        const int nk = w.nkeys;
+        int npick = 0;
+        for (int u = 0; u < a.s; ++u) {
+            unsigned long long best = 0ull;
+            int32_t bestj = INT_MAX;
+            int bslot = -1;
+            for (int t = sub; t < nk; t += GL) {
+                const int sl = w.list[t];
+                const int32_t j = w.key[sl];
+                const unsigned long long ab =
+                    static_cast<unsigned long long>(__double_as_longlong(w.val[sl])) & 0x7fffffffffffffffull;
+                if (ab == 0ull || ab > 0x7ff0000000000000ull) continue;
+                if (ab > best || (ab == best && j < bestj)) {
+                    best = ab;
+                    bestj = j;
+                    bslot = sl;
+                }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const unsigned long long ob = __shfl_xor_sync(gmask, best, off);
+                const int32_t oj = __shfl_xor_sync(gmask, bestj, off);
+                const int os = __shfl_xor_sync(gmask, bslot, off);
+                if (ob > best || (ob == best && oj < bestj)) {
+                    best = ob;
+                    bestj = oj;
+                    bslot = os;
+                }
+            }
+            if (best == 0ull) break;
+            if (sub == 0) {
+                w.val[bslot] = 0.0;
+                w.newj[npick] = bestj;
+            }
+            ++npick;
+            __syncwarp();
+        }
+        if (npick == 0) {
+            if (sub == 0) a.st[i] = kStStop;
+            __syncwarp();
+            continue;
+        }
+        // ---- merge into the sorted pattern ----
+        const int mold = m;
+        for (int t = sub; t < mold; t += GL) {
+            const int32_t pt = w.P[t];
+            int up = 0;
+            for (int u = 0; u < npick; ++u) up += w.newj[u] < pt;
+            w.Pn[t + up] = pt;
+        }
+        for (int u = sub; u < npick; u += GL) {
+            const int32_t j = w.newj[u];
+            int below = 0;
+            for (int q = 0; q < npick; ++q) below += w.newj[q] < j;
+            int lo = 0, hi = mold;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (w.P[mid] < j)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            w.Pn[lo + below] = j;
+        }
+        m = mold + npick;
+        __syncwarp();
+        for (int t = sub; t < m; t += GL) {
+            const int32_t pt = w.Pn[t];
+            w.P[t] = pt;
+            a.P[ii * a.mc + t] = pt;
+            w.rb[t] = a.rowptr[pt];
+            w.re[t] = a.rowptr[pt + 1];
+        }
+        const int tm = tri(m);
+        for (int t = sub; t < tm; t += GL) w.Mw[t] = 0.0;
+        __syncwarp();
+        // ---- systems gather: A[P,P], lower triangle, from the rows of P ----
+        for (int r = 0; r < m; ++r) {
+            const int32_t pr = w.P[r];
+            for (int32_t e = w.rb[r] + sub; e < w.re[r]; e += GL) {
+                const int32_t c = __ldg(&a.col[e]);
+                const double v = __ldg(&a.val[e]);
+                if (c > pr) continue;
+                const int pc = find_sorted(w.P, r + 1, c);
+                if (pc >= 0) w.Mw[tri(r) + pc] = v;
+            }
+        }
+        __syncwarp();
+        for (int t = sub; t < tm; t += GL) a.M[ii * a.tmc + t] = w.Mw[t];
+        if (sub == 0) {
+            a.m[i] = m;
+            a.steps[i] += 1;
+            a.st[i] = kStSolve;
+        }
+        __syncwarp();
+    }
+}
+
+// One lane per row: Cholesky, solve, psi, exit test (plain sequential order).
+template <int MC, bool CHOL32>
+__global__ void __launch_bounds__(64) step_solve(StepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int TMC = MC * (MC + 1) / 2;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int nwb = blockDim.x >> 5;
+    // lane-interleaved per-warp area: element e of lane l at [e * 32 + l]
+    double* Ms = reinterpret_cast<double*>(smem_raw) + static_cast<size_t>(warp) * (TMC + MC) * 32;
+    double* gs = Ms + TMC * 32;
+    float* Lf = reinterpret_cast<float*>(reinterpret_cast<double*>(smem_raw) + static_cast<size_t>(nwb) * (TMC + MC) * 32) +
+                static_cast<size_t>(warp) * (TMC + MC) * 32;
+    float* xf = Lf + TMC * 32;
+#define MS(e) Ms[(e) * 32 + lane]
+#define GS(e) gs[(e) * 32 + lane]
+#define LF(e) Lf[(e) * 32 + lane]
+#define XF(e) xf[(e) * 32 + lane]
+    const int64_t ngroups = (static_cast<int64_t>(a.n) + 31) / 32;
+    for (int64_t grp = static_cast<int64_t>(blockIdx.x) * nwb + warp; grp < ngroups;
+         grp += static_cast<int64_t>(gridDim.x) * nwb) {
+        const int64_t ii = grp * 32 + lane;
+        if (ii >= a.n || a.st[ii] != kStSolve) continue;
+        const int m = a.m[ii];
+        const int tm = tri(m);
+        for (int t = 0; t < tm; ++t) MS(t) = a.M[ii * a.tmc + t];
+        bool spd = true;
+        if (!CHOL32) {
+            for (int c = 0; c < m && spd; ++c) {
+                const double piv = MS(tri(c) + c);
+                if (!positive(piv)) {
+                    spd = false;
+                    break;
+                }
+                const double d = sqrt(piv);
+                MS(tri(c) + c) = d;
+                for (int r = c + 1; r < m; ++r) MS(tri(r) + c) = MS(tri(r) + c) / d;
+                for (int r = c + 1; r < m; ++r)
+                    for (int q = c + 1; q <= r; ++q) MS(tri(r) + q) = fma(-MS(tri(r) + c), MS(tri(q) + c), MS(tri(r) + q));
+            }
+            if (spd) {
+                for (int r = 0; r < m; ++r) GS(r) = 0.0;
+                GS(m - 1) = 1.0 / MS(tri(m - 1) + m - 1);
+                for (int c = m - 1; c >= 0; --c) {
+                    const double gc = GS(c) / MS(tri(c) + c);
+                    GS(c) = gc;
+                    for (int r = 0; r < c; ++r) GS(r) = fma(-MS(tri(c) + r), gc, GS(r));
+                }
+            }
+        } else {
+            for (int t = 0; t < tm; ++t) LF(t) = static_cast<float>(MS(t));
+            for (int c = 0; c < m && spd; ++c) {
+                const float piv = LF(tri(c) + c);
+                if (!positive(piv)) {
+                    spd = false;
+                    break;
+                }
+                const float d = sqrtf(piv);
+                LF(tri(c) + c) = d;
+                for (int r = c + 1; r < m; ++r) LF(tri(r) + c) = LF(tri(r) + c) / d;
+                for (int r = c + 1; r < m; ++r)
+                    for (int q = c + 1; q <= r; ++q) LF(tri(r) + q) = fmaf(-LF(tri(r) + c), LF(tri(q) + c), LF(tri(r) + q));
+            }
+            if (spd) {
+                // x = L^{-T} L^{-1} e_m in FP32
+                for (int r = 0; r < m; ++r) XF(r) = 0.0f;
+                XF(m - 1) = 1.0f / LF(tri(m - 1) + m - 1);
+                for (int c = m - 1; c >= 0; --c) {
+                    const float gc = XF(c) / LF(tri(c) + c);
+                    XF(c) = gc;
+                    for (int r = 0; r < c; ++r) XF(r) = fmaf(-LF(tri(c) + r), gc, XF(r));
+                }
+                for (int r = 0; r < m; ++r) GS(r) = static_cast<double>(XF(r));
+                // one FP64 refinement step
+                for (int r = 0; r < m; ++r) {
+                    double acc = (r == m - 1) ? 1.0 : 0.0;
+                    for (int q = 0; q < m; ++q) {
+                        const double arq = (q <= r) ? MS(tri(r) + q) : MS(tri(q) + r);
+                        acc = fma(-arq, GS(q), acc);
+                    }
+                    XF(r) = static_cast<float>(acc);
+                }
+                for (int c = 0; c < m; ++c) {
+                    const float zc = XF(c) / LF(tri(c) + c);
+                    XF(c) = zc;
+                    for (int r = c + 1; r < m; ++r) XF(r) = fmaf(-LF(tri(r) + c), zc, XF(r));
+                }
+                for (int c = m - 1; c >= 0; --c) {
+                    const float gc = XF(c) / LF(tri(c) + c);
+                    XF(c) = gc;
+                    for (int r = 0; r < c; ++r) XF(r) = fmaf(-LF(tri(c) + r), gc, XF(r));
+                }
+                for (int r = 0; r < m; ++r) GS(r) = GS(r) + static_cast<double>(XF(r));
+            }
+        }
+        if (!spd) {
+            a.st[ii] = kRowNotSpd;
+            continue;
+        }
+        const double psi = 1.0 / GS(m - 1);
+        const double psi_prev = a.psi[ii];
+        const bool stop = (a.exit_mode == 0) ? ((psi_prev - psi) < a.eps * psi_prev) : ((psi / a.psi0[ii]) <= a.eps);
+        a.psi[ii] = psi;
+        for (int r = 0; r < m; ++r) a.g[ii * a.mc + r] = GS(r);
+        a.st[ii] = stop ? kStStop : kStActive;
+    }
+#undef MS
+#undef GS
+#undef LF
+#undef XF
+}
+
+// Final scaling and output slots (same layout as the fused kernel).
+__global__ void step_finish(StepArgs a, SetupArgs o) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < a.n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int32_t stv = a.st[i];
+        if (stv == kStActive || stv == kStStop) {
+            const int m = a.m[i];
+            const double sq = sqrt(a.g[i * a.mc + m - 1]);
+            for (int t = 0; t < m; ++t) {
+                o.out_col[i * o.mcap + t] = a.P[i * a.mc + t];
+                o.out_val[i * o.mcap + t] = a.g[i * a.mc + t] / sq;
+            }
+            o.out_len[i] = m;
+            o.psi[i] = a.psi[i];
+            o.steps[i] = a.steps[i];
+            o.status[i] = kRowOk;
+        } else {
+            o.out_len[i] = 0;
+            o.status[i] = stv;
+            if (stv == kRowOverflow) {
+                const int32_t slot = atomicAdd(&o.counters[0], 1);
+                o.retry_rows[slot] = static_cast<int32_t>(i);
+            } else {
+                atomicAdd(&o.counters[1], 1);
+            }
+        }
+    }
+}
+
+template <int MC, int HT, bool CHOL32>
+afsai_status run_stepwise_t(const SetupArgs& o, int32_t kiter, cudaStream_t st) {
+    const int32_t n = o.n;
+    constexpr int TMC = MC * (MC + 1) / 2;
+    DevBuf<int32_t> P, mm, steps, stt;
+    DevBuf<double> g, M, psi, psi0;
+    AFSAI_TRY(P.alloc(static_cast<size_t>(n) * MC, st));
+    AFSAI_TRY(g.alloc(static_cast<size_t>(n) * MC, st));
+    AFSAI_TRY(M.alloc(static_cast<size_t>(n) * TMC, st));
+    AFSAI_TRY(mm.alloc(n, st));
+    AFSAI_TRY(steps.alloc(n, st));
+    AFSAI_TRY(stt.alloc(n, st));
+    AFSAI_TRY(psi.alloc(n, st));
+    AFSAI_TRY(psi0.alloc(n, st));
+    StepArgs a{};
+    a.n = n;
+    a.rowptr = o.rowptr;
+    a.col = o.col;
+    a.val = o.val;
+    a.s = o.s;
+    a.exit_mode = o.exit_mode;
+    a.eps = o.eps;
+    a.mc = MC;
+    a.tmc = TMC;
+    a.P = P.p;
+    a.g = g.p;
+    a.M = M.p;
+    a.m = mm.p;
+    a.steps = steps.p;
+    a.st = stt.p;
+    a.psi = psi.p;
+    a.psi0 = psi0.p;
+    const int vec_blocks = std::max(1, std::min(ceil_div(n, 256), num_sms() * 8));
+    step_init<<<vec_blocks, 256, 0, st>>>(a);
+    AFSAI_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    // gather kernel: 8 warps per block
+    auto kg = step_gather<MC, HT>;
+    const size_t smem_g = sizeof(GatherWs<MC, HT>) * 8;
+    AFSAI_CUDA_TRY(cudaFuncSetAttribute(kg, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_g)));
+    int per_sm_g = 0;
+    AFSAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_g, kg, 256, smem_g));
+    const int blocks_g = std::max(1, std::min(per_sm_g * num_sms(), ceil_div(n, 8)));
+    // solve kernel: lane-interleaved systems, 1 or 2 warps per block
+    auto ks = step_solve<MC, CHOL32>;
+    const size_t per_warp = static_cast<size_t>(TMC + MC) * 32 * (sizeof(double) + (CHOL32 ? sizeof(float) : 0));
+    const int wpb = per_warp * 2 <= 200u * 1024u ? 2 : 1;
+    const size_t smem_s = per_warp * wpb;
+    AFSAI_CUDA_TRY(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_s)));
+    int per_sm_s = 0;
+    AFSAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, ks, 32 * wpb, smem_s));
+    if (per_sm_s < 1 || per_sm_g < 1) return fail(AFSAI_ENOTSUP, "stepwise set-up does not fit in shared memory");
+    const int blocks_s = std::max(1, std::min(per_sm_s * num_sms(), ceil_div(ceil_div(n, 32), wpb)));
+    for (int32_t k = 1; k <= kiter; ++k) {
+        kg<<<blocks_g, 256, smem_g, st>>>(a);
+        ks<<<blocks_s, 32 * wpb, smem_s, st>>>(a);
+        AFSAI_CUDA_TRY(cudaGetLastError());
+        count_launches(2);
+    }
+    step_finish<<<vec_blocks, 256, 0, st>>>(a, o);
+    AFSAI_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return AFSAI_OK;
+}
+
+// Pattern capacities served by the stepwise path.
+int stepwise_max() {
+    static const int v = [] {
+        const char* e = std::getenv("AFSAI_STEPWISE_MAX");
+        const int k = e ? std::atoi(e) : 0;
+        return k == 32 ? 32 : 20;
+    }();
+    return v;
+}
+bool stepwise_supported(int64_t mcap) { return mcap <= stepwise_max(); }
+
+afsai_status run_stepwise(const SetupArgs& o, int64_t mcap, int ht, int32_t kiter, bool chol32, cudaStream_t st) {
+    if (mcap <= 12) {
+        if (ht == 256)
+            return chol32 ? run_stepwise_t<12, 256, true>(o, kiter, st) : run_stepwise_t<12, 256, false>(o, kiter, st);
+        return chol32 ? run_stepwise_t<12, 512, true>(o, kiter, st) : run_stepwise_t<12, 512, false>(o, kiter, st);
+    }
+    if (mcap <= 16) {
+        if (ht == 256)
+            return chol32 ? run_stepwise_t<16, 256, true>(o, kiter, st) : run_stepwise_t<16, 256, false>(o, kiter, st);
+        return chol32 ? run_stepwise_t<16, 512, true>(o, kiter, st) : run_stepwise_t<16, 512, false>(o, kiter, st);
+    }
+    if (mcap <= 20) {
+        if (ht == 256)
+            return chol32 ? run_stepwise_t<20, 256, true>(o, kiter, st) : run_stepwise_t<20, 256, false>(o, kiter, st);
+        return chol32 ? run_stepwise_t<20, 512, true>(o, kiter, st) : run_stepwise_t<20, 512, false>(o, kiter, st);
+    }
+    if (chol32) return fail(AFSAI_ENOTSUP, "stepwise path: FP32 factorisation up to 20 entries");
+    return ht == 256 ? run_stepwise_t<32, 256, false>(o, kiter, st) : run_stepwise_t<32, 512, false>(o, kiter, st);
+}
+
 int lanes_per_row(int mcap_t, bool chol32) {
     (void)mcap_t;
     (void)chol32;
@@ -696,13 +1163,14 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
     const int32_t n = A->n;
     const int64_t mcap = 1 + static_cast<int64_t>(p->kiter) * p->s;
     if (mcap > 128) return fail(AFSAI_ENOTSUP, "1 + kiter*s must be <= 128");
-    const int mcap_t = mcap <= 16 ? 16 : (mcap <= 32 ? 32 : (mcap <= 64 ? 64 : 128));
+    const int mcap_t = mcap <= 16 ? 16 : (mcap <= 20 ? 20 : (mcap <= 32 ? 32 : (mcap <= 64 ? 64 : 128)));
     // Shared table size: candidates are bounded by |P| * (longest row); the
     // table keeps a load factor <= 3/4 up to that bound, else it relies on
     // the overflow retry.
     const int64_t cand_bound = mcap * static_cast<int64_t>(max_row_nnz);
     int ht = 512;
     if (mcap_t <= 32 && cand_bound * 8 <= 256 * 7) ht = 256;
+    // (20-entry patterns use the 20-entry workspace template)
     const bool chol32 = p->chol_prec == 1;
     const int gl = lanes_per_row(mcap_t, chol32);
 
@@ -747,7 +1215,16 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
     AFSAI_CUDA_TRY(cudaEventCreate(&evk0));
     AFSAI_CUDA_TRY(cudaEventCreate(&evk1));
     AFSAI_CUDA_TRY(cudaEventRecord(evk0, st));
-    AFSAI_TRY(dispatch(mcap_t, ht, gl, a, n, INT64_MAX, false, chol32, st));
+    static const bool fused_only = [] {
+        const char* e = std::getenv("AFSAI_SETUP_FUSED_ONLY");
+        return e && std::atoi(e) != 0;
+    }();
+    // the stepwise path pays off where FP64 square roots and divisions
+    // dominate: FP64 factorisation of small patterns
+    if (!fused_only && stepwise_supported(mcap) && p->kiter > 0 && !chol32)
+        AFSAI_TRY(run_stepwise(a, mcap, ht, p->kiter, chol32, st));
+    else
+        AFSAI_TRY(dispatch(mcap_t, ht, gl, a, n, INT64_MAX, false, chol32, st));
     AFSAI_CUDA_TRY(cudaEventRecord(evk1, st));
 
     int32_t hc[4];

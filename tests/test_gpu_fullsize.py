@@ -1,0 +1,86 @@
+"""Full-size parity in the benchmark's launch configuration.
+
+The elasticity 48^3 solve (the benchmark workload) and the 256^3
+heterogeneous diffusion solve run at full size through the C ABI as
+bench.py runs them.  The oracle cannot redo every row at these sizes in a
+test, so it recomputes sampled rows one by one (the first rows, the last
+rows and seeded random row ranges): their patterns and FP64 values must be
+identical.  The solves are checked by properties that hold at any size:
+convergence to the true residual 1e-8, the oracle's iteration count +-1 for
+the elasticity case (the full oracle solve takes seconds there), and at most
+10% more iterations for the mixed form than for FP64."""
+import numpy as np
+import pytest
+
+from paper_2010_14175_gb300 import matgen as mg
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2010_14175_gb300 import afsai
+
+    afsai.load()
+    return afsai
+
+
+def _sample_ranges(n, seed, count=12, width=64):
+    rng = np.random.default_rng(seed)
+    starts = sorted(set([0, n - width] + list(rng.integers(0, n - width, size=count))))
+    return [(int(s), int(s) + width) for s in starts]
+
+
+def _check_rows(oracle_mod, A, p, rp, ci, va, psi, steps, ranges):
+    for r0, r1 in ranges:
+        ref = oracle_mod.afsai_setup(A, p["kiter"], p["s"], p["eps"], rows=(r0, r1), nthreads=1)
+        a, b = rp[r0], rp[r1]
+        assert np.array_equal(np.diff(rp[r0:r1 + 1]), np.diff(ref.rowptr)), (r0, r1)
+        assert np.array_equal(ci[a:b], ref.col), (r0, r1)
+        assert np.array_equal(va[a:b], ref.val), (r0, r1)
+        assert np.array_equal(psi[r0:r1], ref.psi) and np.array_equal(steps[r0:r1], ref.steps)
+
+
+def _solve(afsai, A, b, p, g_prec=0, chol_prec=0):
+    import torch
+
+    Ad = afsai.DeviceCSR.from_host(A)
+    M = afsai.afsai_setup(Ad, afsai.params(p["kiter"], p["s"], p["eps"], 0, g_prec, chol_prec))
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    info = afsai.pcg_solve(Ad, M, bd, x, rtol=1e-8, maxit=20000)
+    return M, info, x
+
+
+def test_elasticity48_full_size(gpu, oracle_mod):
+    A, b, xs, p = mg.workload("elast48")
+    M, info, x = _solve(gpu, A, b, p)
+    rp, ci, va = M.export()
+    psi, steps = M.rows()
+    _check_rows(oracle_mod, A, p, rp, ci, va, psi, steps, _sample_ranges(A.n, 1))
+    assert info["converged"] == 1 and info["relres_true"] <= 1.05e-8
+    # full oracle solve (set-up + PCG) for the iteration count
+    G = oracle_mod.afsai_setup(A, p["kiter"], p["s"], p["eps"])
+    assert G.nnz == M.info()["nnz_G"]
+    _, it_o, _, _ = oracle_mod.pcg(A, G, b, rtol=1e-8, maxit=20000)
+    assert abs(info["iters"] - it_o) <= 1, (info["iters"], it_o)
+    # mixed form on the same input
+    _, im, _ = _solve(gpu, A, b, p, 1, 1)
+    assert im["relres_true"] <= 1.05e-8 and im["iters"] <= int(np.ceil(1.10 * info["iters"]))
+
+
+def test_hetero256_full_size(gpu, oracle_mod):
+    A, b, xs, p = mg.workload("hetero256")
+    M, info, x = _solve(gpu, A, b, p)
+    rp, ci, va = M.export()
+    psi, steps = M.rows()
+    _check_rows(oracle_mod, A, p, rp, ci, va, psi, steps, _sample_ranges(A.n, 2, count=8, width=256))
+    assert info["converged"] == 1 and info["relres_true"] <= 1.05e-8
+    M.close()
+    for g_prec, chol_prec in ((1, 1), (1, 0)):
+        _, im, _ = _solve(gpu, A, b, p, g_prec, chol_prec)
+        assert im["relres_true"] <= 1.05e-8
+        assert im["iters"] <= int(np.ceil(1.10 * info["iters"])), (g_prec, chol_prec, im["iters"], info["iters"])
