@@ -44,7 +44,7 @@ if ROOT not in sys.path:
 
 METRIC = "aFSAI set-up+PCG s/solve to relres 1e-8 (FP64; mixed reported beside)"
 WORKLOAD_NAMES = {"elast48": "elasticity_hex48", "hetero256": "hetero_diffusion7_256", "poisson20": "poisson7_20",
-                  "batch512": "batch_uneven", "serve": "serve_poisson_arrivals"}
+                  "batch512": "batch_uneven", "serve": "serve_poisson_arrivals", "poisson_sweep": "poisson7_sweep"}
 # precision forms: storage/arithmetic of G and of the row Cholesky solves
 FORMS = {
     "fp64": dict(g_prec=0, chol_prec=0, desc="FP64 G, FP64 Cholesky"),
@@ -93,7 +93,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the other precision forms")
     ap.add_argument("--workload", default="elast48",
-                    choices=["elast48", "hetero256", "poisson20", "batch512", "serve"])
+                    choices=["elast48", "hetero256", "poisson20", "batch512", "serve", "poisson_sweep"])
     ap.add_argument("--requests", type=int, default=2000, help="timed requests of the serve workload")
     ap.add_argument("--warm-requests", type=int, default=200)
     ap.add_argument("--nsys", type=int, default=512, help="systems of the batch512 workload")
@@ -540,6 +540,57 @@ def run_serve(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_sweep(args, rank, world, local):
+    """Single-GPU size sweep of the 7-point Poisson problem (the analogue of
+    the paper's weak-scaling study, which keeps 121^3 = 1,771,561 rows per
+    GPU): set-up time per row and PCG time per iteration against n, FP64
+    and mixed forms.  The JSON line's value is the s/solve of the 121^3 case."""
+    import torch
+
+    from paper_2010_14175_gb300 import afsai, matgen as mg
+
+    torch.cuda.set_device(local)
+    afsai.load()
+    rows = []
+    value = None
+    for N in (32, 64, 96, 121, 160, 200):
+        A = mg.poisson7(N)
+        b, _ = mg.rhs(A, mg.BASE_SEED + N)
+        Ad = afsai.DeviceCSR.from_host(A)
+        bd = torch.from_numpy(b).cuda()
+        x = torch.zeros_like(bd)
+        rec = {"N": N, "n": A.n}
+        for form in ("fp64", "mixed"):
+            f = FORMS[form]
+            prm = afsai.params(5, 2, 1e-3, 0, f["g_prec"], f["chol_prec"])
+            ts, ss, its = [], [], []
+            for rep in range(args.warmup + args.steps):
+                x.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                M = afsai.afsai_setup(Ad, prm)
+                inf = afsai.pcg_solve(Ad, M, bd, x, rtol=1e-8, maxit=20000)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                if rep >= args.warmup:
+                    ts.append(t1 - t0)
+                    ss.append(M.info()["setup_ms"])
+                    its.append(inf)
+                M.close()
+            rec[form] = {"s_per_solve": float(np.median(ts)), "setup_ns_per_row": float(np.median(ss)) * 1e6 / A.n,
+                         "iters": its[-1]["iters"], "us_per_iter": its[-1]["solve_ms"] * 1e3 / max(1, its[-1]["iters"]),
+                         "relres_true": its[-1]["relres_true"]}
+        rows.append(rec)
+        if N == 121:
+            value = rec["fp64"]["s_per_solve"]
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "value": value, "unit": "s/solve", "n_gpus": world, "steps": args.steps,
+                          "warmup": args.warmup, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                          "dtype": "f64", "data": "synthetic (7-point Poisson, Dirichlet)",
+                          "config": {"workload": "poisson7_sweep", "kiter": 5, "s": 2, "eps": 1e-3, "rtol": 1e-8},
+                          "sweep": rows, "roofline": None, "e2e": None, "cpu_baseline": None}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_init(args)
@@ -551,6 +602,9 @@ def main():
         return
     if args.workload == "serve":
         run_serve(args, rank, world, local)
+        return
+    if args.workload == "poisson_sweep":
+        run_sweep(args, rank, world, local)
         return
     import torch
 
@@ -638,7 +692,7 @@ def main():
     if not args.no_mixed:
         names = args.extra_forms.split(",") if args.extra_forms else (
             ["g32", "bf16", "mixed", "jacobi"] if args.workload == "hetero256" else ["mixed", "jacobi"])
-        for form in [f for f in names if f and f != args.form]:
+        for form in [f for f in names if f and f != args.form and f != "none"]:
             pf = prm_of(form)
             for _ in range(2):
                 Mm, sm_, pm_ = one_solve(pf)

@@ -173,17 +173,51 @@ __global__ void k_spmv_A_dot(int32_t n, int64_t nnz, const int32_t* __restrict__
 }
 
 // ---- x += alpha p, r -= alpha q, rr = r.r, convergence --------------------
+// Pairs of elements per load (16-byte aligned vectors), several pairs per
+// thread in flight; the per-thread dot partial runs over its elements in
+// index order.
 __global__ void k_update_xr(int32_t n, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
                             const double* __restrict__ q, Scalars* s, double* partials) {
     if (s->done) return;
     const double alpha = s->alpha;
     double v[1] = {0.0};
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        x[i] = fma(alpha, p[i], x[i]);
-        const double ri = fma(-alpha, q[i], r[i]);
-        r[i] = ri;
-        v[0] = fma(ri, ri, v[0]);
+    const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t nth = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(r) |
+                           reinterpret_cast<uintptr_t>(p) | reinterpret_cast<uintptr_t>(q)) & 15u) == 0;
+    if (aligned) {
+        const int64_t n2 = n / 2;
+        auto* x2 = reinterpret_cast<double2*>(x);
+        auto* r2 = reinterpret_cast<double2*>(r);
+        const auto* p2 = reinterpret_cast<const double2*>(p);
+        const auto* q2 = reinterpret_cast<const double2*>(q);
+#pragma unroll 4
+        for (int64_t k = tid; k < n2; k += nth) {
+            double2 xv = x2[k], rv = r2[k];
+            const double2 pv = p2[k], qv = q2[k];
+            xv.x = fma(alpha, pv.x, xv.x);
+            xv.y = fma(alpha, pv.y, xv.y);
+            rv.x = fma(-alpha, qv.x, rv.x);
+            rv.y = fma(-alpha, qv.y, rv.y);
+            x2[k] = xv;
+            r2[k] = rv;
+            v[0] = fma(rv.x, rv.x, v[0]);
+            v[0] = fma(rv.y, rv.y, v[0]);
+        }
+        if ((n & 1) && tid == 0) {
+            const int64_t i = n - 1;
+            x[i] = fma(alpha, p[i], x[i]);
+            const double ri = fma(-alpha, q[i], r[i]);
+            r[i] = ri;
+            v[0] = fma(ri, ri, v[0]);
+        }
+    } else {
+        for (int64_t i = tid; i < n; i += nth) {
+            x[i] = fma(alpha, p[i], x[i]);
+            const double ri = fma(-alpha, q[i], r[i]);
+            r[i] = ri;
+            v[0] = fma(ri, ri, v[0]);
+        }
     }
     if (grid_sum<1>(v, partials, &s->ticket[3]) && threadIdx.x == 0) {
         s->rr = v[0];
@@ -232,9 +266,24 @@ __global__ void k_spmv_Gt_dot(int32_t n, int64_t nnz, const int32_t* __restrict_
 __global__ void k_update_p(int32_t n, const double* __restrict__ z, double* __restrict__ p, const Scalars* s) {
     if (s->done) return;
     const double beta = s->beta;
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        p[i] = fma(beta, p[i], z[i]);
+    const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t nth = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    if (((reinterpret_cast<uintptr_t>(z) | reinterpret_cast<uintptr_t>(p)) & 15u) == 0) {
+        const int64_t n2 = n / 2;
+        auto* p2 = reinterpret_cast<double2*>(p);
+        const auto* z2 = reinterpret_cast<const double2*>(z);
+#pragma unroll 4
+        for (int64_t k = tid; k < n2; k += nth) {
+            double2 pv = p2[k];
+            const double2 zv = z2[k];
+            pv.x = fma(beta, pv.x, zv.x);
+            pv.y = fma(beta, pv.y, zv.y);
+            p2[k] = pv;
+        }
+        if ((n & 1) && tid == 0) p[n - 1] = fma(beta, p[n - 1], z[n - 1]);
+    } else {
+        for (int64_t i = tid; i < n; i += nth) p[i] = fma(beta, p[i], z[i]);
+    }
 }
 
 // ---- identity preconditioner (M = NULL): z = r, rz' = r.r ------------------
@@ -290,6 +339,8 @@ bool with_mode(int mode, F f) {
         case 2: f(std::integral_constant<int, 2>{}); return true;
         case 4: f(std::integral_constant<int, 4>{}); return true;
         case 8: f(std::integral_constant<int, 8>{}); return true;
+        case 3: f(std::integral_constant<int, 3>{}); return true;
+        case 6: f(std::integral_constant<int, 6>{}); return true;
         case 101: f(std::integral_constant<int, 101>{}); return true;
         case 102: f(std::integral_constant<int, 102>{}); return true;
         default: return false;
@@ -405,7 +456,8 @@ afsai_status pcg_body(const CsrDev& A, const afsai_precond* M, const double* b, 
     const int32_t n = A.n;
     DevBuf<double> vec, partials, trueres;
     DevBuf<Scalars> sc;
-    AFSAI_TRY(vec.alloc(static_cast<size_t>(n) * 5, st));
+    const size_t vs = (static_cast<size_t>(n) + 31) / 32 * 32;  // 256-byte aligned vector stride
+    AFSAI_TRY(vec.alloc(vs * 5, st));
     AFSAI_TRY(partials.alloc(static_cast<size_t>(num_sms()) * 64, st));
     AFSAI_TRY(sc.alloc(1, st));
     AFSAI_TRY(trueres.alloc(1, st));
@@ -419,10 +471,10 @@ afsai_status pcg_body(const CsrDev& A, const afsai_precond* M, const double* b, 
     L.x = x;
     L.b = b;
     L.r = vec.p;
-    L.p = vec.p + n;
-    L.q = vec.p + 2 * static_cast<size_t>(n);
-    L.z = vec.p + 3 * static_cast<size_t>(n);
-    L.t = vec.p + 4 * static_cast<size_t>(n);
+    L.p = vec.p + vs;
+    L.q = vec.p + 2 * vs;
+    L.z = vec.p + 3 * vs;
+    L.t = vec.p + 4 * vs;
     L.s = sc.p;
     L.partials = partials.p;
     L.st = st;

@@ -343,7 +343,8 @@ bool make_mode(int mode, const CsrDev& C, SpmvMode* m) {
         return true;
     }
     m->threads = 256;
-    m->blocks = grid_for(static_cast<int64_t>(C.n) * mode, 256);
+    const int64_t lanes = (mode == 3 || mode == 6) ? static_cast<int64_t>(C.n) * 32 / (32 / mode) : static_cast<int64_t>(C.n) * mode;
+    m->blocks = grid_for(lanes, 256);
     m->smem = 0;
     m->cap = 0;
     return true;
@@ -368,6 +369,8 @@ afsai_status launch_plain(const SpmvMode& m, const CsrDev& C, const XT* x, YT* y
         case 2: return launch_plain_mode<2, VT, XT, ACC, YT>(m, C, x, y, st);
         case 4: return launch_plain_mode<4, VT, XT, ACC, YT>(m, C, x, y, st);
         case 8: return launch_plain_mode<8, VT, XT, ACC, YT>(m, C, x, y, st);
+        case 3: return launch_plain_mode<3, VT, XT, ACC, YT>(m, C, x, y, st);
+        case 6: return launch_plain_mode<6, VT, XT, ACC, YT>(m, C, x, y, st);
         case 101: return launch_plain_mode<101, VT, XT, ACC, YT>(m, C, x, y, st);
         case 102: return launch_plain_mode<102, VT, XT, ACC, YT>(m, C, x, y, st);
         default: return fail(AFSAI_EINVAL, "unknown SpMV mode");
@@ -431,7 +434,7 @@ afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode*
         return AFSAI_OK;
     }
     // time the candidates on this matrix
-    std::vector<int> cand = {2, 4, 8, 101, 102};
+    std::vector<int> cand = {2, 3, 4, 6, 8, 101, 102};
     if (avg <= 16.0) cand.insert(cand.begin(), 1);
     DevBuf<double> xb, yb;
     AFSAI_TRY(xb.alloc(static_cast<size_t>(C.n), st));

@@ -246,14 +246,51 @@ __device__ __forceinline__ void spmv_strided(int32_t n, const int32_t* __restric
     }
 }
 
+// Grouped rows: groups of L consecutive lanes (L not a power of two; the
+// last 32 mod L lanes of a warp idle), each group strides one row, partial
+// sums combined by a fixed tree of shuffles.  For rows whose length is a
+// multiple of L (81 = 27 x 3 for 3-dof elasticity) every lane does the same
+// number of fmas, so FP64 warp instructions stay full.
+template <int L, typename VT, typename XT, typename ACC, class Epi>
+__device__ __forceinline__ void spmv_grouped(int32_t n, const int32_t* __restrict__ rowptr,
+                                             const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                             const XT* __restrict__ x, Epi& epi) {
+    constexpr int G = 32 / L;  // groups per warp
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / L;
+    const int sub = lane - grp * L;
+    const bool live = grp < G;
+    const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    const int64_t nloop = (n + nwarp * G - 1) / (nwarp * G);
+    for (int64_t it = 0; it < nloop; ++it) {
+        const int64_t i = (warp + it * nwarp) * G + grp;
+        ACC acc = ACC(0);
+        if (live && i < n) {
+            const int32_t b = rowptr[i], e = rowptr[i + 1];
+            for (int32_t k = b + sub; k < e; k += L) acc = Mul<ACC>::fma_(__ldg(&val[k]), __ldg(&x[__ldg(&col[k])]), acc);
+        }
+#pragma unroll
+        for (int o = 1; o < L; o <<= 1) {
+            const ACC other = __shfl_down_sync(0xffffffffu, acc, o);
+            if ((sub & ((o << 1) - 1)) == 0 && sub + o < L) acc += other;
+        }
+        if (live && i < n && sub == 0) epi.row(i, acc);
+    }
+}
+
 // SpMV row engine.  MODE 1, 2, 4, 8: strided with MODE lanes per row;
-// MODE 101, 102: TMA-staged tiles with MODE - 100 threads per row.
+// MODE 3, 6: grouped with MODE lanes per row; MODE 101, 102: TMA-staged
+// tiles with MODE - 100 threads per row.
 template <int MODE, typename VT, typename XT, typename ACC, class Epi>
 __device__ __forceinline__ bool spmv_rows(int32_t n, int64_t nnz, const int32_t* __restrict__ rowptr,
                                           const int32_t* __restrict__ col, const VT* __restrict__ val,
                                           const XT* __restrict__ x, int cap, int32_t* errflag, Epi& epi) {
     if constexpr (MODE > 100) {
         return spmv_tiles<MODE - 100, VT, XT, ACC>(n, nnz, rowptr, col, val, x, cap, errflag, epi);
+    } else if constexpr (MODE == 3 || MODE == 6) {
+        spmv_grouped<MODE, VT, XT, ACC>(n, rowptr, col, val, x, epi);
+        return true;
     } else {
         spmv_strided<MODE, VT, XT, ACC>(n, rowptr, col, val, x, epi);
         return true;
