@@ -8,7 +8,8 @@ only builds it and marshals numpy arrays.
 
 Every function cites the part of the paper it follows:
   * ``afsai_setup``   - Section 2 (Eqs. "DensSys", "blocksys", "diagScal",
-    "kap2", "grapsi", "exit_crit").
+    "kap2", "grapsi", "exit_crit"); optional locality bound of Section 4
+    (stripe graph of G inside the lower part of Ahat^k).
   * ``row_trace``     - the same iteration for one row, step by step.
   * ``spmv``/``apply``- Eq. "prec": M^{-1} r = G^T (G r).
   * ``pcg``           - PCG with M^{-1} = G^T G, stopping at an 8-order
@@ -55,7 +56,8 @@ def _load():
             lib = ctypes.CDLL(path)
             P = ctypes.c_void_p
             i32, f64 = ctypes.c_int32, ctypes.c_double
-            lib.oracle_afsai_rows.argtypes = [i32, P, P, P, i32, i32, f64, i32, i32, i32, i32, P, P, P, P, P]
+            lib.oracle_afsai_rows.argtypes = [i32, P, P, P, i32, i32, f64, i32, i32, i32, i32, i32, i32, P, P, P, P,
+                                              P]
             lib.oracle_afsai_rows.restype = ctypes.c_int
             lib.oracle_afsai_row_trace.argtypes = [i32, P, P, P, i32, i32, f64, i32, i32, P, P, P, P, P]
             lib.oracle_afsai_row_trace.restype = ctypes.c_int
@@ -108,10 +110,14 @@ class OracleG:
         return sp.csr_matrix((self.val, self.col, self.rowptr), shape=(self.n, self.n))
 
 
-def afsai_setup(A, kiter: int, s: int, eps: float, exit_mode: int = 0, rows=None, nthreads: int = 0) -> OracleG:
+def afsai_setup(A, kiter: int, s: int, eps: float, exit_mode: int = 0, rows=None, nthreads: int = 0,
+                block_rows: int = 0, block_power: int = 1) -> OracleG:
     """aFSAI set-up (Section 2) for all rows, or for rows [r0, r1) when
     ``rows=(r0, r1)`` (the returned G then holds only those rows, with
-    row pointers relative to r0)."""
+    row pointers relative to r0).  ``block_rows > 0`` applies the locality
+    bound of the distributed set-up (Section 4): stripes of ``block_rows``
+    rows, candidates only from stripes allowed by the stripe adjacency raised
+    to ``block_power``."""
     lib = _load()
     rp, ci, va = _csr_args(A)
     r0, r1 = (0, A.n) if rows is None else rows
@@ -122,8 +128,8 @@ def afsai_setup(A, kiter: int, s: int, eps: float, exit_mode: int = 0, rows=None
     m = np.zeros(max(nr, 1), dtype=np.int32)
     psi = np.zeros(max(nr, 1), dtype=np.float64)
     steps = np.zeros(max(nr, 1), dtype=np.int32)
-    st = lib.oracle_afsai_rows(A.n, _p(rp), _p(ci), _p(va), kiter, s, float(eps), exit_mode, r0, r1, nthreads,
-                               _p(Gc), _p(Gv), _p(m), _p(psi), _p(steps))
+    st = lib.oracle_afsai_rows(A.n, _p(rp), _p(ci), _p(va), kiter, s, float(eps), exit_mode, int(block_rows),
+                               int(block_power), r0, r1, nthreads, _p(Gc), _p(Gv), _p(m), _p(psi), _p(steps))
     if st != OK:
         raise RuntimeError(f"oracle_afsai_rows failed with status {st}")
     m = m[:nr]

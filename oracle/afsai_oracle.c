@@ -44,6 +44,10 @@
  *       acc = fma(a_rj, g_r, acc) starting from acc = 0.
  *   R9  PCG: x0 = 0, stop when ||r_k||_2 <= rtol ||b||_2 for the recursive
  *       residual (Section 5.2: "reduce the initial residual of 8 orders").
+ *   R13 locality bound (Section 4): stripes are runs of block_rows
+ *       consecutive rows (the last one may be shorter); Ahat includes the
+ *       diagonal blocks; power 0 keeps each row inside its own stripe;
+ *       block_rows = 0 means no bound.
  */
 #include <math.h>
 #include <stdint.h>
@@ -140,6 +144,52 @@ static int solve_em(const csr_view* A, const int32_t* P, int32_t m, double* M, d
     return ORC_OK;
 }
 
+/*
+ * Locality bound of the distributed set-up (Section 4, "aFSAI set-up on a
+ * distributed memory computer").  The rows are cut into stripes of
+ * block_rows consecutive rows (one stripe per process there).  Ahat is the
+ * stripe adjacency of A (Ahat_IJ = 1 iff block (I, J) of A holds a
+ * nonzero) and the stripe graph of G must lie in the lower part of
+ * Ahat^power.  Each process gathers only the blocks of A among its allowed
+ * stripes, so a row i of stripe I can only ever see candidates j of stripes
+ * J with (Ahat^power)_IJ = 1 (and J <= I, which j < i already implies):
+ * filtering the candidates is the same computation as running on the
+ * gathered local matrix.  Returns the np x np table reach (1 = allowed),
+ * built by power-fold boolean products starting from the identity; NULL
+ * when out of memory.
+ */
+static uint8_t* block_reach(const csr_view* A, int32_t block_rows, int32_t power, int32_t* np_out) {
+    int32_t np = (int32_t)(((int64_t)A->n + block_rows - 1) / block_rows);
+    size_t nn = (size_t)np * (size_t)np;
+    uint8_t* ahat = (uint8_t*)calloc(nn, 1);
+    uint8_t* reach = (uint8_t*)calloc(nn, 1);
+    uint8_t* next = (uint8_t*)calloc(nn, 1);
+    if (!ahat || !reach || !next) {
+        free(ahat);
+        free(reach);
+        free(next);
+        return NULL;
+    }
+    for (int32_t r = 0; r < A->n; ++r)
+        for (int32_t e = A->rowptr[r]; e < A->rowptr[r + 1]; ++e)
+            ahat[(size_t)(r / block_rows) * np + A->col[e] / block_rows] = 1;
+    for (int32_t I = 0; I < np; ++I) reach[(size_t)I * np + I] = 1; /* Ahat^0 = identity */
+    for (int32_t t = 0; t < power; ++t) {
+        memset(next, 0, nn);
+        for (int32_t I = 0; I < np; ++I)
+            for (int32_t K = 0; K < np; ++K) {
+                if (!reach[(size_t)I * np + K]) continue;
+                for (int32_t J = 0; J < np; ++J)
+                    if (ahat[(size_t)K * np + J]) next[(size_t)I * np + J] = 1;
+            }
+        memcpy(reach, next, nn);
+    }
+    free(ahat);
+    free(next);
+    *np_out = np;
+    return reach;
+}
+
 /* Optional per-step trace of one row (for tests). */
 typedef struct {
     int32_t max_steps;
@@ -157,8 +207,8 @@ typedef struct {
  * enlargement steps performed.  Returns ORC_OK or ORC_ENOTSPD.
  */
 static int afsai_row(const csr_view* A, int32_t i, int32_t kiter, int32_t s, double eps, int32_t exit_mode,
-                     row_ws* w, int32_t* Gcol, double* Gval, int32_t* m_out, double* psi_out, int32_t* steps_out,
-                     row_trace* tr) {
+                     const uint8_t* reach, int32_t np, int32_t block_rows, row_ws* w, int32_t* Gcol, double* Gval,
+                     int32_t* m_out, double* psi_out, int32_t* steps_out, row_trace* tr) {
     double aii = diag_entry(A, i);
     if (!(aii > 0.0)) return ORC_ENOTSPD;
     int32_t m = 1;
@@ -183,6 +233,8 @@ static int afsai_row(const csr_view* A, int32_t i, int32_t kiter, int32_t s, dou
             for (int32_t e = A->rowptr[r]; e < A->rowptr[r + 1]; ++e) {
                 int32_t j = A->col[e];
                 if (j >= i) continue;
+                /* locality bound (block_reach): stripes outside the gathered set */
+                if (reach && !reach[(size_t)(i / block_rows) * np + j / block_rows]) continue;
                 if (!w->mark[j]) {
                     w->mark[j] = 1;
                     w->acc[j] = 0.0;
@@ -302,10 +354,18 @@ static int32_t max_row_nnz(const csr_view* A) {
  * (its m_out is then 0).  nthreads <= 0 uses the OpenMP default.
  */
 int oracle_afsai_rows(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val, int32_t kiter,
-                      int32_t s, double eps, int32_t exit_mode, int32_t row_begin, int32_t row_end, int32_t nthreads,
-                      int32_t* Gcol, double* Gval, int32_t* m_out, double* psi_out, int32_t* steps_out) {
+                      int32_t s, double eps, int32_t exit_mode, int32_t block_rows, int32_t block_power,
+                      int32_t row_begin, int32_t row_end, int32_t nthreads, int32_t* Gcol, double* Gval,
+                      int32_t* m_out, double* psi_out, int32_t* steps_out) {
     if (n <= 0 || kiter < 0 || s < 1 || row_begin < 0 || row_end > n || row_begin > row_end) return ORC_EINVAL;
+    if (block_rows < 0 || block_power < 0) return ORC_EINVAL;
     csr_view A = {n, rowptr, col, val};
+    uint8_t* reach = NULL;
+    int32_t np = 0;
+    if (block_rows > 0) {
+        reach = block_reach(&A, block_rows, block_power, &np);
+        if (!reach) return ORC_ENOMEM;
+    }
     int64_t mcap = 1 + (int64_t)kiter * s;
     int64_t candcap = mcap * (int64_t)max_row_nnz(&A) + 1;
     int status = ORC_OK;
@@ -329,8 +389,8 @@ int oracle_afsai_rows(int32_t n, const int32_t* rowptr, const int32_t* col, cons
 #endif
             for (int32_t i = row_begin; i < row_end; ++i) {
                 int64_t o = (int64_t)(i - row_begin);
-                int st = afsai_row(&A, i, kiter, s, eps, exit_mode, &w, Gcol + o * mcap, Gval + o * mcap, &m_out[o],
-                                   &psi_out[o], &steps_out[o], NULL);
+                int st = afsai_row(&A, i, kiter, s, eps, exit_mode, reach, np, block_rows, &w, Gcol + o * mcap,
+                                   Gval + o * mcap, &m_out[o], &psi_out[o], &steps_out[o], NULL);
                 if (st != ORC_OK) {
                     m_out[o] = 0;
 #ifdef _OPENMP
@@ -345,6 +405,7 @@ int oracle_afsai_rows(int32_t n, const int32_t* rowptr, const int32_t* col, cons
 #ifdef _OPENMP
     omp_set_num_threads(nt_before);
 #endif
+    free(reach);
     return status;
 }
 
@@ -370,7 +431,7 @@ int oracle_afsai_row_trace(int32_t n, const int32_t* rowptr, const int32_t* col,
     double* Gv = (double*)malloc(sizeof(double) * (size_t)mcap);
     int32_t mo, so;
     double po;
-    int st = afsai_row(&A, i, kiter, s, eps, exit_mode, &w, Gc, Gv, &mo, &po, &so, &tr);
+    int st = afsai_row(&A, i, kiter, s, eps, exit_mode, NULL, 0, 0, &w, Gc, Gv, &mo, &po, &so, &tr);
     *nsteps = tr.nsteps;
     free(Gc);
     free(Gv);
