@@ -54,6 +54,14 @@ FORMS = {
     # the paper's comparison preconditioner (Section 5.2): kiter = 0 keeps
     # the diagonal pattern, G^T G = diag(A)^{-1}
     "jacobi": dict(g_prec=0, chol_prec=0, kiter=0, desc="Jacobi (aFSAI with kiter = 0), FP64"),
+    # locality bound of the distributed set-up (Section 4): 64 row stripes,
+    # stripe graph of G inside lower(Ahat^k)
+    "local64k1": dict(g_prec=0, chol_prec=0, stripes=64, power=1,
+                      desc="FP64, candidates bounded to lower(Ahat^1) over 64 row stripes"),
+    "local64k2": dict(g_prec=0, chol_prec=0, stripes=64, power=2,
+                      desc="FP64, candidates bounded to lower(Ahat^2) over 64 row stripes"),
+    "local64k0": dict(g_prec=0, chol_prec=0, stripes=64, power=0,
+                      desc="FP64, candidates bounded to each row's own stripe of 64 (block-diagonal aFSAI)"),
 }
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
@@ -143,7 +151,11 @@ class ClockSampler:
     def __init__(self, gpu_index=0):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples: $BENCH_CLOCKS_DIR (default: the system temp folder)
+        import tempfile
+
+        self.path = os.path.join(os.environ.get("BENCH_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -622,7 +634,9 @@ def main():
 
     def prm_of(form):
         f = FORMS[form]
-        return afsai.params(f.get("kiter", p["kiter"]), p["s"], p["eps"], 0, f["g_prec"], f["chol_prec"])
+        br = -(-A.n // f["stripes"]) if "stripes" in f else 0
+        return afsai.params(f.get("kiter", p["kiter"]), p["s"], p["eps"], 0, f["g_prec"], f["chol_prec"], br,
+                            f.get("power", 1))
 
     def one_solve(prm_):
         x.zero_()

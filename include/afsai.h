@@ -80,7 +80,21 @@ typedef struct {
  *   chol_prec  0: FP64 Cholesky of every row system (bit-exact with the
  *              plain FP64 definition); 1: FP32 Cholesky followed by one
  *              FP64 iterative-refinement step.  The Kaporin gradient and the
- *              selection stay FP64 in both. */
+ *              selection stay FP64 in both.
+ *   block_rows, block_power
+ *              locality bound of the distributed set-up (Section 4, "aFSAI
+ *              set-up on a distributed memory computer"): with
+ *              block_rows > 0 the rows are cut into stripes of block_rows
+ *              consecutive rows (the last may be shorter), Ahat is the
+ *              stripe adjacency of A (Ahat_IJ = 1 iff block (I, J) holds a
+ *              nonzero) and a row of stripe I only takes candidates from
+ *              stripes J with (Ahat^block_power)_IJ = 1, so that the stripe
+ *              graph of G lies in the lower part of Ahat^block_power.
+ *              block_rows = 0: no bound (block_power is then ignored);
+ *              block_power in [0, 64], 0 keeps every row inside its own
+ *              stripe; at most 8192 stripes (else AFSAI_ENOTSUP).  Single
+ *              system set-ups only (the batched and served forms return
+ *              AFSAI_ENOTSUP for block_rows != 0). */
 typedef struct {
     int32_t kiter;
     int32_t s;
@@ -88,6 +102,8 @@ typedef struct {
     int32_t exit_mode;
     int32_t g_prec;
     int32_t chol_prec;
+    int32_t block_rows;
+    int32_t block_power;
 } afsai_params;
 
 /* Opaque preconditioner: G (lower triangular, CSR, sorted columns), its

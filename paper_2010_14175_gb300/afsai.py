@@ -48,7 +48,8 @@ class Csr(ctypes.Structure):
 
 class Params(ctypes.Structure):
     _fields_ = [("kiter", ctypes.c_int32), ("s", ctypes.c_int32), ("eps", ctypes.c_double),
-                ("exit_mode", ctypes.c_int32), ("g_prec", ctypes.c_int32), ("chol_prec", ctypes.c_int32)]
+                ("exit_mode", ctypes.c_int32), ("g_prec", ctypes.c_int32), ("chol_prec", ctypes.c_int32),
+                ("block_rows", ctypes.c_int32), ("block_power", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -193,8 +194,9 @@ class DeviceCSR:
         return Csr(self.n, self.nnz, self.rowptr.data_ptr(), self.col.data_ptr(), self.val.data_ptr())
 
 
-def params(kiter, s, eps, exit_mode=0, g_prec=0, chol_prec=0) -> Params:
-    return Params(int(kiter), int(s), float(eps), int(exit_mode), int(g_prec), int(chol_prec))
+def params(kiter, s, eps, exit_mode=0, g_prec=0, chol_prec=0, block_rows=0, block_power=1) -> Params:
+    return Params(int(kiter), int(s), float(eps), int(exit_mode), int(g_prec), int(chol_prec), int(block_rows),
+                  int(block_power))
 
 
 class Precond:

@@ -69,6 +69,8 @@ afsai_status check_params(const afsai_params* p) {
     if (p->g_prec < 0 || p->g_prec > 2) return fail(AFSAI_EINVAL, "g_prec must be 0, 1 or 2");
     if (p->chol_prec != 0 && p->chol_prec != 1) return fail(AFSAI_EINVAL, "chol_prec must be 0 or 1");
     if (1 + static_cast<int64_t>(p->kiter) * p->s > 128) return fail(AFSAI_ENOTSUP, "1 + kiter*s must be <= 128");
+    if (p->block_rows < 0) return fail(AFSAI_EINVAL, "block_rows must be >= 0");
+    if (p->block_power < 0 || p->block_power > 64) return fail(AFSAI_EINVAL, "block_power must be in [0, 64]");
     return AFSAI_OK;
 }
 

@@ -78,6 +78,11 @@ struct SetupArgs {
     double* __restrict__ gval;
     int32_t* __restrict__ glist;
     int32_t ght_log2;
+    // locality bound (Section 4): reach words of each stripe (nullptr: none)
+    const uint32_t* __restrict__ reach;
+    int32_t reach_words;
+    int32_t stripe_shift;
+    uint64_t stripe_magic;
 };
 
 template <int MCAP, int HT>
@@ -229,6 +234,54 @@ __device__ void group_llt_solve(const T* L, T* x, int m, bool em, int sub, unsig
     }
 }
 
+// Locality bound of the distributed set-up (Section 4): the rows are cut
+// into stripes of block_rows rows and a row of stripe I takes candidates
+// only from the stripes J whose bit is set in I's reach words (the stripe
+// adjacency of A raised to the chosen power).  J = j / block_rows by a
+// multiply-shift that is exact for 0 <= j < 2^31 (Granlund and Montgomery,
+// "Division by invariant integers using multiplication", 1994: magic =
+// floor(2^(31+l) / d) + 1 with l = ceil(log2 d), shift 31 + l).
+//
+// The gradient table still accumulates every column j < i; the bound then
+// zeroes the gradient of the columns outside the allowed stripes, which
+// makes them ineligible exactly as if they had been skipped (only
+// candidates with a nonzero gradient are ever taken, and the sums of the
+// allowed columns do not depend on the others).  This keeps the hot
+// accumulation loop free of the test.
+struct StripeBound {
+    const uint32_t* row = nullptr;  // reach words of the row's stripe; nullptr: no bound
+    uint64_t magic = 0;
+    int shift = 0;
+    __device__ __forceinline__ bool allows(int32_t j) const {
+        const uint32_t J = static_cast<uint32_t>((static_cast<uint64_t>(j) * magic) >> shift);
+        return (__ldg(&row[J >> 5]) >> (J & 31u)) & 1u;
+    }
+};
+
+__device__ __forceinline__ StripeBound stripe_bound(const uint32_t* reach, int32_t words, uint64_t magic, int shift,
+                                                    int32_t i) {
+    StripeBound b;
+    if (reach != nullptr) {
+        const uint32_t I = static_cast<uint32_t>((static_cast<uint64_t>(i) * magic) >> shift);
+        b.row = reach + static_cast<size_t>(I) * words;
+        b.magic = magic;
+        b.shift = shift;
+    }
+    return b;
+}
+
+// Zeroes the gradient of the table's columns outside the row's allowed
+// stripes (no-op without a bound).
+__device__ __forceinline__ void apply_stripe_bound(const StripeBound& bd, const int32_t* key, double* hv,
+                                                   const int32_t* list, int nk, int sub, int gl, unsigned gmask) {
+    if (bd.row == nullptr) return;
+    for (int t = sub; t < nk; t += gl) {
+        const int sl = list[t];
+        if (!bd.allows(key[sl])) hv[sl] = 0.0;
+    }
+    __syncwarp(gmask);
+}
+
 // Entries of one row of A held in registers: chunk q covers the entries
 // rb + sub + q*GL (up to NPF chunks; longer rows continue directly).  NPF is
 // 1 for short rows (small candidate tables), 4 otherwise, to keep the
@@ -310,6 +363,7 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
     double psi_prev = psi0;
     int steps = 0;
     int32_t status = positive(aii) ? kRowOk : kRowNotSpd;
+    const StripeBound bd = stripe_bound(a.reach, a.reach_words, a.stripe_magic, a.stripe_shift, i);
 
     for (int k = 1; k <= a.kiter && status == kRowOk; ++k) {
         // ---- Kaporin gradient over j < i (Eq. "grapsi") ----
@@ -350,6 +404,7 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
         }
         __syncwarp(gmask);
         const int nk = w.nkeys;
+        apply_stripe_bound(bd, key, hv, list, nk, sub, GL, gmask);
         // ---- select the s largest |gradient| (ties: smaller column) ----
         int npick = 0;
         for (int u = 0; u < a.s; ++u) {
@@ -723,6 +778,10 @@ struct StepArgs {
     int32_t* st;
     double* psi;
     double* psi0;
+    const uint32_t* reach;  // locality bound, as in SetupArgs
+    int32_t reach_words;
+    int32_t stripe_shift;
+    uint64_t stripe_magic;
 };
 
 __global__ void step_init(StepArgs a) {
@@ -814,8 +873,10 @@ __global__ void __launch_bounds__(256) step_gather(StepArgs a) {
             if (slot >= 0) w.val[slot] = 0.0;
         }
         __syncwarp();
-        // ---- select the s largest |gradient| (ties: smaller column) ----
         const int nk = w.nkeys;
+        apply_stripe_bound(stripe_bound(a.reach, a.reach_words, a.stripe_magic, a.stripe_shift, i), w.key, w.val,
+                           w.list, nk, sub, GL, gmask);
+        // ---- select the s largest |gradient| (ties: smaller column) ----
         int npick = 0;
         for (int u = 0; u < a.s; ++u) {
             unsigned long long best = 0ull;
@@ -1086,6 +1147,10 @@ afsai_status run_stepwise_t(const SetupArgs& o, int32_t kiter, cudaStream_t st) 
     a.st = stt.p;
     a.psi = psi.p;
     a.psi0 = psi0.p;
+    a.reach = o.reach;
+    a.reach_words = o.reach_words;
+    a.stripe_shift = o.stripe_shift;
+    a.stripe_magic = o.stripe_magic;
     const int vec_blocks = std::max(1, std::min(ceil_div(n, 256), num_sms() * 8));
     step_init<<<vec_blocks, 256, 0, st>>>(a);
     AFSAI_CUDA_TRY(cudaGetLastError());
@@ -1150,6 +1215,112 @@ afsai_status run_stepwise(const SetupArgs& o, int64_t mcap, int ht, int32_t kite
     return ht == 256 ? run_stepwise_t<32, 256, false>(o, kiter, st) : run_stepwise_t<32, 512, false>(o, kiter, st);
 }
 
+// ---------------------------------------------------------------------------
+// Locality bound (Section 4): stripe adjacency Ahat of A and its boolean
+// powers, as bit rows of `words` 32-bit words per stripe.
+// ---------------------------------------------------------------------------
+constexpr int64_t kMaxStripes = 8192;
+
+__device__ __forceinline__ uint32_t stripe_of(int32_t j, uint64_t magic, int shift) {
+    return static_cast<uint32_t>((static_cast<uint64_t>(j) * magic) >> shift);
+}
+
+// bit (I, J) of ahat set iff block (I, J) of A holds a nonzero; one thread
+// per row, a word is or-ed only when the stripe of the (sorted) columns
+// changes
+__global__ void k_stripe_adjacency(int32_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                   uint64_t magic, int shift, int32_t words, uint32_t* __restrict__ ahat) {
+    for (int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n;
+         r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        uint32_t* row = ahat + static_cast<size_t>(stripe_of(static_cast<int32_t>(r), magic, shift)) * words;
+        uint32_t last = 0xffffffffu;
+        for (int32_t e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+            const uint32_t J = stripe_of(col[e], magic, shift);
+            if (J != last) {
+                atomicOr(&row[J >> 5], 1u << (J & 31u));
+                last = J;
+            }
+        }
+    }
+}
+
+__global__ void k_stripe_identity(int32_t nb, int32_t words, uint32_t* __restrict__ r) {
+    for (int64_t I = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; I < nb;
+         I += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        r[static_cast<size_t>(I) * words + (I >> 5)] = 1u << (I & 31);
+}
+
+// next[I] = OR over the stripes K set in cur[I] of ahat[K] (one boolean
+// product); one block per stripe I, threads over the output words
+__global__ void k_stripe_power(int32_t nb, int32_t words, const uint32_t* __restrict__ cur,
+                               const uint32_t* __restrict__ ahat, uint32_t* __restrict__ next) {
+    for (int32_t I = blockIdx.x; I < nb; I += gridDim.x) {
+        const uint32_t* cr = cur + static_cast<size_t>(I) * words;
+        for (int32_t w = threadIdx.x; w < words; w += blockDim.x) {
+            uint32_t acc = 0u;
+            for (int32_t wk = 0; wk < words; ++wk) {
+                uint32_t bits = cr[wk];
+                while (bits) {
+                    const int b = __ffs(bits) - 1;
+                    bits &= bits - 1u;
+                    acc |= ahat[static_cast<size_t>(wk * 32 + b) * words + w];
+                }
+            }
+            next[static_cast<size_t>(I) * words + w] = acc;
+        }
+    }
+}
+
+// Fills the bound fields of `a`; `buf` holds the reach rows until the
+// set-up ends.  No bound for block_rows = 0 or a single stripe.
+afsai_status build_stripe_reach(const afsai_csr* A, const afsai_params* p, cudaStream_t st, SetupArgs* a,
+                                DevBuf<uint32_t>* buf) {
+    a->reach = nullptr;
+    a->reach_words = 0;
+    a->stripe_magic = 0;
+    a->stripe_shift = 0;
+    if (p->block_rows <= 0) return AFSAI_OK;
+    const int64_t nb = (static_cast<int64_t>(A->n) + p->block_rows - 1) / p->block_rows;
+    if (nb <= 1) return AFSAI_OK;
+    if (nb > kMaxStripes) return fail(AFSAI_ENOTSUP, "more than 8192 stripes in the locality bound");
+    const int32_t words = static_cast<int32_t>((nb + 31) / 32);
+    // multiply-shift division by block_rows, exact for 0 <= j < 2^31
+    int l = 0;
+    while ((int64_t(1) << l) < p->block_rows) ++l;
+    const uint64_t magic = ((uint64_t(1) << (31 + l)) / static_cast<uint64_t>(p->block_rows)) + 1u;
+    const int shift = 31 + l;
+    const size_t cells = static_cast<size_t>(nb) * words;
+    DevBuf<uint32_t> ahat, tmp;
+    AFSAI_TRY(ahat.alloc(cells, st));
+    AFSAI_TRY(tmp.alloc(cells, st));
+    AFSAI_TRY(buf->alloc(cells, st));
+    AFSAI_CUDA_TRY(cudaMemsetAsync(ahat.p, 0, cells * sizeof(uint32_t), st));
+    AFSAI_CUDA_TRY(cudaMemsetAsync(buf->p, 0, cells * sizeof(uint32_t), st));
+    const int rb = std::max(1, std::min(ceil_div(A->n, 256), num_sms() * 8));
+    k_stripe_adjacency<<<rb, 256, 0, st>>>(A->n, A->rowptr, A->col, magic, shift, words, ahat.p);
+    const int ib = std::max(1, std::min(ceil_div(nb, 256), num_sms() * 8));
+    k_stripe_identity<<<ib, 256, 0, st>>>(static_cast<int32_t>(nb), words, buf->p);
+    AFSAI_CUDA_TRY(cudaGetLastError());
+    count_launches(2);
+    uint32_t* cur = buf->p;
+    uint32_t* nxt = tmp.p;
+    for (int32_t t = 0; t < p->block_power; ++t) {
+        const int pb = static_cast<int>(std::min<int64_t>(nb, static_cast<int64_t>(num_sms()) * 16));
+        k_stripe_power<<<pb, 128, 0, st>>>(static_cast<int32_t>(nb), words, cur, ahat.p, nxt);
+        AFSAI_CUDA_TRY(cudaGetLastError());
+        count_launches(1);
+        std::swap(cur, nxt);
+    }
+    if (cur != buf->p)
+        AFSAI_CUDA_TRY(cudaMemcpyAsync(buf->p, cur, cells * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+    a->reach = buf->p;
+    a->reach_words = words;
+    a->stripe_magic = magic;
+    a->stripe_shift = shift;
+    // ahat and tmp are freed in stream order after the kernels that read them
+    return AFSAI_OK;
+}
+
 int lanes_per_row(int mcap_t, bool chol32) {
     (void)mcap_t;
     (void)chol32;
@@ -1211,6 +1382,8 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
     a.nrows = n;
     a.retry_rows = retry.p;
     a.counters = counters.p;
+    DevBuf<uint32_t> reach;
+    AFSAI_TRY(build_stripe_reach(A, p, st, &a, &reach));
     cudaEvent_t evk0, evk1;
     AFSAI_CUDA_TRY(cudaEventCreate(&evk0));
     AFSAI_CUDA_TRY(cudaEventCreate(&evk1));

@@ -71,7 +71,8 @@ def test_struct_layout_matches_header(tmp_path):
 #include "afsai.h"
 int main(void) {
   printf("%zu %zu %zu %zu\\n", sizeof(afsai_csr), sizeof(afsai_params), sizeof(afsai_info), sizeof(pcg_info));
-  printf("%zu %zu %zu\\n", offsetof(afsai_csr, val), offsetof(afsai_params, chol_prec), offsetof(pcg_info, solve_ms));
+  printf("%zu %zu %zu %zu\\n", offsetof(afsai_csr, val), offsetof(afsai_params, chol_prec), offsetof(pcg_info, solve_ms),
+         offsetof(afsai_params, block_power));
   return 0;
 }
 """)
@@ -86,3 +87,4 @@ int main(void) {
     assert sizes[4] == afsai.Csr.val.offset
     assert sizes[5] == afsai.Params.chol_prec.offset
     assert sizes[6] == afsai.PcgInfo.solve_ms.offset
+    assert sizes[7] == afsai.Params.block_power.offset

@@ -28,9 +28,9 @@ def gpu():
     return afsai
 
 
-def run_gpu(afsai, A, kiter, s, eps, exit_mode=0, g_prec=0, chol_prec=0):
+def run_gpu(afsai, A, kiter, s, eps, exit_mode=0, g_prec=0, chol_prec=0, block_rows=0, block_power=1):
     Ad = afsai.DeviceCSR.from_host(A)
-    M = afsai.afsai_setup(Ad, afsai.params(kiter, s, eps, exit_mode, g_prec, chol_prec))
+    M = afsai.afsai_setup(Ad, afsai.params(kiter, s, eps, exit_mode, g_prec, chol_prec, block_rows, block_power))
     rp, ci, va = M.export()
     trp, tci, tva = M.export(transpose=True)
     psi, steps = M.rows()
@@ -150,3 +150,51 @@ def test_indefinite_matrix_reports_not_spd(gpu, oracle_mod):
     with pytest.raises(afsai.AfsaiError) as e:
         afsai.afsai_setup(afsai.DeviceCSR.from_host(A), afsai.params(1, 1, 0.0))
     assert e.value.status == afsai.ENOTSPD
+
+
+# Locality bound of the distributed set-up (Section 4): stripes of
+# block_rows rows, candidates only from stripes allowed by Ahat^power.  Both
+# set-up paths (stepwise for patterns of <= 20 entries, fused above) and the
+# overflow retry must apply the same bound as the oracle.
+BOUND_CASES = [
+    ("poisson_stepwise", lambda: mg.poisson7(17, 13, 11), 5, 2, 1e-3, [(0.11, 1), (0.05, 2), (0.2, 0), (1e-9, 1)]),
+    ("elast_fused", lambda: mg.elasticity_hex(6, 17), 10, 3, 1e-3, [(0.1, 1), (0.25, 0), (0.06, 2)]),
+    ("fe27_fused", lambda: mg.stencil27_fe(9, 8, 7, scale=(1.0, 1.0, 100.0)), 8, 3, 1e-3, [(0.13, 1), (0.3, 2)]),
+    ("random_spd", lambda: mg.random_spd(700, 0.01, 5), 6, 3, 1e-3, [(0.07, 1), (0.5, 0)]),
+    ("single_stripe", lambda: mg.poisson7(9), 5, 2, 1e-3, [(1.0, 1), (1.7, 3)]),
+]
+
+
+@pytest.mark.parametrize("name,make,kiter,s,eps,bounds", BOUND_CASES, ids=[c[0] for c in BOUND_CASES])
+def test_locality_bound_bit_identical(gpu, oracle_mod, name, make, kiter, s, eps, bounds):
+    A = make()
+    for frac, power in bounds:
+        br = max(1, int(round(frac * A.n)))
+        ref = oracle_mod.afsai_setup(A, kiter, s, eps, block_rows=br, block_power=power)
+        g = run_gpu(gpu, A, kiter, s, eps, block_rows=br, block_power=power)
+        assert g["info"]["nnz_G"] == ref.nnz, (br, power)
+        assert_identical(g, ref, A)
+
+
+def test_locality_bound_overflow_retry(gpu, oracle_mod):
+    A = mg.random_spd(3000, 0.1, 41)
+    ref = oracle_mod.afsai_setup(A, 3, 2, 0.0, block_rows=700, block_power=1)
+    g = run_gpu(gpu, A, 3, 2, 0.0, block_rows=700, block_power=1)
+    assert_identical(g, ref, A)
+
+
+def test_locality_bound_arguments(gpu):
+    afsai = gpu
+    A = mg.poisson7(6)
+    Ad = afsai.DeviceCSR.from_host(A)
+    for br, pw, st in ((-1, 1, afsai.EINVAL), (8, -1, afsai.EINVAL), (8, 65, afsai.EINVAL), (1, 1, None)):
+        if st is None:
+            afsai.afsai_setup(Ad, afsai.params(3, 2, 1e-3, 0, 0, 0, br, pw)).close()
+            continue
+        with pytest.raises(afsai.AfsaiError) as e:
+            afsai.afsai_setup(Ad, afsai.params(3, 2, 1e-3, 0, 0, 0, br, pw))
+        assert e.value.status == st
+    big = mg.laplace1d(9000)
+    with pytest.raises(afsai.AfsaiError) as e:  # more than 8192 stripes
+        afsai.afsai_setup(afsai.DeviceCSR.from_host(big), afsai.params(3, 2, 1e-3, 0, 0, 0, 1, 1))
+    assert e.value.status == afsai.ENOTSUP
