@@ -344,7 +344,11 @@ bool make_mode(int mode, const CsrDev& C, SpmvMode* m) {
     }
     m->threads = 256;
     const int64_t lanes = (mode == 3 || mode == 6) ? static_cast<int64_t>(C.n) * 32 / (32 / mode) : static_cast<int64_t>(C.n) * mode;
-    m->blocks = grid_for(lanes, 256);
+    // one resident wave (8 blocks of 256 per SM): every block pays an FP64
+    // shuffle reduction for the fused dot products, and at 1/64-rate FP64
+    // those per-block costs are worth keeping to one per resident block
+    const int64_t need = (lanes + 255) / 256;
+    m->blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(need, static_cast<int64_t>(num_sms()) * 8)));
     m->smem = 0;
     m->cap = 0;
     return true;
