@@ -98,8 +98,7 @@ struct WarpWs {
     int32_t Pn[MCAP];                      // merge buffers
     int32_t rbn[MCAP];
     int32_t ren[MCAP];
-    int32_t nkeys;                         // keys in the candidate table this step
-    int32_t pad_;
+    int32_t pad_[2];
     union {
         struct {
             double val[HT];
@@ -134,27 +133,36 @@ __device__ __forceinline__ uint32_t slot_of(int32_t j, int log2) {
     return (static_cast<uint32_t>(j) * 0x9E3779B1u) >> (32 - log2);
 }
 
-// Inserts j (or finds it) and returns its slot; -1 if the table is full.
-// New slots are appended to the compact list.  `full` is set once the
-// table holds more than 7/8 of its slots, which sends the row to the retry
-// pass with a larger table (bounded probing).
-__device__ __forceinline__ int table_insert(int32_t* key, int32_t* list, int log2, int32_t j, int32_t* nkeys,
-                                            bool& full) {
+// Finds j in the table or claims an empty slot for it (CAS); returns the
+// slot, or -1 if every slot is taken, and sets `fresh` for a claimed slot.
+__device__ __forceinline__ int table_claim(int32_t* key, int log2, int32_t j, bool& fresh) {
     const uint32_t mask = (1u << log2) - 1u;
     uint32_t h = slot_of(j, log2);
+    fresh = false;
     for (uint32_t probe = 0; probe <= mask; ++probe) {
         const int32_t cur = atomicCAS(&key[h], -1, j);
         if (cur == -1) {
-            const int32_t at = atomicAdd(nkeys, 1);
-            list[at] = static_cast<int32_t>(h);
-            if (at >= static_cast<int32_t>((mask + 1) - ((mask + 1) >> 3))) full = true;
+            fresh = true;
             return static_cast<int>(h);
         }
         if (cur == j) return static_cast<int>(h);
         h = (h + 1) & mask;
     }
-    full = true;
     return -1;
+}
+
+// Appends the slots claimed in one pass to the compact list in lane order,
+// with one ballot instead of an atomic counter per new key; nk (the list
+// length) is kept equal in every lane of the group.  Sets `full` once the
+// table holds more than 7/8 of its slots or a probe found no slot, which
+// sends the row to the retry pass with a larger table (bounded probing).
+__device__ __forceinline__ void table_append(int32_t* list, int slot, bool fresh, bool failed, int& nk, bool& full,
+                                             int log2, unsigned gmask) {
+    const unsigned bal = __ballot_sync(gmask, fresh);
+    if (fresh) list[nk + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u))] = slot;
+    nk += __popc(bal);
+    const int ht = 1 << log2;
+    if (failed || nk > ht - (ht >> 3)) full = true;
 }
 
 __device__ __forceinline__ int table_find(const int32_t* key, int log2, int32_t j) {
@@ -309,24 +317,26 @@ template <int GL, int NPF>
 __device__ __forceinline__ void accumulate_row(const RowPref<NPF>& R, const int32_t* __restrict__ colA,
                                                const double* __restrict__ valA, int32_t rb, int32_t re, int32_t i,
                                                double gr, int32_t* key, double* hv, int32_t* list, int log2,
-                                               int32_t* nkeys, bool& ovf, int sub, unsigned gmask) {
+                                               int& nk, bool& ovf, int sub, unsigned gmask) {
 #pragma unroll
     for (int q = 0; q < NPF; ++q) {
         const int32_t j = R.c[q];
         if (!__any_sync(gmask, j < i)) return;  // columns are sorted
-        if (j < i) {
-            const int slot = table_insert(key, list, log2, j, nkeys, ovf);
-            if (slot >= 0) hv[slot] = fma(R.v[q], gr, hv[slot]);
-        }
+        bool fresh = false;
+        int slot = -1;
+        if (j < i) slot = table_claim(key, log2, j, fresh);
+        table_append(list, slot, fresh, j < i && slot < 0, nk, ovf, log2, gmask);
+        if (slot >= 0) hv[slot] = fma(R.v[q], gr, hv[slot]);
     }
     for (int32_t e = rb + sub + NPF * GL;; e += GL) {
         const int32_t j = e < re ? __ldg(&colA[e]) : INT_MAX;
         const double v = e < re ? __ldg(&valA[e]) : 0.0;
         if (!__any_sync(gmask, j < i)) return;
-        if (j < i) {
-            const int slot = table_insert(key, list, log2, j, nkeys, ovf);
-            if (slot >= 0) hv[slot] = fma(v, gr, hv[slot]);
-        }
+        bool fresh = false;
+        int slot = -1;
+        if (j < i) slot = table_claim(key, log2, j, fresh);
+        table_append(list, slot, fresh, j < i && slot < 0, nk, ovf, log2, gmask);
+        if (slot >= 0) hv[slot] = fma(v, gr, hv[slot]);
     }
 }
 
@@ -371,7 +381,7 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
             key[t] = -1;
             hv[t] = 0.0;
         }
-        if (sub == 0) w.nkeys = 0;
+        int nkr = 0;  // keys in the table, equal in every lane
         __syncwarp(gmask);
         bool ovf = false;
         {
@@ -382,13 +392,13 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
             prefetch_row<GL, NPF>(RA, colA, valA, w.rb[0], w.re[0], sub);
             for (int t = 0; t < m; t += 2) {
                 if (t + 1 < m) prefetch_row<GL, NPF>(RB, colA, valA, w.rb[t + 1], w.re[t + 1], sub);
-                accumulate_row<GL, NPF>(RA, colA, valA, w.rb[t], w.re[t], i, w.g[t], key, hv, list, log2, &w.nkeys, ovf,
-                                   sub, gmask);
+                accumulate_row<GL, NPF>(RA, colA, valA, w.rb[t], w.re[t], i, w.g[t], key, hv, list, log2, nkr, ovf,
+                                        sub, gmask);
                 __syncwarp(gmask);
                 if (t + 1 < m) {
                     if (t + 2 < m) prefetch_row<GL, NPF>(RA, colA, valA, w.rb[t + 2], w.re[t + 2], sub);
                     accumulate_row<GL, NPF>(RB, colA, valA, w.rb[t + 1], w.re[t + 1], i, w.g[t + 1], key, hv, list, log2,
-                                       &w.nkeys, ovf, sub, gmask);
+                                            nkr, ovf, sub, gmask);
                     __syncwarp(gmask);
                 }
             }
@@ -403,7 +413,7 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
             if (slot >= 0) hv[slot] = 0.0;
         }
         __syncwarp(gmask);
-        const int nk = w.nkeys;
+        const int nk = nkr;
         apply_stripe_bound(bd, key, hv, list, nk, sub, GL, gmask);
         // ---- select the s largest |gradient| (ties: smaller column) ----
         int npick = 0;
@@ -809,8 +819,7 @@ struct GatherWs {
     int32_t Pn[MC];
     int32_t rb[MC];
     int32_t re[MC];
-    int32_t nkeys;
-    int32_t pad_;
+    int32_t pad_[2];
     double val[HT];
     int32_t key[HT];
     int32_t list[HT];
@@ -842,7 +851,7 @@ __global__ void __launch_bounds__(256) step_gather(StepArgs a) {
             w.key[t] = -1;
             w.val[t] = 0.0;
         }
-        if (sub == 0) w.nkeys = 0;
+        int nkr = 0;  // keys in the table, equal in every lane
         __syncwarp();
         // ---- Kaporin gradient over j < i (Eq. "grapsi") ----
         bool ovf = false;
@@ -853,12 +862,12 @@ __global__ void __launch_bounds__(256) step_gather(StepArgs a) {
             for (int t = 0; t < m; t += 2) {
                 if (t + 1 < m) prefetch_row<GL, NPF>(RB, a.col, a.val, w.rb[t + 1], w.re[t + 1], sub);
                 accumulate_row<GL, NPF>(RA, a.col, a.val, w.rb[t], w.re[t], i, w.g[t], w.key, w.val, w.list, log2,
-                                        &w.nkeys, ovf, sub, gmask);
+                                        nkr, ovf, sub, gmask);
                 __syncwarp();
                 if (t + 1 < m) {
                     if (t + 2 < m) prefetch_row<GL, NPF>(RA, a.col, a.val, w.rb[t + 2], w.re[t + 2], sub);
                     accumulate_row<GL, NPF>(RB, a.col, a.val, w.rb[t + 1], w.re[t + 1], i, w.g[t + 1], w.key, w.val,
-                                            w.list, log2, &w.nkeys, ovf, sub, gmask);
+                                            w.list, log2, nkr, ovf, sub, gmask);
                     __syncwarp();
                 }
             }
@@ -873,7 +882,7 @@ __global__ void __launch_bounds__(256) step_gather(StepArgs a) {
             if (slot >= 0) w.val[slot] = 0.0;
         }
         __syncwarp();
-        const int nk = w.nkeys;
+        const int nk = nkr;
         apply_stripe_bound(stripe_bound(a.reach, a.reach_words, a.stripe_magic, a.stripe_shift, i), w.key, w.val,
                            w.list, nk, sub, GL, gmask);
         // ---- select the s largest |gradient| (ties: smaller column) ----
