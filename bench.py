@@ -763,6 +763,10 @@ def main():
             "solve_gbs": pcg_iteration_bytes(A, sinfo, args.form) * n_it / (float(np.median(solve_ms)) * 1e-3) / 1e9,
             "gpu_launches": int(launches), "roofline": roof, "forms": extra, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clk,
+            # SpMV engines the timed run used (AFSAI_SPMV_MODES="a,g,gt" pins them for a profile)
+            "spmv_engines": {"A": afsai.spmv_engine(0, A.n, A.nnz, 0),
+                             "G": afsai.spmv_engine(1, A.n, sinfo["nnz_G"], FORMS[args.form]["g_prec"]),
+                             "Gt": afsai.spmv_engine(2, A.n, sinfo["nnz_G"], FORMS[args.form]["g_prec"])},
         }
         print(json.dumps(line), flush=True)
     if world > 1:

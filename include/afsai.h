@@ -297,6 +297,16 @@ AFSAI_API int64_t afsai_kernel_launches(void);
 /* Library version string. */
 AFSAI_API const char* afsai_version(void);
 
+/* Diagnostic: the CSR SpMV engine chosen (timed once per matrix shape) for
+ * role 0 (A), 1 (G) or 2 (G^T) of an n x n matrix with nnz entries and value
+ * type vtype (0 fp64, 1 fp32, 2 bf16) on the calling thread's device, or 0
+ * if none was chosen yet.  Engines: 1, 2, 4, 8 = that many lanes per row,
+ * strided; 3, 6 = grouped lanes; 101, 102 = staged tiles with 1 or 2
+ * threads per row.  The environment variable AFSAI_SPMV_MODES="a,g,gt" (or
+ * AFSAI_SPMV_MODE for all roles) pins the engines instead of timing them,
+ * e.g. to profile the engines a timed run chose. */
+AFSAI_API int32_t afsai_spmv_engine(int32_t role, int32_t n, int64_t nnz, int32_t vtype);
+
 #ifdef __cplusplus
 }
 #endif

@@ -31,7 +31,7 @@ EXPORTS = (
     "afsai_setup", "afsai_apply", "afsai_spmv", "pcg_solve", "afsai_solve_host", "afsai_get_info",
     "afsai_export_G", "afsai_export_Gt", "afsai_export_rows", "afsai_destroy", "afsai_last_error", "afsai_version",
     "afsai_kernel_launches", "afsai_apply_static", "afsai_batch_solve", "serve_create", "serve_register",
-    "serve_submit", "serve_poll", "serve_get_stats", "serve_destroy",
+    "serve_submit", "serve_poll", "serve_get_stats", "serve_destroy", "afsai_spmv_engine",
 )
 
 
@@ -146,10 +146,17 @@ def load(build_if_missing: bool = True):
         lib.serve_get_stats.restype = st
         lib.serve_destroy.argtypes = [P]
         lib.serve_destroy.restype = None
+        lib.afsai_spmv_engine.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32]
+        lib.afsai_spmv_engine.restype = ctypes.c_int32
         lib.afsai_kernel_launches.argtypes = []
         lib.afsai_kernel_launches.restype = ctypes.c_int64
         _lib = lib
         return lib
+
+
+def spmv_engine(role: int, n: int, nnz: int, vtype: int = 0) -> int:
+    """Engine chosen for role 0 (A), 1 (G), 2 (G^T) of a matrix shape (0: none)."""
+    return int(load().afsai_spmv_engine(int(role), int(n), int(nnz), int(vtype)))
 
 
 def kernel_launches() -> int:

@@ -107,6 +107,10 @@ namespace afsai {
 afsai_status validate_csr(const afsai_csr* A, cudaStream_t st, int32_t* max_row_nnz);
 
 // Set-up (setup.cu).  Fills M->G, M->Gt, M->psi, M->steps.
+// CSR SpMV engine chosen so far for a role (0 A, 1 G, 2 G^T) and matrix
+// shape on the current device (0 if none).
+int spmv_engine_of(int role, int32_t n, int64_t nnz, int vtype);
+
 afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_row_nnz, cudaStream_t st,
                         afsai_precond* M);
 

@@ -174,6 +174,11 @@ const char* afsai_version(void) { return "afsai-gb300 0.1 (sm_103a)"; }
 
 int64_t afsai_kernel_launches(void) { return launches_so_far(); }
 
+int32_t afsai_spmv_engine(int32_t role, int32_t n, int64_t nnz, int32_t vtype) {
+    if (role < 0 || role > 2) return 0;
+    return spmv_engine_of(role, n, nnz, vtype);
+}
+
 afsai_status afsai_setup(const afsai_csr* A, const afsai_params* params, void* stream, afsai_precond** out) {
     if (!out) return fail(AFSAI_EINVAL, "out is NULL");
     *out = nullptr;

@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <climits>
 #include <cstdlib>
+#include <array>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -410,23 +411,56 @@ struct ModeKey {
     }
 };
 
+// engines chosen so far, per device, role and matrix shape
+std::mutex g_mode_mu;
+std::map<ModeKey, int> g_mode_cache;
+
+// Engine pinned by the environment for a role: AFSAI_SPMV_MODES = "a,g,gt"
+// (per role) or AFSAI_SPMV_MODE (all roles); 0 if none.
+int forced_mode(int role) {
+    static const std::array<int, 3> per_role = [] {
+        std::array<int, 3> v{0, 0, 0};
+        if (const char* e = std::getenv("AFSAI_SPMV_MODES")) {
+            int k = 0;
+            for (const char* c = e; *c && k < 3; ++k) {
+                v[k] = std::atoi(c);
+                while (*c && *c != ',') ++c;
+                if (*c == ',') ++c;
+            }
+        } else if (const char* e1 = std::getenv("AFSAI_SPMV_MODE")) {
+            v.fill(std::atoi(e1));
+        }
+        return v;
+    }();
+    return role >= 0 && role < 3 ? per_role[role] : 0;
+}
+
 }  // namespace
 
 afsai_status spmv_launch_role(int role, const SpmvMode& m, const CsrDev& C, const void* x, void* y, cudaStream_t st) {
     return launch_role(role, m, C, x, y, st);
 }
 
+int spmv_engine_of(int role, int32_t n, int64_t nnz, int vtype) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(g_mode_mu);
+    auto it = g_mode_cache.find(ModeKey{dev, role, vtype, n, nnz});
+    return it == g_mode_cache.end() ? 0 : it->second;
+}
+
 afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode* out, bool allow_tuning) {
-    static std::mutex mu;
-    static std::map<ModeKey, int> cache;
-    static const int forced = [] {
-        const char* e = std::getenv("AFSAI_SPMV_MODE");
-        return e ? std::atoi(e) : 0;
-    }();
+    auto& mu = g_mode_mu;
+    auto& cache = g_mode_cache;
+    const int forced = forced_mode(role);
     int dev = 0;
     cudaGetDevice(&dev);
     const ModeKey key{dev, role, C.vtype, C.n, C.nnz};
-    if (forced && make_mode(forced, C, out)) return AFSAI_OK;
+    if (forced && make_mode(forced, C, out)) {
+        std::lock_guard<std::mutex> lock(mu);
+        cache[key] = forced;
+        return AFSAI_OK;
+    }
     {
         std::lock_guard<std::mutex> lock(mu);
         auto it = cache.find(key);
@@ -450,16 +484,23 @@ afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode*
     const int64_t launches_before = launches_so_far();
     int best = -1;
     float best_ms = 0.f;
+    // each candidate: one warm-up launch, then the best of three timings of
+    // four launches (single timings of a few tens of microseconds are noisy)
     for (int mode : cand) {
         SpmvMode m;
         if (!make_mode(mode, C, &m)) continue;
         if (launch_role(role, m, C, xb.p, yb.p, st) != AFSAI_OK) continue;
-        cudaEventRecord(e0, st);
-        for (int r = 0; r < 3; ++r) launch_role(role, m, C, xb.p, yb.p, st);
-        cudaEventRecord(e1, st);
-        if (cudaEventSynchronize(e1) != cudaSuccess) break;
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
+        float ms = -1.f;
+        for (int trial = 0; trial < 3; ++trial) {
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < 4; ++r) launch_role(role, m, C, xb.p, yb.p, st);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) break;
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (ms < 0.f || t < ms) ms = t;
+        }
+        if (ms < 0.f) break;
         if (best < 0 || ms < best_ms) {
             best = mode;
             best_ms = ms;
