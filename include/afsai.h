@@ -307,6 +307,19 @@ AFSAI_API const char* afsai_version(void);
  * e.g. to profile the engines a timed run chose. */
 AFSAI_API int32_t afsai_spmv_engine(int32_t role, int32_t n, int64_t nnz, int32_t vtype);
 
+/* Self-check of the library's own FP64 arithmetic (no counterpart in the
+ * paper).  The lane-per-row dense solves of the FP64 set-up compute their
+ * square roots and divisions on the integer pipes (GB300 runs FP64 at 1/64
+ * of the FP32 rate) and must give the IEEE round-to-nearest results bit for
+ * bit.  This call draws n operand sets on the device from a counter-based
+ * generator seeded by `seed` (random and structured significands, normal
+ * and extreme exponents, near-exact quotients, zero numerators, squares and
+ * their neighbours), compares every result with the hardware IEEE
+ * operation and writes the mismatch counts to mismatches[0] (divisions) and
+ * mismatches[1] (square roots), a host array of two entries.  Synchronous
+ * on `stream`.  Returns AFSAI_EINVAL for n < 0 or mismatches == NULL. */
+AFSAI_API afsai_status afsai_check_arith(int64_t n, uint64_t seed, int64_t* mismatches, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

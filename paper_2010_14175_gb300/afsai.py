@@ -31,7 +31,7 @@ EXPORTS = (
     "afsai_setup", "afsai_apply", "afsai_spmv", "pcg_solve", "afsai_solve_host", "afsai_get_info",
     "afsai_export_G", "afsai_export_Gt", "afsai_export_rows", "afsai_destroy", "afsai_last_error", "afsai_version",
     "afsai_kernel_launches", "afsai_apply_static", "afsai_batch_solve", "serve_create", "serve_register",
-    "serve_submit", "serve_poll", "serve_get_stats", "serve_destroy", "afsai_spmv_engine",
+    "serve_submit", "serve_poll", "serve_get_stats", "serve_destroy", "afsai_spmv_engine", "afsai_check_arith",
 )
 
 
@@ -148,6 +148,8 @@ def load(build_if_missing: bool = True):
         lib.serve_destroy.restype = None
         lib.afsai_spmv_engine.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32]
         lib.afsai_spmv_engine.restype = ctypes.c_int32
+        lib.afsai_check_arith.argtypes = [ctypes.c_int64, ctypes.c_uint64, P, P]
+        lib.afsai_check_arith.restype = ctypes.c_int
         lib.afsai_kernel_launches.argtypes = []
         lib.afsai_kernel_launches.restype = ctypes.c_int64
         _lib = lib
@@ -157,6 +159,16 @@ def load(build_if_missing: bool = True):
 def spmv_engine(role: int, n: int, nnz: int, vtype: int = 0) -> int:
     """Engine chosen for role 0 (A), 1 (G), 2 (G^T) of a matrix shape (0: none)."""
     return int(load().afsai_spmv_engine(int(role), int(n), int(nnz), int(vtype)))
+
+
+def check_arith(n: int, seed: int = 1, stream=None):
+    """Mismatch counts (divisions, square roots) of the library's integer-
+    pipe FP64 arithmetic against the hardware IEEE operations on n operand
+    sets drawn on the device."""
+    out = (ctypes.c_int64 * 2)()
+    _check(load().afsai_check_arith(int(n), int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.cast(out, ctypes.c_void_p),
+                                    _stream(stream)))
+    return int(out[0]), int(out[1])
 
 
 def kernel_launches() -> int:

@@ -44,6 +44,7 @@
 #include <string>
 
 #include "afsai_internal.cuh"
+#include "fp64_rn.cuh"
 
 namespace afsai {
 namespace {
@@ -992,13 +993,18 @@ __global__ void __launch_bounds__(64) step_solve(StepArgs a) {
     const int lane = threadIdx.x & 31;
     const int nwb = blockDim.x >> 5;
     // lane-interleaved per-warp area: element e of lane l at [e * 32 + l]
-    double* Ms = reinterpret_cast<double*>(smem_raw) + static_cast<size_t>(warp) * (TMC + MC) * 32;
+    // FP64: MC extra words per lane for the prepared pivot reciprocals
+    constexpr int MCV = CHOL32 ? 0 : MC;
+    double* Ms = reinterpret_cast<double*>(smem_raw) + static_cast<size_t>(warp) * (TMC + MC + MCV) * 32;
     double* gs = Ms + TMC * 32;
-    float* Lf = reinterpret_cast<float*>(reinterpret_cast<double*>(smem_raw) + static_cast<size_t>(nwb) * (TMC + MC) * 32) +
+    uint64_t* vs = reinterpret_cast<uint64_t*>(gs + MC * 32);
+    float* Lf = reinterpret_cast<float*>(reinterpret_cast<double*>(smem_raw) +
+                                         static_cast<size_t>(nwb) * (TMC + MC + MCV) * 32) +
                 static_cast<size_t>(warp) * (TMC + MC) * 32;
     float* xf = Lf + TMC * 32;
 #define MS(e) Ms[(e) * 32 + lane]
 #define GS(e) gs[(e) * 32 + lane]
+#define VS(e) vs[(e) * 32 + lane]
 #define LF(e) Lf[(e) * 32 + lane]
 #define XF(e) xf[(e) * 32 + lane]
     const int64_t ngroups = (static_cast<int64_t>(a.n) + 31) / 32;
@@ -1011,23 +1017,28 @@ __global__ void __launch_bounds__(64) step_solve(StepArgs a) {
         for (int t = 0; t < tm; ++t) MS(t) = a.M[ii * a.tmc + t];
         bool spd = true;
         if (!CHOL32) {
+            // square roots and divisions on the integer pipes (rn::, the
+            // IEEE results bit for bit); each pivot's reciprocal is prepared
+            // once and kept (VS) for the back substitution
             for (int c = 0; c < m && spd; ++c) {
                 const double piv = MS(tri(c) + c);
                 if (!positive(piv)) {
                     spd = false;
                     break;
                 }
-                const double d = sqrt(piv);
+                const double d = rn::sqrt_rn(piv);
                 MS(tri(c) + c) = d;
-                for (int r = c + 1; r < m; ++r) MS(tri(r) + c) = MS(tri(r) + c) / d;
+                const rn::Divisor dv = rn::make_divisor(d);
+                VS(c) = dv.v;
+                for (int r = c + 1; r < m; ++r) MS(tri(r) + c) = rn::div_rn(MS(tri(r) + c), dv);
                 for (int r = c + 1; r < m; ++r)
                     for (int q = c + 1; q <= r; ++q) MS(tri(r) + q) = fma(-MS(tri(r) + c), MS(tri(q) + c), MS(tri(r) + q));
             }
             if (spd) {
                 for (int r = 0; r < m; ++r) GS(r) = 0.0;
-                GS(m - 1) = 1.0 / MS(tri(m - 1) + m - 1);
+                GS(m - 1) = rn::div_rn(1.0, rn::divisor_from(MS(tri(m - 1) + m - 1), VS(m - 1)));
                 for (int c = m - 1; c >= 0; --c) {
-                    const double gc = GS(c) / MS(tri(c) + c);
+                    const double gc = rn::div_rn(GS(c), rn::divisor_from(MS(tri(c) + c), VS(c)));
                     GS(c) = gc;
                     for (int r = 0; r < c; ++r) GS(r) = fma(-MS(tri(c) + r), gc, GS(r));
                 }
@@ -1091,6 +1102,7 @@ __global__ void __launch_bounds__(64) step_solve(StepArgs a) {
     }
 #undef MS
 #undef GS
+#undef VS
 #undef LF
 #undef XF
 }
@@ -1173,7 +1185,8 @@ afsai_status run_stepwise_t(const SetupArgs& o, int32_t kiter, cudaStream_t st) 
     const int blocks_g = std::max(1, std::min(per_sm_g * num_sms(), ceil_div(n, 8)));
     // solve kernel: lane-interleaved systems, 1 or 2 warps per block
     auto ks = step_solve<MC, CHOL32>;
-    const size_t per_warp = static_cast<size_t>(TMC + MC) * 32 * (sizeof(double) + (CHOL32 ? sizeof(float) : 0));
+    const size_t per_warp = static_cast<size_t>(TMC + MC) * 32 * (sizeof(double) + (CHOL32 ? sizeof(float) : 0)) +
+                            (CHOL32 ? 0 : static_cast<size_t>(MC) * 32 * sizeof(uint64_t));
     const int wpb = per_warp * 2 <= 200u * 1024u ? 2 : 1;
     const size_t smem_s = per_warp * wpb;
     AFSAI_CUDA_TRY(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_s)));
