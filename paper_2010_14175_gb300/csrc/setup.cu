@@ -193,15 +193,29 @@ __device__ __forceinline__ bool positive(float x) {
 // The trailing update of column c is spread over the lanes as (r, q) pairs
 // through the per-block table `pairs` (idx -> rr << 8 | qq, idx = rr(rr+1)/2
 // + qq).  Returns false (warp-uniform) on a non-positive pivot.
+//
+// FP64 (T = double): IEEE square roots and divisions, the operations of the
+// plain definition.  FP32 (T = float, the precision form, whose result is
+// corrected by an FP64 refinement step): the pivot's reciprocal square root
+// r = rsqrt(piv) gives L_cc = piv r and L_rc = M_rc r, and the diagonal slot
+// keeps r (the reciprocal of L_cc) for the triangular solves, which then
+// multiply instead of divide.
 template <int GL, typename T>
 __device__ bool group_cholesky(T* M, int m, int sub, unsigned gmask, const uint16_t* pairs) {
     for (int c = 0; c < m; ++c) {
         const T piv = M[tri(c) + c];
         if (!positive(piv)) return false;
-        const T d = sqrt(piv);
-        for (int r = c + 1 + sub; r < m; r += GL) M[tri(r) + c] = M[tri(r) + c] / d;
-        __syncwarp(gmask);
-        if (sub == 0) M[tri(c) + c] = d;
+        if constexpr (sizeof(T) == 4) {
+            const float rinv = rsqrtf(piv);
+            for (int r = c + 1 + sub; r < m; r += GL) M[tri(r) + c] = M[tri(r) + c] * rinv;
+            __syncwarp(gmask);
+            if (sub == 0) M[tri(c) + c] = rinv;
+        } else {
+            const T d = sqrt(piv);
+            for (int r = c + 1 + sub; r < m; r += GL) M[tri(r) + c] = M[tri(r) + c] / d;
+            __syncwarp(gmask);
+            if (sub == 0) M[tri(c) + c] = d;
+        }
         const int w = m - c - 1;
         const int T_ = (w * (w + 1)) >> 1;
         for (int idx = sub; idx < T_; idx += GL) {
@@ -218,16 +232,25 @@ __device__ bool group_cholesky(T* M, int m, int sub, unsigned gmask, const uint1
 // oriented as in the plain definition: forward L z = rhs, back L^T x = z.
 // When `em` is true the right-hand side is e_m and the forward solve
 // reduces to z = e_m / L_mm.
+// FP32: the diagonal slots hold the reciprocals of L_cc (group_cholesky).
+template <int GL, typename T>
+__device__ __forceinline__ T div_diag(T v, const T* L, int c) {
+    if constexpr (sizeof(T) == 4)
+        return v * L[tri(c) + c];
+    else
+        return v / L[tri(c) + c];
+}
+
 template <int GL, typename T>
 __device__ void group_llt_solve(const T* L, T* x, int m, bool em, int sub, unsigned gmask) {
     if (em) {
         for (int t = sub; t < m; t += GL) x[t] = T(0);
         __syncwarp(gmask);
-        if (sub == 0) x[m - 1] = T(1) / L[tri(m - 1) + m - 1];
+        if (sub == 0) x[m - 1] = div_diag<GL, T>(T(1), L, m - 1);
         __syncwarp(gmask);
     } else {
         for (int c = 0; c < m; ++c) {
-            const T zc = x[c] / L[tri(c) + c];
+            const T zc = div_diag<GL, T>(x[c], L, c);
             __syncwarp(gmask);
             if (sub == 0) x[c] = zc;
             for (int r = c + 1 + sub; r < m; r += GL) x[r] = fma(-L[tri(r) + c], zc, x[r]);
@@ -235,7 +258,7 @@ __device__ void group_llt_solve(const T* L, T* x, int m, bool em, int sub, unsig
         }
     }
     for (int c = m - 1; c >= 0; --c) {
-        const T gc = x[c] / L[tri(c) + c];
+        const T gc = div_diag<GL, T>(x[c], L, c);
         __syncwarp(gmask);
         if (sub == 0) x[c] = gc;
         for (int r = sub; r < c; r += GL) x[r] = fma(-L[tri(c) + r], gc, x[r]);
