@@ -678,12 +678,14 @@ def main():
     M, sinfo, pinfo = last
     value = ms_total / 1e3 / (args.steps * world)
 
-    # dominant kernel: the fused set-up kernel (one launch per step)
+    # dominant kernel: the set-up's pattern-search kernels, timed together
+    # with CUDA events around their launches (one set-up: the fused kernel,
+    # or the stepwise gather and solve kernels of every step)
     kern_ms = float(np.mean(kernel_ms))
     rp, ci, va = M.export()
     psi, steps = M.rows()
     flops = setup_flops(rp, steps, p["s"], A.nnz / A.n)
-    kkey = f"afsai_setup_kernel/{args.form}"
+    kkey = f"setup/{args.workload}/{args.form}"
     traffic, traffic_note = measured_traffic(kkey, A.n)
     if FORMS[args.form]["chol_prec"] == 0:
         fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12  # TFLOP/s: SMs x DFMA/clk x 2 x max clock

@@ -826,6 +826,7 @@ __global__ void step_init(StepArgs a) {
             if (a.col[e] == i) aii = a.val[e];
         a.P[i * a.mc] = static_cast<int32_t>(i);
         a.g[i * a.mc] = 1.0 / aii;
+        a.M[i * a.tmc] = aii;  // the 1 x 1 system, extended incrementally
         a.m[i] = 1;
         a.steps[i] = 0;
         a.psi[i] = aii;
@@ -843,13 +844,19 @@ struct GatherWs {
     int32_t Pn[MC];
     int32_t rb[MC];
     int32_t re[MC];
+    int32_t opos[MC];   // new position of each old position (incremental gather)
+    int32_t isnew[MC];  // 1 for positions inserted this step
     int32_t pad_[2];
     double val[HT];
     int32_t key[HT];
     int32_t list[HT];
 };
 
-template <int MC, int HT>
+// INC: the gathered system is extended incrementally (the previous step's
+// raw triangle is read back from a.M, moved to the new positions, and only
+// the rows of the new indices of A are read), as in the fused kernel; else
+// A[P,P] is gathered in full from the rows of P.
+template <int MC, int HT, bool INC>
 __global__ void __launch_bounds__(256) step_gather(StepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using WS = GatherWs<MC, HT>;
@@ -958,6 +965,8 @@ __global__ void __launch_bounds__(256) step_gather(StepArgs a) {
             int up = 0;
             for (int u = 0; u < npick; ++u) up += w.newj[u] < pt;
             w.Pn[t + up] = pt;
+            w.opos[t] = t + up;
+            w.isnew[t + up] = 0;
         }
         for (int u = sub; u < npick; u += GL) {
             const int32_t j = w.newj[u];
@@ -972,6 +981,7 @@ __global__ void __launch_bounds__(256) step_gather(StepArgs a) {
                     hi = mid;
             }
             w.Pn[lo + below] = j;
+            w.isnew[lo + below] = 1;
         }
         m = mold + npick;
         __syncwarp();
@@ -985,15 +995,42 @@ __global__ void __launch_bounds__(256) step_gather(StepArgs a) {
         const int tm = tri(m);
         for (int t = sub; t < tm; t += GL) w.Mw[t] = 0.0;
         __syncwarp();
-        // ---- systems gather: A[P,P], lower triangle, from the rows of P ----
-        for (int r = 0; r < m; ++r) {
-            const int32_t pr = w.P[r];
-            for (int32_t e = w.rb[r] + sub; e < w.re[r]; e += GL) {
-                const int32_t c = __ldg(&a.col[e]);
-                const double v = __ldg(&a.val[e]);
-                if (c > pr) continue;
-                const int pc = find_sorted(w.P, r + 1, c);
-                if (pc >= 0) w.Mw[tri(r) + pc] = v;
+        if (INC) {
+            // ---- systems gather, incremental: old entries to their new
+            // positions, then the rows of the new indices (A symmetric) ----
+            const int told = tri(mold);
+            for (int t = sub; t < told; t += GL) {
+                int r = static_cast<int>((sqrtf(8.0f * static_cast<float>(t) + 1.0f) - 1.0f) * 0.5f);
+                if (tri(r + 1) <= t) ++r;
+                if (tri(r) > t) --r;
+                const int q = t - tri(r);
+                w.Mw[tri(w.opos[r]) + w.opos[q]] = a.M[ii * a.tmc + t];
+            }
+            __syncwarp();
+            for (int pj = 0; pj < m; ++pj) {
+                if (!w.isnew[pj]) continue;
+                for (int32_t e = w.rb[pj] + sub; e < w.re[pj]; e += GL) {
+                    const int32_t c = __ldg(&a.col[e]);
+                    const double v = __ldg(&a.val[e]);
+                    const int pc = find_sorted(w.P, m, c);
+                    if (pc < 0) continue;
+                    if (pc <= pj)
+                        w.Mw[tri(pj) + pc] = v;
+                    else if (!w.isnew[pc])
+                        w.Mw[tri(pc) + pj] = v;
+                }
+            }
+        } else {
+            // ---- systems gather: A[P,P], lower triangle, from the rows of P ----
+            for (int r = 0; r < m; ++r) {
+                const int32_t pr = w.P[r];
+                for (int32_t e = w.rb[r] + sub; e < w.re[r]; e += GL) {
+                    const int32_t c = __ldg(&a.col[e]);
+                    const double v = __ldg(&a.val[e]);
+                    if (c > pr) continue;
+                    const int pc = find_sorted(w.P, r + 1, c);
+                    if (pc >= 0) w.Mw[tri(r) + pc] = v;
+                }
             }
         }
         __syncwarp();
@@ -1130,6 +1167,116 @@ __global__ void __launch_bounds__(64) step_solve(StepArgs a) {
 #undef XF
 }
 
+// LPR lanes per row, 32 / LPR rows per warp: Cholesky, solve, psi, exit
+// test of larger systems (up to MC = 32 entries), whose lane-per-row
+// workspace would not fit shared memory.  Each FP64 square root and each
+// back-substitution division serves all rows of the warp in one warp
+// instruction, and each column's divisions are spread over the row's lanes,
+// so a row pays a few FP64 division/square-root warp operations per column
+// instead of three.  Per element the operations and their order are those
+// of the plain definition (right-looking; element (r, q) updated by the
+// columns c < q in ascending order; lanes only split the elements).  Each
+// row's triangle lives in shared memory with an odd stride so that the same
+// element of the warp's rows falls in different banks.
+template <int MC, int LPR>
+__global__ void __launch_bounds__(128) step_solve_wide(StepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int TMC = MC * (MC + 1) / 2;
+    constexpr int RPW = 32 / LPR;            // rows per warp
+    constexpr int RS = (TMC + MC) | 1;       // doubles per row (odd)
+    constexpr size_t kPairBytes = (sizeof(uint16_t) * TMC + 15) / 16 * 16;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / LPR;
+    const int sub = lane % LPR;
+    const int nwb = blockDim.x >> 5;
+    uint16_t* pairs = reinterpret_cast<uint16_t*>(smem_raw);
+    for (int idx = threadIdx.x; idx < TMC; idx += blockDim.x) {
+        int r = static_cast<int>((sqrtf(8.0f * static_cast<float>(idx) + 1.0f) - 1.0f) * 0.5f);
+        if (tri(r + 1) <= idx) ++r;
+        if (tri(r) > idx) --r;
+        pairs[idx] = static_cast<uint16_t>((r << 8) | (idx - tri(r)));
+    }
+    __syncthreads();
+    double* wbase = reinterpret_cast<double*>(smem_raw + kPairBytes) + static_cast<size_t>(warp) * RPW * RS;
+    double* M = wbase + grp * RS;  // this row's packed lower triangle
+    double* g = M + TMC;           // this row's solution
+    const int64_t nrw = static_cast<int64_t>(gridDim.x) * nwb * RPW;
+    for (int64_t r0 = (static_cast<int64_t>(blockIdx.x) * nwb + warp) * RPW; r0 < a.n; r0 += nrw) {
+        const int64_t ii = r0 + grp;
+        const bool row = ii < a.n && a.st[ii] == kStSolve;
+        const int m = row ? a.m[ii] : 0;
+        // load the warp's triangles, one row at a time with all lanes
+        for (int q = 0; q < RPW; ++q) {
+            const int mq = __shfl_sync(0xffffffffu, m, q * LPR);
+            const int tq = tri(mq);
+            double* Mq = wbase + q * RS;
+            for (int t = lane; t < tq; t += 32) Mq[t] = a.M[(r0 + q) * a.tmc + t];
+        }
+        int mmax = m;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mmax = max(mmax, __shfl_xor_sync(0xffffffffu, mmax, o));
+        __syncwarp();
+        bool spd = true;
+        for (int c = 0; c < mmax; ++c) {
+            const bool act = spd && c < m;
+            const double piv = act ? M[tri(c) + c] : 1.0;
+            if (act && !positive(piv)) spd = false;
+            const double d = sqrt(piv);  // one warp instruction for all rows
+            if (act && spd)
+                for (int r = c + 1 + sub; r < m; r += LPR) M[tri(r) + c] = M[tri(r) + c] / d;
+            __syncwarp();
+            if (act && spd) {
+                if (sub == 0) M[tri(c) + c] = d;
+                const int w = m - c - 1;
+                const int T_ = (w * (w + 1)) >> 1;
+                for (int idx = sub; idx < T_; idx += LPR) {
+                    const int pr = pairs[idx];
+                    const int r = c + 1 + (pr >> 8), q = c + 1 + (pr & 0xff);
+                    M[tri(r) + q] = fma(-M[tri(r) + c], M[tri(q) + c], M[tri(r) + q]);
+                }
+            }
+            __syncwarp();
+        }
+        // z = e_m / L_mm, back substitution L^T g = z (column oriented)
+        for (int t = sub; t < m; t += LPR) g[t] = 0.0;
+        __syncwarp();
+        {
+            const double lmm = (row && spd) ? M[tri(m - 1) + m - 1] : 1.0;
+            const double z = 1.0 / lmm;
+            if (row && spd && sub == 0) g[m - 1] = z;
+        }
+        __syncwarp();
+        for (int t = 0; t < mmax; ++t) {
+            const int c = m - 1 - t;
+            const bool act = row && spd && c >= 0;
+            const double gc = act ? g[c] / M[tri(c) + c] : 0.0;  // one warp instruction
+            __syncwarp();
+            if (act) {
+                if (sub == 0) g[c] = gc;
+                for (int r = sub; r < c; r += LPR) g[r] = fma(-M[tri(c) + r], gc, g[r]);
+            }
+            __syncwarp();
+        }
+        if (row) {
+            if (!spd) {
+                if (sub == 0) a.st[ii] = kRowNotSpd;
+            } else {
+                const double psi = 1.0 / g[m - 1];
+                const double psi_prev = a.psi[ii];
+                const bool stop =
+                    (a.exit_mode == 0) ? ((psi_prev - psi) < a.eps * psi_prev) : ((psi / a.psi0[ii]) <= a.eps);
+                for (int t = sub; t < m; t += LPR) a.g[ii * a.mc + t] = g[t];
+                if (sub == 0) {
+                    a.psi[ii] = psi;
+                    a.st[ii] = stop ? kStStop : kStActive;
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // Final scaling and output slots (same layout as the fused kernel).
 __global__ void step_finish(StepArgs a, SetupArgs o) {
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < a.n;
@@ -1159,7 +1306,9 @@ __global__ void step_finish(StepArgs a, SetupArgs o) {
     }
 }
 
-template <int MC, int HT, bool CHOL32>
+// LPR = 0: lane-per-row solve kernel (step_solve); LPR > 0: step_solve_wide
+// with LPR lanes per row (FP64 only).  INC: incremental gather.
+template <int MC, int HT, bool CHOL32, bool INC = false, int LPR = 0>
 afsai_status run_stepwise_t(const SetupArgs& o, int32_t kiter, cudaStream_t st) {
     const int32_t n = o.n;
     constexpr int TMC = MC * (MC + 1) / 2;
@@ -1200,23 +1349,33 @@ afsai_status run_stepwise_t(const SetupArgs& o, int32_t kiter, cudaStream_t st) 
     AFSAI_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     // gather kernel: 8 warps per block
-    auto kg = step_gather<MC, HT>;
+    auto kg = step_gather<MC, HT, INC>;
     const size_t smem_g = sizeof(GatherWs<MC, HT>) * 8;
     AFSAI_CUDA_TRY(cudaFuncSetAttribute(kg, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_g)));
     int per_sm_g = 0;
     AFSAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_g, kg, 256, smem_g));
     const int blocks_g = std::max(1, std::min(per_sm_g * num_sms(), ceil_div(n, 8)));
-    // solve kernel: lane-interleaved systems, 1 or 2 warps per block
-    auto ks = step_solve<MC, CHOL32>;
-    const size_t per_warp = static_cast<size_t>(TMC + MC) * 32 * (sizeof(double) + (CHOL32 ? sizeof(float) : 0)) +
-                            (CHOL32 ? 0 : static_cast<size_t>(MC) * 32 * sizeof(uint64_t));
-    const int wpb = per_warp * 2 <= 200u * 1024u ? 2 : 1;
-    const size_t smem_s = per_warp * wpb;
+    // solve kernel: lane-interleaved systems, 1 or 2 warps per block (or the
+    // several-lanes-per-row kernel)
+    auto ks = [] {
+        if constexpr (LPR > 0)
+            return step_solve_wide<MC, LPR>;
+        else
+            return step_solve<MC, CHOL32>;
+    }();
+    const size_t per_warp =
+        LPR > 0 ? static_cast<size_t>(32 / (LPR > 0 ? LPR : 1)) * ((TMC + MC) | 1) * sizeof(double)
+                : static_cast<size_t>(TMC + MC) * 32 * (sizeof(double) + (CHOL32 ? sizeof(float) : 0)) +
+                      (CHOL32 ? 0 : static_cast<size_t>(MC) * 32 * sizeof(uint64_t));
+    const size_t pair_bytes = LPR > 0 ? (sizeof(uint16_t) * TMC + 15) / 16 * 16 : 0;
+    const int wpb = per_warp * 2 + pair_bytes <= 200u * 1024u ? 2 : 1;
+    const size_t smem_s = per_warp * wpb + pair_bytes;
     AFSAI_CUDA_TRY(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_s)));
     int per_sm_s = 0;
     AFSAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, ks, 32 * wpb, smem_s));
     if (per_sm_s < 1 || per_sm_g < 1) return fail(AFSAI_ENOTSUP, "stepwise set-up does not fit in shared memory");
-    const int blocks_s = std::max(1, std::min(per_sm_s * num_sms(), ceil_div(ceil_div(n, 32), wpb)));
+    const int rows_per_warp_s = LPR > 0 ? 32 / (LPR > 0 ? LPR : 1) : 32;
+    const int blocks_s = std::max(1, std::min(per_sm_s * num_sms(), ceil_div(ceil_div(n, rows_per_warp_s), wpb)));
     for (int32_t k = 1; k <= kiter; ++k) {
         kg<<<blocks_g, 256, smem_g, st>>>(a);
         ks<<<blocks_s, 32 * wpb, smem_s, st>>>(a);
@@ -1239,6 +1398,16 @@ int stepwise_max() {
     return v;
 }
 bool stepwise_supported(int64_t mcap) { return mcap <= stepwise_max(); }
+
+// FP64 systems of 21 to 32 entries: incremental gather, LPR lanes per row
+// in the solve.
+afsai_status run_stepwise_wide(const SetupArgs& o, int ht, int lpr, int32_t kiter, cudaStream_t st) {
+    if (lpr == 8)
+        return ht == 256 ? run_stepwise_t<32, 256, false, true, 8>(o, kiter, st)
+                         : run_stepwise_t<32, 512, false, true, 8>(o, kiter, st);
+    return ht == 256 ? run_stepwise_t<32, 256, false, true, 4>(o, kiter, st)
+                     : run_stepwise_t<32, 512, false, true, 4>(o, kiter, st);
+}
 
 afsai_status run_stepwise(const SetupArgs& o, int64_t mcap, int ht, int32_t kiter, bool chol32, cudaStream_t st) {
     if (mcap <= 12) {
@@ -1439,8 +1608,18 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
     }();
     // the stepwise path pays off where FP64 square roots and divisions
     // dominate: FP64 factorisation of small patterns
+    // FP64 systems of 21 to 32 entries: incremental stepwise gather and the
+    // several-lanes-per-row solve (8 lanes per row, 4 rows per warp);
+    // AFSAI_STEPWISE_WIDE = 4 or 8 sets the lanes per row, 0 keeps the fused
+    // kernel
+    static const int wide_lpr = [] {
+        const char* e = std::getenv("AFSAI_STEPWISE_WIDE");
+        return e ? std::atoi(e) : 8;
+    }();
     if (!fused_only && stepwise_supported(mcap) && p->kiter > 0 && !chol32)
         AFSAI_TRY(run_stepwise(a, mcap, ht, p->kiter, chol32, st));
+    else if (!fused_only && (wide_lpr == 4 || wide_lpr == 8) && mcap > 20 && mcap <= 32 && p->kiter > 0 && !chol32)
+        AFSAI_TRY(run_stepwise_wide(a, ht, wide_lpr, p->kiter, st));
     else
         AFSAI_TRY(dispatch(mcap_t, ht, gl, a, n, INT64_MAX, false, chol32, st));
     AFSAI_CUDA_TRY(cudaEventRecord(evk1, st));
