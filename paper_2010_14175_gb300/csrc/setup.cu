@@ -1178,12 +1178,17 @@ __global__ void __launch_bounds__(64) step_solve(StepArgs a) {
 // columns c < q in ascending order; lanes only split the elements).  Each
 // row's triangle lives in shared memory with an odd stride so that the same
 // element of the warp's rows falls in different banks.
+//
+// The square roots and divisions run on the integer pipes (rn::, the IEEE
+// results bit for bit): this kernel leaves most issue slots free while the
+// FP64 pipe is the bottleneck.  Each pivot's reciprocal is prepared once
+// and kept for the back substitution.
 template <int MC, int LPR>
 __global__ void __launch_bounds__(128) step_solve_wide(StepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int TMC = MC * (MC + 1) / 2;
     constexpr int RPW = 32 / LPR;            // rows per warp
-    constexpr int RS = (TMC + MC) | 1;       // doubles per row (odd)
+    constexpr int RS = (TMC + 2 * MC) | 1;   // doubles per row (odd): L, g, prepared reciprocals
     constexpr size_t kPairBytes = (sizeof(uint16_t) * TMC + 15) / 16 * 16;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -1201,6 +1206,7 @@ __global__ void __launch_bounds__(128) step_solve_wide(StepArgs a) {
     double* wbase = reinterpret_cast<double*>(smem_raw + kPairBytes) + static_cast<size_t>(warp) * RPW * RS;
     double* M = wbase + grp * RS;  // this row's packed lower triangle
     double* g = M + TMC;           // this row's solution
+    uint64_t* V = reinterpret_cast<uint64_t*>(g + MC);  // prepared pivot reciprocals
     const int64_t nrw = static_cast<int64_t>(gridDim.x) * nwb * RPW;
     for (int64_t r0 = (static_cast<int64_t>(blockIdx.x) * nwb + warp) * RPW; r0 < a.n; r0 += nrw) {
         const int64_t ii = r0 + grp;
@@ -1222,12 +1228,16 @@ __global__ void __launch_bounds__(128) step_solve_wide(StepArgs a) {
             const bool act = spd && c < m;
             const double piv = act ? M[tri(c) + c] : 1.0;
             if (act && !positive(piv)) spd = false;
-            const double d = sqrt(piv);  // one warp instruction for all rows
+            const double d = rn::sqrt_rn(piv);  // one warp operation for all rows
+            const rn::Divisor dv = rn::make_divisor(d);
             if (act && spd)
-                for (int r = c + 1 + sub; r < m; r += LPR) M[tri(r) + c] = M[tri(r) + c] / d;
+                for (int r = c + 1 + sub; r < m; r += LPR) M[tri(r) + c] = rn::div_rn(M[tri(r) + c], dv);
             __syncwarp();
             if (act && spd) {
-                if (sub == 0) M[tri(c) + c] = d;
+                if (sub == 0) {
+                    M[tri(c) + c] = d;
+                    V[c] = dv.v;
+                }
                 const int w = m - c - 1;
                 const int T_ = (w * (w + 1)) >> 1;
                 for (int idx = sub; idx < T_; idx += LPR) {
@@ -1242,15 +1252,15 @@ __global__ void __launch_bounds__(128) step_solve_wide(StepArgs a) {
         for (int t = sub; t < m; t += LPR) g[t] = 0.0;
         __syncwarp();
         {
-            const double lmm = (row && spd) ? M[tri(m - 1) + m - 1] : 1.0;
-            const double z = 1.0 / lmm;
-            if (row && spd && sub == 0) g[m - 1] = z;
+            const bool ok = row && spd;
+            const double z = ok ? rn::div_rn(1.0, rn::divisor_from(M[tri(m - 1) + m - 1], V[m - 1])) : 0.0;
+            if (ok && sub == 0) g[m - 1] = z;
         }
         __syncwarp();
         for (int t = 0; t < mmax; ++t) {
             const int c = m - 1 - t;
             const bool act = row && spd && c >= 0;
-            const double gc = act ? g[c] / M[tri(c) + c] : 0.0;  // one warp instruction
+            const double gc = act ? rn::div_rn(g[c], rn::divisor_from(M[tri(c) + c], V[c])) : 0.0;
             __syncwarp();
             if (act) {
                 if (sub == 0) g[c] = gc;
@@ -1364,7 +1374,7 @@ afsai_status run_stepwise_t(const SetupArgs& o, int32_t kiter, cudaStream_t st) 
             return step_solve<MC, CHOL32>;
     }();
     const size_t per_warp =
-        LPR > 0 ? static_cast<size_t>(32 / (LPR > 0 ? LPR : 1)) * ((TMC + MC) | 1) * sizeof(double)
+        LPR > 0 ? static_cast<size_t>(32 / (LPR > 0 ? LPR : 1)) * ((TMC + 2 * MC) | 1) * sizeof(double)
                 : static_cast<size_t>(TMC + MC) * 32 * (sizeof(double) + (CHOL32 ? sizeof(float) : 0)) +
                       (CHOL32 ? 0 : static_cast<size_t>(MC) * 32 * sizeof(uint64_t));
     const size_t pair_bytes = LPR > 0 ? (sizeof(uint16_t) * TMC + 15) / 16 * 16 : 0;
