@@ -838,7 +838,6 @@ __global__ void step_init(StepArgs a) {
 template <int MC, int HT>
 struct GatherWs {
     double g[MC];
-    double Mw[MC * (MC + 1) / 2];
     int32_t P[MC];
     int32_t newj[MC];
     int32_t Pn[MC];
@@ -847,9 +846,17 @@ struct GatherWs {
     int32_t opos[MC];   // new position of each old position (incremental gather)
     int32_t isnew[MC];  // 1 for positions inserted this step
     int32_t pad_[2];
-    double val[HT];
-    int32_t key[HT];
-    int32_t list[HT];
+    // the candidate table is dead once the step's picks are made; the
+    // gathered system is built in the same space (the next row clears the
+    // table again)
+    union {
+        struct {
+            double val[HT];
+            int32_t key[HT];
+            int32_t list[HT];
+        };
+        double Mw[MC * (MC + 1) / 2];
+    };
 };
 
 // INC: the gathered system is extended incrementally (the previous step's
