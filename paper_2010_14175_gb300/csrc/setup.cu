@@ -1294,6 +1294,154 @@ __global__ void __launch_bounds__(128) step_solve_wide(StepArgs a) {
     }
 }
 
+// The precision form of step_solve_wide: FP32 Cholesky and triangular
+// solves (the pivot's reciprocal square root r = rsqrt(piv) gives
+// L_cc = piv r and L_rc = M_rc r; the diagonal slots keep r), then one FP64
+// refinement step res = e_m - A[P,P] g (FP64, from the raw triangle),
+// L L^T d = res (FP32), g += d (FP64).  Same lanes and layout as
+// step_solve_wide; each row keeps its raw FP64 triangle for the residual.
+template <int MC, int LPR>
+__global__ void __launch_bounds__(128) step_solve_wide32(StepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int TMC = MC * (MC + 1) / 2;
+    constexpr int RPW = 32 / LPR;
+    // per row: raw triangle (double) + g (double) | factor (float) + x (float)
+    constexpr int RSD = (TMC + MC) | 1;          // doubles
+    constexpr int RSF = ((TMC + MC) | 1) + 1;    // floats (even count keeps 8-byte alignment)
+    constexpr size_t kRowBytes = RSD * sizeof(double) + RSF * sizeof(float);
+    constexpr size_t kPairBytes = (sizeof(uint16_t) * TMC + 15) / 16 * 16;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / LPR;
+    const int sub = lane % LPR;
+    const int nwb = blockDim.x >> 5;
+    uint16_t* pairs = reinterpret_cast<uint16_t*>(smem_raw);
+    for (int idx = threadIdx.x; idx < TMC; idx += blockDim.x) {
+        int r = static_cast<int>((sqrtf(8.0f * static_cast<float>(idx) + 1.0f) - 1.0f) * 0.5f);
+        if (tri(r + 1) <= idx) ++r;
+        if (tri(r) > idx) --r;
+        pairs[idx] = static_cast<uint16_t>((r << 8) | (idx - tri(r)));
+    }
+    __syncthreads();
+    unsigned char* wbase = smem_raw + kPairBytes + static_cast<size_t>(warp) * RPW * kRowBytes;
+    double* M = reinterpret_cast<double*>(wbase + grp * kRowBytes);  // raw A[P,P], packed lower
+    double* g = M + TMC;
+    float* L = reinterpret_cast<float*>(reinterpret_cast<double*>(wbase + grp * kRowBytes) + RSD);
+    float* x = L + TMC;
+    const int64_t nrw = static_cast<int64_t>(gridDim.x) * nwb * RPW;
+    for (int64_t r0 = (static_cast<int64_t>(blockIdx.x) * nwb + warp) * RPW; r0 < a.n; r0 += nrw) {
+        const int64_t ii = r0 + grp;
+        const bool row = ii < a.n && a.st[ii] == kStSolve;
+        const int m = row ? a.m[ii] : 0;
+        for (int q = 0; q < RPW; ++q) {
+            const int mq = __shfl_sync(0xffffffffu, m, q * LPR);
+            const int tq = tri(mq);
+            double* Mq = reinterpret_cast<double*>(wbase + q * kRowBytes);
+            float* Lq = reinterpret_cast<float*>(Mq + RSD);
+            for (int t = lane; t < tq; t += 32) {
+                const double v = a.M[(r0 + q) * a.tmc + t];
+                Mq[t] = v;
+                Lq[t] = static_cast<float>(v);
+            }
+        }
+        int mmax = m;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mmax = max(mmax, __shfl_xor_sync(0xffffffffu, mmax, o));
+        __syncwarp();
+        bool spd = true;
+        for (int c = 0; c < mmax; ++c) {
+            const bool act = spd && c < m;
+            const float piv = act ? L[tri(c) + c] : 1.0f;
+            if (act && !positive(piv)) spd = false;
+            const float rinv = rsqrtf(piv);
+            if (act && spd)
+                for (int r = c + 1 + sub; r < m; r += LPR) L[tri(r) + c] = L[tri(r) + c] * rinv;
+            __syncwarp();
+            if (act && spd) {
+                if (sub == 0) L[tri(c) + c] = rinv;
+                const int w = m - c - 1;
+                const int T_ = (w * (w + 1)) >> 1;
+                for (int idx = sub; idx < T_; idx += LPR) {
+                    const int pr = pairs[idx];
+                    const int r = c + 1 + (pr >> 8), q = c + 1 + (pr & 0xff);
+                    L[tri(r) + q] = fmaf(-L[tri(r) + c], L[tri(q) + c], L[tri(r) + q]);
+                }
+            }
+            __syncwarp();
+        }
+        const bool ok = row && spd;
+        // x = L^{-T} L^{-1} e_m (FP32)
+        for (int t = sub; t < m; t += LPR) x[t] = 0.0f;
+        __syncwarp();
+        if (ok && sub == 0) x[m - 1] = L[tri(m - 1) + m - 1];
+        __syncwarp();
+        for (int t = 0; t < mmax; ++t) {
+            const int c = m - 1 - t;
+            const bool act = ok && c >= 0;
+            const float gc = act ? x[c] * L[tri(c) + c] : 0.0f;
+            __syncwarp();
+            if (act) {
+                if (sub == 0) x[c] = gc;
+                for (int r = sub; r < c; r += LPR) x[r] = fmaf(-L[tri(c) + r], gc, x[r]);
+            }
+            __syncwarp();
+        }
+        for (int t = sub; t < m; t += LPR) g[t] = static_cast<double>(x[t]);
+        __syncwarp();
+        // one FP64 refinement step: res = e_m - A[P,P] g
+        if (ok)
+            for (int r = sub; r < m; r += LPR) {
+                double acc = (r == m - 1) ? 1.0 : 0.0;
+                for (int q = 0; q < m; ++q) {
+                    const double arq = (q <= r) ? M[tri(r) + q] : M[tri(q) + r];
+                    acc = fma(-arq, g[q], acc);
+                }
+                x[r] = static_cast<float>(acc);
+            }
+        __syncwarp();
+        // L z = res (forward), L^T d = z (back), in x
+        for (int c = 0; c < mmax; ++c) {
+            const bool act = ok && c < m;
+            const float zc = act ? x[c] * L[tri(c) + c] : 0.0f;
+            __syncwarp();
+            if (act) {
+                if (sub == 0) x[c] = zc;
+                for (int r = c + 1 + sub; r < m; r += LPR) x[r] = fmaf(-L[tri(r) + c], zc, x[r]);
+            }
+            __syncwarp();
+        }
+        for (int t = 0; t < mmax; ++t) {
+            const int c = m - 1 - t;
+            const bool act = ok && c >= 0;
+            const float gc = act ? x[c] * L[tri(c) + c] : 0.0f;
+            __syncwarp();
+            if (act) {
+                if (sub == 0) x[c] = gc;
+                for (int r = sub; r < c; r += LPR) x[r] = fmaf(-L[tri(c) + r], gc, x[r]);
+            }
+            __syncwarp();
+        }
+        for (int t = sub; t < m; t += LPR) g[t] = g[t] + static_cast<double>(x[t]);
+        __syncwarp();
+        if (row) {
+            if (!spd) {
+                if (sub == 0) a.st[ii] = kRowNotSpd;
+            } else {
+                const double psi = 1.0 / g[m - 1];
+                const double psi_prev = a.psi[ii];
+                const bool stop =
+                    (a.exit_mode == 0) ? ((psi_prev - psi) < a.eps * psi_prev) : ((psi / a.psi0[ii]) <= a.eps);
+                for (int t = sub; t < m; t += LPR) a.g[ii * a.mc + t] = g[t];
+                if (sub == 0) {
+                    a.psi[ii] = psi;
+                    a.st[ii] = stop ? kStStop : kStActive;
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // Final scaling and output slots (same layout as the fused kernel).
 __global__ void step_finish(StepArgs a, SetupArgs o) {
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < a.n;
@@ -1375,13 +1523,18 @@ afsai_status run_stepwise_t(const SetupArgs& o, int32_t kiter, cudaStream_t st) 
     // solve kernel: lane-interleaved systems, 1 or 2 warps per block (or the
     // several-lanes-per-row kernel)
     auto ks = [] {
-        if constexpr (LPR > 0)
+        if constexpr (LPR > 0 && CHOL32)
+            return step_solve_wide32<MC, LPR>;
+        else if constexpr (LPR > 0)
             return step_solve_wide<MC, LPR>;
         else
             return step_solve<MC, CHOL32>;
     }();
+    constexpr int RPW_S = LPR > 0 ? 32 / (LPR > 0 ? LPR : 1) : 32;
     const size_t per_warp =
-        LPR > 0 ? static_cast<size_t>(32 / (LPR > 0 ? LPR : 1)) * ((TMC + 2 * MC) | 1) * sizeof(double)
+        LPR > 0 ? (CHOL32 ? static_cast<size_t>(RPW_S) * (((TMC + MC) | 1) * sizeof(double) +
+                                                         (((TMC + MC) | 1) + 1) * sizeof(float))
+                          : static_cast<size_t>(RPW_S) * ((TMC + 2 * MC) | 1) * sizeof(double))
                 : static_cast<size_t>(TMC + MC) * 32 * (sizeof(double) + (CHOL32 ? sizeof(float) : 0)) +
                       (CHOL32 ? 0 : static_cast<size_t>(MC) * 32 * sizeof(uint64_t));
     const size_t pair_bytes = LPR > 0 ? (sizeof(uint16_t) * TMC + 15) / 16 * 16 : 0;
@@ -1418,7 +1571,10 @@ bool stepwise_supported(int64_t mcap) { return mcap <= stepwise_max(); }
 
 // FP64 systems of 21 to 32 entries: incremental gather, LPR lanes per row
 // in the solve.
-afsai_status run_stepwise_wide(const SetupArgs& o, int ht, int lpr, int32_t kiter, cudaStream_t st) {
+afsai_status run_stepwise_wide(const SetupArgs& o, int ht, int lpr, int32_t kiter, bool chol32, cudaStream_t st) {
+    if (chol32)
+        return ht == 256 ? run_stepwise_t<32, 256, true, true, 8>(o, kiter, st)
+                         : run_stepwise_t<32, 512, true, true, 8>(o, kiter, st);
     if (lpr == 8)
         return ht == 256 ? run_stepwise_t<32, 256, false, true, 8>(o, kiter, st)
                          : run_stepwise_t<32, 512, false, true, 8>(o, kiter, st);
@@ -1633,10 +1789,17 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
         const char* e = std::getenv("AFSAI_STEPWISE_WIDE");
         return e ? std::atoi(e) : 8;
     }();
+    // the mixed form takes the same path (FP32 solve + FP64 refinement in
+    // step_solve_wide32) unless AFSAI_STEPWISE_WIDE_MIXED = 0
+    static const bool wide_mixed = [] {
+        const char* e = std::getenv("AFSAI_STEPWISE_WIDE_MIXED");
+        return !e || std::atoi(e) != 0;
+    }();
     if (!fused_only && stepwise_supported(mcap) && p->kiter > 0 && !chol32)
         AFSAI_TRY(run_stepwise(a, mcap, ht, p->kiter, chol32, st));
-    else if (!fused_only && (wide_lpr == 4 || wide_lpr == 8) && mcap > 20 && mcap <= 32 && p->kiter > 0 && !chol32)
-        AFSAI_TRY(run_stepwise_wide(a, ht, wide_lpr, p->kiter, st));
+    else if (!fused_only && (wide_lpr == 4 || wide_lpr == 8) && mcap > 20 && mcap <= 32 && p->kiter > 0 &&
+             (!chol32 || wide_mixed))
+        AFSAI_TRY(run_stepwise_wide(a, ht, wide_lpr, p->kiter, chol32, st));
     else
         AFSAI_TRY(dispatch(mcap_t, ht, gl, a, n, INT64_MAX, false, chol32, st));
     AFSAI_CUDA_TRY(cudaEventRecord(evk1, st));
