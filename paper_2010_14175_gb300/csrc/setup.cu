@@ -1471,6 +1471,31 @@ __global__ void step_finish(StepArgs a, SetupArgs o) {
     }
 }
 
+// kiter = 0 (the diagonal pattern, G = diag(A)^{-1/2}: Jacobi): one thread
+// per row, the same operations as the init and the final scaling of the
+// other paths (g = 1 / a_ii, G_ii = g / sqrt(g), psi = a_ii).
+__global__ void k_setup_diagonal(SetupArgs o) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < o.n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        double aii = 0.0;
+        for (int32_t e = o.rowptr[i]; e < o.rowptr[i + 1]; ++e)
+            if (o.col[e] == i) aii = o.val[e];
+        if (positive(aii)) {
+            const double g = 1.0 / aii;
+            o.out_col[i * o.mcap] = static_cast<int32_t>(i);
+            o.out_val[i * o.mcap] = g / sqrt(g);
+            o.out_len[i] = 1;
+            o.psi[i] = aii;
+            o.steps[i] = 0;
+            o.status[i] = kRowOk;
+        } else {
+            o.out_len[i] = 0;
+            o.status[i] = kRowNotSpd;
+            atomicAdd(&o.counters[1], 1);
+        }
+    }
+}
+
 // LPR = 0: lane-per-row solve kernel (step_solve); LPR > 0: step_solve_wide
 // with LPR lanes per row (FP64 only).  INC: incremental gather.
 template <int MC, int HT, bool CHOL32, bool INC = false, int LPR = 0>
@@ -1795,10 +1820,14 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
         const char* e = std::getenv("AFSAI_STEPWISE_WIDE_MIXED");
         return !e || std::atoi(e) != 0;
     }();
-    if (!fused_only && stepwise_supported(mcap) && p->kiter > 0 && !chol32)
+    if (p->kiter == 0) {
+        const int blocks = std::max(1, std::min(ceil_div(n, 256), num_sms() * 8));
+        k_setup_diagonal<<<blocks, 256, 0, st>>>(a);
+        AFSAI_CUDA_TRY(cudaGetLastError());
+        count_launches(1);
+    } else if (!fused_only && stepwise_supported(mcap) && !chol32)
         AFSAI_TRY(run_stepwise(a, mcap, ht, p->kiter, chol32, st));
-    else if (!fused_only && (wide_lpr == 4 || wide_lpr == 8) && mcap > 20 && mcap <= 32 && p->kiter > 0 &&
-             (!chol32 || wide_mixed))
+    else if (!fused_only && (wide_lpr == 4 || wide_lpr == 8) && mcap > 20 && mcap <= 32 && (!chol32 || wide_mixed))
         AFSAI_TRY(run_stepwise_wide(a, ht, wide_lpr, p->kiter, chol32, st));
     else
         AFSAI_TRY(dispatch(mcap_t, ht, gl, a, n, INT64_MAX, false, chol32, st));
