@@ -576,7 +576,8 @@ def run_sweep(args, rank, world, local):
             f = FORMS[form]
             prm = afsai.params(5, 2, 1e-3, 0, f["g_prec"], f["chol_prec"])
             ts, ss, its = [], [], []
-            for rep in range(args.warmup + args.steps):
+            reps = max(3, args.steps)  # median of at least three timed solves per size
+            for rep in range(args.warmup + reps):
                 x.zero_()
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
