@@ -1186,10 +1186,12 @@ __global__ void __launch_bounds__(64) step_solve(StepArgs a) {
 // row's triangle lives in shared memory with an odd stride so that the same
 // element of the warp's rows falls in different banks.
 //
-// The square roots and divisions run on the integer pipes (rn::, the IEEE
-// results bit for bit): this kernel leaves most issue slots free while the
-// FP64 pipe is the bottleneck.  Each pivot's reciprocal is prepared once
-// and kept for the back substitution.
+// The divisions run on the integer pipes (rn::, the IEEE results bit for
+// bit), which relieves the FP64 pipe; the one square root per column stays
+// the IEEE FP64 operation (measured faster here: the integer version's
+// instructions cost more issue slots than the FP64 pipe time it saves).
+// Each pivot's reciprocal is prepared once and kept for the back
+// substitution.
 template <int MC, int LPR>
 __global__ void __launch_bounds__(128) step_solve_wide(StepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1235,7 +1237,7 @@ __global__ void __launch_bounds__(128) step_solve_wide(StepArgs a) {
             const bool act = spd && c < m;
             const double piv = act ? M[tri(c) + c] : 1.0;
             if (act && !positive(piv)) spd = false;
-            const double d = rn::sqrt_rn(piv);  // one warp operation for all rows
+            const double d = sqrt(piv);  // one warp operation for all rows (IEEE; the FP64 pipe has room)
             const rn::Divisor dv = rn::make_divisor(d);
             if (act && spd)
                 for (int r = c + 1 + sub; r < m; r += LPR) M[tri(r) + c] = rn::div_rn(M[tri(r) + c], dv);
