@@ -1610,6 +1610,25 @@ afsai_status run_stepwise_wide(const SetupArgs& o, int ht, int lpr, int32_t kite
 }
 
 afsai_status run_stepwise(const SetupArgs& o, int64_t mcap, int ht, int32_t kiter, bool chol32, cudaStream_t st) {
+    // FP64: several lanes per row in the solve (measured best: 2 lanes for
+    // patterns of up to 12 entries, 4 up to 20); AFSAI_STEPWISE_SMALL_LPR =
+    // 1 selects the one-lane-per-row solve kernel, 2 or 4 force a width
+    static const int small_lpr = [] {
+        const char* e = std::getenv("AFSAI_STEPWISE_SMALL_LPR");
+        return e ? std::atoi(e) : 0;
+    }();
+    const int lpr = small_lpr != 0 ? small_lpr : (mcap <= 12 ? 2 : 4);
+    if (!chol32 && (lpr == 2 || lpr == 4)) {
+        if (mcap <= 12)
+            return lpr == 4 ? (ht == 256 ? run_stepwise_t<12, 256, false, true, 4>(o, kiter, st)
+                                         : run_stepwise_t<12, 512, false, true, 4>(o, kiter, st))
+                            : (ht == 256 ? run_stepwise_t<12, 256, false, true, 2>(o, kiter, st)
+                                         : run_stepwise_t<12, 512, false, true, 2>(o, kiter, st));
+        return lpr == 4 ? (ht == 256 ? run_stepwise_t<20, 256, false, true, 4>(o, kiter, st)
+                                     : run_stepwise_t<20, 512, false, true, 4>(o, kiter, st))
+                        : (ht == 256 ? run_stepwise_t<20, 256, false, true, 2>(o, kiter, st)
+                                     : run_stepwise_t<20, 512, false, true, 2>(o, kiter, st));
+    }
     if (mcap <= 12) {
         if (ht == 256)
             return chol32 ? run_stepwise_t<12, 256, true>(o, kiter, st) : run_stepwise_t<12, 256, false>(o, kiter, st);

@@ -198,3 +198,43 @@ def test_locality_bound_arguments(gpu):
     with pytest.raises(afsai.AfsaiError) as e:  # more than 8192 stripes
         afsai.afsai_setup(afsai.DeviceCSR.from_host(big), afsai.params(3, 2, 1e-3, 0, 0, 0, 1, 1))
     assert e.value.status == afsai.ENOTSUP
+
+
+# Every set-up path must stay bit-identical to the oracle, not only the
+# default one per pattern size: the fused kernel for all sizes, the
+# one-lane-per-row stepwise solve, and the other lane widths.  The path
+# switches are read once per process, so each runs in a child process.
+_PATH_SCRIPT = r"""
+import sys
+import numpy as np
+sys.path.insert(0, {root!r})
+import oracle
+from paper_2010_14175_gb300 import afsai, matgen as mg
+afsai.load()
+cases = [(mg.poisson7(13, 7, 11), 5, 2), (mg.elasticity_hex(6, 17), 10, 3),
+         (mg.stencil27_fe(9, 8, 7, scale=(1.0, 1.0, 100.0)), 8, 2), (mg.random_spd(700, 0.01, 5), 6, 3)]
+for A, kiter, s in cases:
+    ref = oracle.afsai_setup(A, kiter, s, 1e-3)
+    M = afsai.afsai_setup(afsai.DeviceCSR.from_host(A), afsai.params(kiter, s, 1e-3))
+    rp, ci, va = M.export()
+    psi, steps = M.rows()
+    M.close()
+    assert np.array_equal(rp, ref.rowptr) and np.array_equal(ci, ref.col), "pattern"
+    assert np.array_equal(va, ref.val) and np.array_equal(psi, ref.psi) and np.array_equal(steps, ref.steps), "values"
+print("ok")
+"""
+
+
+@pytest.mark.parametrize("env", [{"AFSAI_SETUP_FUSED_ONLY": "1"}, {"AFSAI_STEPWISE_SMALL_LPR": "1"},
+                                 {"AFSAI_STEPWISE_SMALL_LPR": "4", "AFSAI_STEPWISE_WIDE": "4"},
+                                 {"AFSAI_STEPWISE_WIDE": "0"}],
+                         ids=["fused_only", "lane_per_row", "lpr4_wide4", "wide_off"])
+def test_setup_paths_bit_identical(gpu, env):
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", _PATH_SCRIPT.format(root=root)], env={**os.environ, **env},
+                         capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0 and out.stdout.strip().endswith("ok"), out.stderr[-2000:]
