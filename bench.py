@@ -225,6 +225,41 @@ def setup_touched_bytes(rowptr_G, steps, s, nnz_row_avg):
     return total
 
 
+def g_difference(G_ref, G_other, n):
+    """||G - G_ref||_F / ||G_ref||_F, the largest entrywise relative
+    difference on entries present in both, and the fraction of rows whose
+    pattern equals the reference's."""
+    import scipy.sparse as sp
+
+    def csr(t):
+        rp, ci, va = t
+        return sp.csr_matrix((np.asarray(va, dtype=np.float64), ci, rp), shape=(n, n))
+
+    R, O = csr(G_ref), csr(G_other)
+    D = O - R
+    rel_fro = float(sp.linalg.norm(D) / sp.linalg.norm(R))
+    lr, lo = np.diff(R.indptr), np.diff(O.indptr)
+    row = np.repeat(np.arange(n), lr)
+    eq = lr[row] == lo[row]
+    e = np.arange(R.nnz)
+    match = np.zeros(R.nnz, dtype=bool)
+    idx = e[eq] + (O.indptr[row[eq]] - R.indptr[row[eq]])
+    match[eq] = R.indices[eq] == O.indices[idx]
+    bad_rows = np.zeros(n, dtype=bool)
+    np.logical_or.at(bad_rows, row[~match], True)
+    same_rows = int(np.count_nonzero((lr == lo) & ~bad_rows))
+    # largest entrywise relative difference over the rows whose pattern is
+    # the reference's (entries align one to one there)
+    good = (lr == lo) & ~bad_rows
+    sel = good[row]
+    max_rel = None
+    if sel.any():
+        o_idx = e[sel] + (O.indptr[row[sel]] - R.indptr[row[sel]])
+        rvals = np.asarray(R.data, dtype=np.float64)[sel]
+        max_rel = float(np.max(np.abs(np.asarray(O.data, dtype=np.float64)[o_idx] - rvals) / np.abs(rvals)))
+    return {"rel_frobenius": rel_fro, "max_rel_same_pattern_rows": max_rel, "rows_same_pattern": same_rows / n}
+
+
 def pcg_iteration_bytes(A, sinfo, form):
     """Algorithmic bytes of one PCG iteration: A (12 B/entry + row
     pointers), G and G^T ((4 + w) B/entry + row pointers, w the G value
@@ -703,6 +738,28 @@ def main():
                 "traffic_note": traffic_note, "kernel_ms": kern_ms, "algorithmic_bytes": touched,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
+
+    # preconditioner application z = G^T (G r) through the C ABI: algorithmic
+    # bytes (G and G^T entries and row pointers, r gathered, t written and
+    # gathered, z written) against the measured HBM copy bandwidth
+    w_g = {0: 8, 1: 4, 2: 2}[FORMS[args.form]["g_prec"]]
+    apply_bytes = 2 * (4 + w_g) * sinfo["nnz_G"] + 8 * (A.n + 1) + 32 * A.n
+    rv = torch.rand(A.n, dtype=torch.float64, device=dev)
+    zv = torch.empty_like(rv)
+    for _ in range(3):
+        afsai.afsai_apply(M, rv, zv, stream)
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(20):
+        afsai.afsai_apply(M, rv, zv, stream)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    apply_us = a0.elapsed_time(a1) * 1e3 / 20
+    apply_rec = {"us": apply_us, "bytes": apply_bytes, "gbs": apply_bytes / (apply_us * 1e-6) / 1e9,
+                 "peak_gbs": MEASURED_HBM_GBS,
+                 "frac": apply_bytes / (apply_us * 1e-6) / 1e9 / MEASURED_HBM_GBS}
+    G64 = (rp.copy(), ci.copy(), va.copy())
     M.close()
 
     extra = {}
@@ -726,6 +783,11 @@ def main():
                            "relres_true": pm_["relres_true"], "desc": FORMS[form]["desc"],
                            "setup_ms": sm_["setup_ms"], "solve_ms": pm_["solve_ms"],
                            "iters_vs_fp64": pm_["iters"] / max(1, int(np.median(iters)))}
+            if args.form == "fp64" and FORMS[form].get("kiter", 1) != 0:
+                # error of this form's G against the FP64 G of the same input
+                Mm, _, _ = one_solve(pf)
+                extra[form]["g_vs_fp64"] = g_difference(G64, Mm.export(), A.n)
+                Mm.close()
 
     e2e = None
     if not args.no_e2e:
@@ -766,6 +828,7 @@ def main():
             "solve_gbs": pcg_iteration_bytes(A, sinfo, args.form) * n_it / (float(np.median(solve_ms)) * 1e-3) / 1e9,
             "gpu_launches": int(launches), "roofline": roof, "forms": extra, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clk,
+            "apply": apply_rec,
             # SpMV engines the timed run used (AFSAI_SPMV_MODES="a,g,gt" pins them for a profile)
             "spmv_engines": {"A": afsai.spmv_engine(0, A.n, A.nnz, 0),
                              "G": afsai.spmv_engine(1, A.n, sinfo["nnz_G"], FORMS[args.form]["g_prec"]),
