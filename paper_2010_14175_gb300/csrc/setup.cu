@@ -1565,7 +1565,17 @@ afsai_status run_stepwise_t(const SetupArgs& o, int32_t kiter, cudaStream_t st) 
                 : static_cast<size_t>(TMC + MC) * 32 * (sizeof(double) + (CHOL32 ? sizeof(float) : 0)) +
                       (CHOL32 ? 0 : static_cast<size_t>(MC) * 32 * sizeof(uint64_t));
     const size_t pair_bytes = LPR > 0 ? (sizeof(uint16_t) * TMC + 15) / 16 * 16 : 0;
-    const int wpb = per_warp * 2 + pair_bytes <= 200u * 1024u ? 2 : 1;
+    // warps per block (1 to 4) that maximises resident warps per SM
+    int wpb = 1, best_w = 0;
+    for (int cand = 1; cand <= 4; ++cand) {
+        const size_t blk = per_warp * cand + pair_bytes + 1024;
+        if (blk > 200u * 1024u) break;
+        const int warps = static_cast<int>((227u * 1024u) / blk) * cand;
+        if (warps > best_w) {
+            best_w = warps;
+            wpb = cand;
+        }
+    }
     const size_t smem_s = per_warp * wpb + pair_bytes;
     AFSAI_CUDA_TRY(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_s)));
     int per_sm_s = 0;
