@@ -364,6 +364,113 @@ __device__ __forceinline__ void accumulate_row(const RowPref<NPF>& R, const int3
     }
 }
 
+// Selection of the s largest |gradient| (ties: smaller column) among the
+// table's candidates.  For s <= 4 in one pass: each lane keeps its own best
+// four in registers, then s rounds of a warp arg-max over the lanes' heads,
+// the winning lane dropping its head; (|grad| descending, column ascending)
+// is a total order, so the picks and their order are those of s passes that
+// each take the best remaining candidate (the pass form serves larger s).
+// Writes the picks to newj; returns their number (< s when the eligible
+// candidates, nonzero and not NaN, run out).
+__device__ __forceinline__ bool cand_better(unsigned long long a, int32_t ja, unsigned long long b, int32_t jb) {
+    return a > b || (a == b && ja < jb);
+}
+
+template <int GL>
+__device__ __forceinline__ int select_top_s(const int32_t* key, double* hv, const int32_t* list, int nk, int s, int sub,
+                                            unsigned gmask, int32_t* newj) {
+    int npick = 0;
+    if (s <= 4) {
+        unsigned long long kb[4] = {0ull, 0ull, 0ull, 0ull};
+        int32_t kj[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
+        for (int t = sub; t < nk; t += GL) {
+            const int sl = list[t];
+            const int32_t j = key[sl];
+            const unsigned long long ab =
+                static_cast<unsigned long long>(__double_as_longlong(hv[sl])) & 0x7fffffffffffffffull;
+            if (ab == 0ull || ab > 0x7ff0000000000000ull) continue;  // zero or NaN
+            if (!cand_better(ab, j, kb[3], kj[3])) continue;
+            kb[3] = ab;
+            kj[3] = j;
+#pragma unroll
+            for (int q = 3; q > 0; --q) {
+                if (cand_better(kb[q], kj[q], kb[q - 1], kj[q - 1])) {
+                    const unsigned long long tb = kb[q];
+                    kb[q] = kb[q - 1];
+                    kb[q - 1] = tb;
+                    const int32_t tj = kj[q];
+                    kj[q] = kj[q - 1];
+                    kj[q - 1] = tj;
+                }
+            }
+        }
+        for (int u = 0; u < s; ++u) {
+            unsigned long long best = kb[0];
+            int32_t bestj = kj[0];
+#pragma unroll
+            for (int off = GL / 2; off > 0; off >>= 1) {
+                const unsigned long long ob = __shfl_xor_sync(gmask, best, off, GL);
+                const int32_t oj = __shfl_xor_sync(gmask, bestj, off, GL);
+                if (cand_better(ob, oj, best, bestj)) {
+                    best = ob;
+                    bestj = oj;
+                }
+            }
+            if (best == 0ull) break;
+            if (kb[0] == best && kj[0] == bestj) {  // the owner drops its head
+                kb[0] = kb[1];
+                kj[0] = kj[1];
+                kb[1] = kb[2];
+                kj[1] = kj[2];
+                kb[2] = kb[3];
+                kj[2] = kj[3];
+                kb[3] = 0ull;
+                kj[3] = INT_MAX;
+            }
+            if (sub == 0) newj[npick] = bestj;
+            ++npick;
+        }
+        __syncwarp(gmask);
+        return npick;
+    }
+    for (int u = 0; u < s; ++u) {
+        unsigned long long best = 0ull;
+        int32_t bestj = INT_MAX;
+        int bslot = -1;
+        for (int t = sub; t < nk; t += GL) {
+            const int sl = list[t];
+            const int32_t j = key[sl];
+            const unsigned long long ab =
+                static_cast<unsigned long long>(__double_as_longlong(hv[sl])) & 0x7fffffffffffffffull;
+            if (ab == 0ull || ab > 0x7ff0000000000000ull) continue;  // zero or NaN
+            if (cand_better(ab, j, best, bestj)) {
+                best = ab;
+                bestj = j;
+                bslot = sl;
+            }
+        }
+#pragma unroll
+        for (int off = GL / 2; off > 0; off >>= 1) {
+            const unsigned long long ob = __shfl_xor_sync(gmask, best, off, GL);
+            const int32_t oj = __shfl_xor_sync(gmask, bestj, off, GL);
+            const int os = __shfl_xor_sync(gmask, bslot, off, GL);
+            if (cand_better(ob, oj, best, bestj)) {
+                best = ob;
+                bestj = oj;
+                bslot = os;
+            }
+        }
+        if (best == 0ull) break;
+        if (sub == 0) {
+            hv[bslot] = 0.0;
+            newj[npick] = bestj;
+        }
+        ++npick;
+        __syncwarp(gmask);
+    }
+    return npick;
+}
+
 template <int GL, int MCAP, int HT, bool CHOL32>
 __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, int32_t* key, double* hv,
                           int32_t* list, int log2, int sub, unsigned gmask, const uint16_t* pairs) {
@@ -440,42 +547,7 @@ __device__ void afsai_row(const SetupArgs& a, int32_t i, WarpWs<MCAP, HT>& w, in
         const int nk = nkr;
         apply_stripe_bound(bd, key, hv, list, nk, sub, GL, gmask);
         // ---- select the s largest |gradient| (ties: smaller column) ----
-        int npick = 0;
-        for (int u = 0; u < a.s; ++u) {
-            unsigned long long best = 0ull;
-            int32_t bestj = INT_MAX;
-            int bslot = -1;
-            for (int t = sub; t < nk; t += GL) {
-                const int sl = list[t];
-                const int32_t j = key[sl];
-                const unsigned long long ab =
-                    static_cast<unsigned long long>(__double_as_longlong(hv[sl])) & 0x7fffffffffffffffull;
-                if (ab == 0ull || ab > 0x7ff0000000000000ull) continue;  // zero or NaN
-                if (ab > best || (ab == best && j < bestj)) {
-                    best = ab;
-                    bestj = j;
-                    bslot = sl;
-                }
-            }
-#pragma unroll
-            for (int off = GL / 2; off > 0; off >>= 1) {
-                const unsigned long long ob = __shfl_xor_sync(gmask, best, off, GL);
-                const int32_t oj = __shfl_xor_sync(gmask, bestj, off, GL);
-                const int os = __shfl_xor_sync(gmask, bslot, off, GL);
-                if (ob > best || (ob == best && oj < bestj)) {
-                    best = ob;
-                    bestj = oj;
-                    bslot = os;
-                }
-            }
-            if (best == 0ull) break;
-            if (sub == 0) {
-                hv[bslot] = 0.0;
-                w.newj[npick] = bestj;
-            }
-            ++npick;
-            __syncwarp(gmask);
-        }
+        const int npick = select_top_s<GL>(key, hv, list, nk, a.s, sub, gmask, w.newj);
         if (npick == 0) break;
 
         // ---- merge into the sorted pattern; move the gathered triangle ----
@@ -924,42 +996,7 @@ __global__ void __launch_bounds__(256) step_gather(StepArgs a) {
         apply_stripe_bound(stripe_bound(a.reach, a.reach_words, a.stripe_magic, a.stripe_shift, i), w.key, w.val,
                            w.list, nk, sub, GL, gmask);
         // ---- select the s largest |gradient| (ties: smaller column) ----
-        int npick = 0;
-        for (int u = 0; u < a.s; ++u) {
-            unsigned long long best = 0ull;
-            int32_t bestj = INT_MAX;
-            int bslot = -1;
-            for (int t = sub; t < nk; t += GL) {
-                const int sl = w.list[t];
-                const int32_t j = w.key[sl];
-                const unsigned long long ab =
-                    static_cast<unsigned long long>(__double_as_longlong(w.val[sl])) & 0x7fffffffffffffffull;
-                if (ab == 0ull || ab > 0x7ff0000000000000ull) continue;
-                if (ab > best || (ab == best && j < bestj)) {
-                    best = ab;
-                    bestj = j;
-                    bslot = sl;
-                }
-            }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const unsigned long long ob = __shfl_xor_sync(gmask, best, off);
-                const int32_t oj = __shfl_xor_sync(gmask, bestj, off);
-                const int os = __shfl_xor_sync(gmask, bslot, off);
-                if (ob > best || (ob == best && oj < bestj)) {
-                    best = ob;
-                    bestj = oj;
-                    bslot = os;
-                }
-            }
-            if (best == 0ull) break;
-            if (sub == 0) {
-                w.val[bslot] = 0.0;
-                w.newj[npick] = bestj;
-            }
-            ++npick;
-            __syncwarp();
-        }
+        const int npick = select_top_s<GL>(w.key, w.val, w.list, nk, a.s, sub, gmask, w.newj);
         if (npick == 0) {
             if (sub == 0) a.st[i] = kStStop;
             __syncwarp();
