@@ -1,9 +1,17 @@
 // aFSAI set-up on the GPU (Section 2 of the paper; kernels of Section 3).
 //
-// One warp owns one row i for the whole adaptive iteration, so the three
-// kernels the paper launches per step (Kaporin gradient + selection,
-// systems gather, batched Cholesky) and the exit test run fused in one
-// launch with no intermediate global state:
+// Two paths compute the same rows bit for bit (FP64 form):
+//   fused     one warp owns one row i for the whole adaptive iteration: the
+//             three kernels the paper launches per step (Kaporin gradient +
+//             selection, systems gather, batched Cholesky) and the exit test
+//             run in one launch with no intermediate global state (below);
+//   stepwise  per step a gather kernel (warp per row) and a solve kernel
+//             with several rows per warp, so that each FP64 square root and
+//             division warp operation serves several rows (section
+//             "Stepwise set-up" further down).  Used for FP64 patterns of up
+//             to 32 entries and for the mixed form of 21 to 32 entries.
+//
+// The fused kernel:
 //
 //   init      P = {i}, g = 1/a_ii, psi_0 = a_ii              (G_0 = I)
 //   step k    gradient  (A g)_j over j < i, accumulated in a per-warp hash
@@ -848,17 +856,20 @@ __global__ void compact_rows_kernel(int32_t n, int64_t mcap, const int32_t* __re
 }
 
 // ---------------------------------------------------------------------------
-// Stepwise set-up for small patterns (1 + kiter s <= 20).
+// Stepwise set-up (patterns of up to 32 entries).
 //
-// With few entries per row, the fused kernel spends its FP64 issue slots on
-// square roots and divisions with one useful lane.  Here every step k runs
-// as two kernels, the structure of the paper's Section 3 (gradient +
-// selection + systems gather, then batched Cholesky):
-//   A  one warp per active row: Kaporin gradient, top-s selection, merge,
-//      full gather of A[P,P] into a per-row slot in global memory;
-//   B  one LANE per row: the row's Cholesky, triangular solves, psi and the
-//      exit test, in the exact sequential order of the plain definition, so
-//      each FP64 warp instruction serves 32 rows.
+// The fused kernel spends its FP64 issue slots on per-column square roots
+// and divisions with few useful lanes (a warp-wide FP64 division or square
+// root costs the same whatever the number of active lanes).  Here every
+// step k runs as two kernels, the structure of the paper's Section 3
+// (gradient + selection + systems gather, then batched Cholesky):
+//   A  step_gather, one warp per active row: Kaporin gradient, top-s
+//      selection, merge, and the gather of A[P,P] into a per-row slot in
+//      global memory (full, or incremental from the previous step's slot);
+//   B  the row's Cholesky, triangular solves, psi and the exit test, in the
+//      exact sequential order of the plain definition, with several rows
+//      per warp: step_solve_wide (LPR lanes per row, 32 / LPR rows per
+//      warp) or step_solve (one lane per row).
 // Row state (P, g, psi, step count, status) lives in global memory between
 // the kernels.  Results are bit-identical to the fused kernel.
 // ---------------------------------------------------------------------------
