@@ -1099,29 +1099,23 @@ __global__ void __launch_bounds__(256) step_gather(StepArgs a) {
     }
 }
 
-// One lane per row: Cholesky, solve, psi, exit test (plain sequential order).
-template <int MC, bool CHOL32>
+// One lane per row (FP64): Cholesky, solve, psi, exit test (plain
+// sequential order), 32 rows per warp.
+template <int MC>
 __global__ void __launch_bounds__(64) step_solve(StepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int TMC = MC * (MC + 1) / 2;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int nwb = blockDim.x >> 5;
-    // lane-interleaved per-warp area: element e of lane l at [e * 32 + l]
-    // FP64: MC extra words per lane for the prepared pivot reciprocals
-    constexpr int MCV = CHOL32 ? 0 : MC;
-    double* Ms = reinterpret_cast<double*>(smem_raw) + static_cast<size_t>(warp) * (TMC + MC + MCV) * 32;
+    // lane-interleaved per-warp area: element e of lane l at [e * 32 + l];
+    // MC extra words per lane for the prepared pivot reciprocals
+    double* Ms = reinterpret_cast<double*>(smem_raw) + static_cast<size_t>(warp) * (TMC + 2 * MC) * 32;
     double* gs = Ms + TMC * 32;
     uint64_t* vs = reinterpret_cast<uint64_t*>(gs + MC * 32);
-    float* Lf = reinterpret_cast<float*>(reinterpret_cast<double*>(smem_raw) +
-                                         static_cast<size_t>(nwb) * (TMC + MC + MCV) * 32) +
-                static_cast<size_t>(warp) * (TMC + MC) * 32;
-    float* xf = Lf + TMC * 32;
 #define MS(e) Ms[(e) * 32 + lane]
 #define GS(e) gs[(e) * 32 + lane]
 #define VS(e) vs[(e) * 32 + lane]
-#define LF(e) Lf[(e) * 32 + lane]
-#define XF(e) xf[(e) * 32 + lane]
     const int64_t ngroups = (static_cast<int64_t>(a.n) + 31) / 32;
     for (int64_t grp = static_cast<int64_t>(blockIdx.x) * nwb + warp; grp < ngroups;
          grp += static_cast<int64_t>(gridDim.x) * nwb) {
@@ -1131,77 +1125,30 @@ __global__ void __launch_bounds__(64) step_solve(StepArgs a) {
         const int tm = tri(m);
         for (int t = 0; t < tm; ++t) MS(t) = a.M[ii * a.tmc + t];
         bool spd = true;
-        if (!CHOL32) {
-            // square roots and divisions on the integer pipes (rn::, the
-            // IEEE results bit for bit); each pivot's reciprocal is prepared
-            // once and kept (VS) for the back substitution
-            for (int c = 0; c < m && spd; ++c) {
-                const double piv = MS(tri(c) + c);
-                if (!positive(piv)) {
-                    spd = false;
-                    break;
-                }
-                const double d = rn::sqrt_rn(piv);
-                MS(tri(c) + c) = d;
-                const rn::Divisor dv = rn::make_divisor(d);
-                VS(c) = dv.v;
-                for (int r = c + 1; r < m; ++r) MS(tri(r) + c) = rn::div_rn(MS(tri(r) + c), dv);
-                for (int r = c + 1; r < m; ++r)
-                    for (int q = c + 1; q <= r; ++q) MS(tri(r) + q) = fma(-MS(tri(r) + c), MS(tri(q) + c), MS(tri(r) + q));
+        // square roots and divisions on the integer pipes (rn::, the IEEE
+        // results bit for bit); each pivot's reciprocal is prepared once and
+        // kept (VS) for the back substitution
+        for (int c = 0; c < m && spd; ++c) {
+            const double piv = MS(tri(c) + c);
+            if (!positive(piv)) {
+                spd = false;
+                break;
             }
-            if (spd) {
-                for (int r = 0; r < m; ++r) GS(r) = 0.0;
-                GS(m - 1) = rn::div_rn(1.0, rn::divisor_from(MS(tri(m - 1) + m - 1), VS(m - 1)));
-                for (int c = m - 1; c >= 0; --c) {
-                    const double gc = rn::div_rn(GS(c), rn::divisor_from(MS(tri(c) + c), VS(c)));
-                    GS(c) = gc;
-                    for (int r = 0; r < c; ++r) GS(r) = fma(-MS(tri(c) + r), gc, GS(r));
-                }
-            }
-        } else {
-            for (int t = 0; t < tm; ++t) LF(t) = static_cast<float>(MS(t));
-            for (int c = 0; c < m && spd; ++c) {
-                const float piv = LF(tri(c) + c);
-                if (!positive(piv)) {
-                    spd = false;
-                    break;
-                }
-                const float d = sqrtf(piv);
-                LF(tri(c) + c) = d;
-                for (int r = c + 1; r < m; ++r) LF(tri(r) + c) = LF(tri(r) + c) / d;
-                for (int r = c + 1; r < m; ++r)
-                    for (int q = c + 1; q <= r; ++q) LF(tri(r) + q) = fmaf(-LF(tri(r) + c), LF(tri(q) + c), LF(tri(r) + q));
-            }
-            if (spd) {
-                // x = L^{-T} L^{-1} e_m in FP32
-                for (int r = 0; r < m; ++r) XF(r) = 0.0f;
-                XF(m - 1) = 1.0f / LF(tri(m - 1) + m - 1);
-                for (int c = m - 1; c >= 0; --c) {
-                    const float gc = XF(c) / LF(tri(c) + c);
-                    XF(c) = gc;
-                    for (int r = 0; r < c; ++r) XF(r) = fmaf(-LF(tri(c) + r), gc, XF(r));
-                }
-                for (int r = 0; r < m; ++r) GS(r) = static_cast<double>(XF(r));
-                // one FP64 refinement step
-                for (int r = 0; r < m; ++r) {
-                    double acc = (r == m - 1) ? 1.0 : 0.0;
-                    for (int q = 0; q < m; ++q) {
-                        const double arq = (q <= r) ? MS(tri(r) + q) : MS(tri(q) + r);
-                        acc = fma(-arq, GS(q), acc);
-                    }
-                    XF(r) = static_cast<float>(acc);
-                }
-                for (int c = 0; c < m; ++c) {
-                    const float zc = XF(c) / LF(tri(c) + c);
-                    XF(c) = zc;
-                    for (int r = c + 1; r < m; ++r) XF(r) = fmaf(-LF(tri(r) + c), zc, XF(r));
-                }
-                for (int c = m - 1; c >= 0; --c) {
-                    const float gc = XF(c) / LF(tri(c) + c);
-                    XF(c) = gc;
-                    for (int r = 0; r < c; ++r) XF(r) = fmaf(-LF(tri(c) + r), gc, XF(r));
-                }
-                for (int r = 0; r < m; ++r) GS(r) = GS(r) + static_cast<double>(XF(r));
+            const double d = rn::sqrt_rn(piv);
+            MS(tri(c) + c) = d;
+            const rn::Divisor dv = rn::make_divisor(d);
+            VS(c) = dv.v;
+            for (int r = c + 1; r < m; ++r) MS(tri(r) + c) = rn::div_rn(MS(tri(r) + c), dv);
+            for (int r = c + 1; r < m; ++r)
+                for (int q = c + 1; q <= r; ++q) MS(tri(r) + q) = fma(-MS(tri(r) + c), MS(tri(q) + c), MS(tri(r) + q));
+        }
+        if (spd) {
+            for (int r = 0; r < m; ++r) GS(r) = 0.0;
+            GS(m - 1) = rn::div_rn(1.0, rn::divisor_from(MS(tri(m - 1) + m - 1), VS(m - 1)));
+            for (int c = m - 1; c >= 0; --c) {
+                const double gc = rn::div_rn(GS(c), rn::divisor_from(MS(tri(c) + c), VS(c)));
+                GS(c) = gc;
+                for (int r = 0; r < c; ++r) GS(r) = fma(-MS(tri(c) + r), gc, GS(r));
             }
         }
         if (!spd) {
@@ -1218,8 +1165,6 @@ __global__ void __launch_bounds__(64) step_solve(StepArgs a) {
 #undef MS
 #undef GS
 #undef VS
-#undef LF
-#undef XF
 }
 
 // LPR lanes per row, 32 / LPR rows per warp: Cholesky, solve, psi, exit
@@ -1597,21 +1542,21 @@ afsai_status run_stepwise_t(const SetupArgs& o, int32_t kiter, cudaStream_t st) 
     const int blocks_g = std::max(1, std::min(per_sm_g * num_sms(), ceil_div(n, 8)));
     // solve kernel: lane-interleaved systems, 1 or 2 warps per block (or the
     // several-lanes-per-row kernel)
+    static_assert(LPR > 0 || !CHOL32, "the one-lane-per-row solve is FP64 only");
     auto ks = [] {
         if constexpr (LPR > 0 && CHOL32)
             return step_solve_wide32<MC, LPR>;
         else if constexpr (LPR > 0)
             return step_solve_wide<MC, LPR>;
         else
-            return step_solve<MC, CHOL32>;
+            return step_solve<MC>;
     }();
     constexpr int RPW_S = LPR > 0 ? 32 / (LPR > 0 ? LPR : 1) : 32;
     const size_t per_warp =
         LPR > 0 ? (CHOL32 ? static_cast<size_t>(RPW_S) * (((TMC + MC) | 1) * sizeof(double) +
                                                          (((TMC + MC) | 1) + 1) * sizeof(float))
                           : static_cast<size_t>(RPW_S) * ((TMC + 2 * MC) | 1) * sizeof(double))
-                : static_cast<size_t>(TMC + MC) * 32 * (sizeof(double) + (CHOL32 ? sizeof(float) : 0)) +
-                      (CHOL32 ? 0 : static_cast<size_t>(MC) * 32 * sizeof(uint64_t));
+                : static_cast<size_t>(TMC + 2 * MC) * 32 * sizeof(double);
     const size_t pair_bytes = LPR > 0 ? (sizeof(uint16_t) * TMC + 15) / 16 * 16 : 0;
     // warps per block (1 to 4) that maximises resident warps per SM
     int wpb = 1, best_w = 0;
@@ -1643,16 +1588,9 @@ afsai_status run_stepwise_t(const SetupArgs& o, int32_t kiter, cudaStream_t st) 
     return AFSAI_OK;
 }
 
-// Pattern capacities served by the stepwise path.
-int stepwise_max() {
-    static const int v = [] {
-        const char* e = std::getenv("AFSAI_STEPWISE_MAX");
-        const int k = e ? std::atoi(e) : 0;
-        return k == 32 ? 32 : 20;
-    }();
-    return v;
-}
-bool stepwise_supported(int64_t mcap) { return mcap <= stepwise_max(); }
+// Pattern capacities served by the small-pattern stepwise path (21 to 32
+// entries: run_stepwise_wide).
+bool stepwise_supported(int64_t mcap) { return mcap <= 20; }
 
 // FP64 systems of 21 to 32 entries: incremental gather, LPR lanes per row
 // in the solve.
@@ -1676,7 +1614,7 @@ afsai_status run_stepwise(const SetupArgs& o, int64_t mcap, int ht, int32_t kite
         return e ? std::atoi(e) : 0;
     }();
     const int lpr = small_lpr != 0 ? small_lpr : (mcap <= 12 ? 2 : 4);
-    if (!chol32 && (lpr == 2 || lpr == 4)) {
+    if (!chol32 && mcap <= 20 && (lpr == 2 || lpr == 4)) {
         if (mcap <= 12)
             return lpr == 4 ? (ht == 256 ? run_stepwise_t<12, 256, false, true, 4>(o, kiter, st)
                                          : run_stepwise_t<12, 512, false, true, 4>(o, kiter, st))
@@ -1687,23 +1625,12 @@ afsai_status run_stepwise(const SetupArgs& o, int64_t mcap, int ht, int32_t kite
                         : (ht == 256 ? run_stepwise_t<20, 256, false, true, 2>(o, kiter, st)
                                      : run_stepwise_t<20, 512, false, true, 2>(o, kiter, st));
     }
-    if (mcap <= 12) {
-        if (ht == 256)
-            return chol32 ? run_stepwise_t<12, 256, true>(o, kiter, st) : run_stepwise_t<12, 256, false>(o, kiter, st);
-        return chol32 ? run_stepwise_t<12, 512, true>(o, kiter, st) : run_stepwise_t<12, 512, false>(o, kiter, st);
-    }
-    if (mcap <= 16) {
-        if (ht == 256)
-            return chol32 ? run_stepwise_t<16, 256, true>(o, kiter, st) : run_stepwise_t<16, 256, false>(o, kiter, st);
-        return chol32 ? run_stepwise_t<16, 512, true>(o, kiter, st) : run_stepwise_t<16, 512, false>(o, kiter, st);
-    }
-    if (mcap <= 20) {
-        if (ht == 256)
-            return chol32 ? run_stepwise_t<20, 256, true>(o, kiter, st) : run_stepwise_t<20, 256, false>(o, kiter, st);
-        return chol32 ? run_stepwise_t<20, 512, true>(o, kiter, st) : run_stepwise_t<20, 512, false>(o, kiter, st);
-    }
-    if (chol32) return fail(AFSAI_ENOTSUP, "stepwise path: FP32 factorisation up to 20 entries");
-    return ht == 256 ? run_stepwise_t<32, 256, false>(o, kiter, st) : run_stepwise_t<32, 512, false>(o, kiter, st);
+    if (chol32) return fail(AFSAI_ENOTSUP, "small-pattern stepwise path: FP64 only");
+    if (mcap <= 12)
+        return ht == 256 ? run_stepwise_t<12, 256, false>(o, kiter, st) : run_stepwise_t<12, 512, false>(o, kiter, st);
+    if (mcap <= 20)
+        return ht == 256 ? run_stepwise_t<20, 256, false>(o, kiter, st) : run_stepwise_t<20, 512, false>(o, kiter, st);
+    return fail(AFSAI_ENOTSUP, "small-pattern stepwise path: up to 20 entries");
 }
 
 // ---------------------------------------------------------------------------
