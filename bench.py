@@ -541,6 +541,8 @@ def run_serve(args, rank, world, local):
     st = S.stats()
     S.close()
     lat = np.array([r[2]["latency_ms"] for r in done])
+    qms = np.array([r[2]["queue_ms"] for r in done])
+    sms = np.array([r[2]["setup_ms"] for r in done])
     solves = sum(r[2]["nrhs"] for r in done)
     worst = max(r[2]["max_relres_true"] for r in done)
     conv = all(r[2]["converged"] == 1 for r in done)
@@ -575,6 +577,9 @@ def run_serve(args, rank, world, local):
                        "form": FORMS[form]["desc"], "parallelism": f"replicas x{world}"},
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "solves_per_s": solves / wall, "requests": len(done),
+            "queue_ms": {"p50": float(np.percentile(qms, 50)), "p99": float(np.percentile(qms, 99))},
+            "setup_ms": {"p50": float(np.percentile(sms, 50)), "p99": float(np.percentile(sms, 99)),
+                         "requests_paying": int((sms > 0).sum())},
             "all_converged": conv, "relres_true_max": worst, "server_steps": st["steps"],
             "peak_mem_gb": st["peak_mem_bytes"] / 2 ** 30, "gpu_launches": int(launches),
             "sequential_fp64": {"solves_per_s": seq_solves, "p50_ms": float(np.percentile(lat_seq, 50)),
