@@ -75,6 +75,25 @@ enum ValType : int32_t { VAL_F64 = 0, VAL_F32 = 1, VAL_BF16 = 2 };
 
 inline size_t val_bytes(int32_t vt) { return vt == VAL_F64 ? 8 : (vt == VAL_F32 ? 4 : 2); }
 
+// Sliced ELLPACK copy of a CSR matrix (SELL-32-sigma): rows are sorted by
+// decreasing length inside windows of 4096 rows (stable, so rows of equal
+// length keep their order) and cut into slices of 32; slice s stores its
+// entries k-major in slots [32 kptr[s], 32 kptr[s + 1]): entry k of lane l
+// at slot 32 (kptr[s] + k) + l, with kptr[s + 1] - kptr[s] the longest row
+// of the slice.  Slots past a row's length hold column 0 and value 0 and
+// are never read.  rowlen[32 s + l] = (row, length), row -1 past n.  Each
+// row keeps the CSR order of its entries.
+constexpr int kSellWindowSlices = 128;  // slices per sorting window (4096 rows)
+
+struct SellDev {
+    int32_t nslices = 0;
+    int64_t nslots = 0;
+    int32_t* kptr = nullptr;  // nslices + 1
+    int2* rowlen = nullptr;   // 32 nslices
+    int32_t* col = nullptr;   // nslots
+    void* val = nullptr;      // nslots, the value type of the CSR
+};
+
 struct CsrDev {
     int32_t n = 0;
     int64_t nnz = 0;
@@ -83,6 +102,7 @@ struct CsrDev {
     void* val = nullptr;  // double / float / __nv_bfloat16 by vtype
     int32_t vtype = VAL_F64;
     int32_t max_row = 0;
+    SellDev sell;         // empty unless a sliced copy was built
 };
 
 }  // namespace afsai
@@ -106,17 +126,27 @@ namespace afsai {
 // Validates a device CSR (see afsai.h); synchronises the stream.
 afsai_status validate_csr(const afsai_csr* A, cudaStream_t st, int32_t* max_row_nnz);
 
-// Set-up (setup.cu).  Fills M->G, M->Gt, M->psi, M->steps.
-// CSR SpMV engine chosen so far for a role (0 A, 1 G, 2 G^T) and matrix
-// shape on the current device (0 if none).
+// SpMV engine chosen so far for a role (0 A, 1 G, 2 G^T) and matrix shape
+// on the current device (0 if none).
 int spmv_engine_of(int role, int32_t n, int64_t nnz, int vtype);
 
+// Set-up (setup.cu).  Fills M->G, M->Gt, M->psi, M->steps.
+// sliced = true also builds the sliced copies of G and G^T (the PCG and
+// apply engines of a single system); the batched and serving forms, which
+// run their own kernels on the CSR, pass false.
 afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_row_nnz, cudaStream_t st,
-                        afsai_precond* M);
+                        afsai_precond* M, bool sliced);
+
+// afsai_setup with the choice of sliced copies (api.cu).
+afsai_status setup_precond(const afsai_csr* A, const afsai_params* p, cudaStream_t st, bool sliced,
+                           afsai_precond** out);
 
 // Sparse building blocks (sparse.cu).
 afsai_status exclusive_scan_i32(const int32_t* in, int32_t* out, int32_t n, cudaStream_t st, int64_t* total_host);
 afsai_status build_transpose(const CsrDev& G, CsrDev* Gt, cudaStream_t st);
+// Sliced copy of C (sell.cu); *S stays empty on failure.
+afsai_status build_sell(const CsrDev& C, SellDev* S, cudaStream_t st);
+void free_sell(SellDev* S, cudaStream_t st);
 afsai_status spmv_csr(const CsrDev& A, const double* x, double* y, cudaStream_t st);
 afsai_status apply_precond(const afsai_precond* M, const double* r, double* t, double* z, cudaStream_t st);
 void free_csr(CsrDev* A, cudaStream_t st);

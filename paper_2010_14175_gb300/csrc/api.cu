@@ -162,6 +162,28 @@ afsai_status validate_csr(const afsai_csr* A, cudaStream_t st, int32_t* max_row_
     return AFSAI_OK;
 }
 
+afsai_status setup_precond(const afsai_csr* A, const afsai_params* params, cudaStream_t st, bool sliced,
+                           afsai_precond** out) {
+    if (!out) return fail(AFSAI_EINVAL, "out is NULL");
+    *out = nullptr;
+    AFSAI_TRY(check_params(params));
+    int32_t maxrow = 0;
+    AFSAI_TRY(validate_csr(A, st, &maxrow));
+    afsai_precond* M = new (std::nothrow) afsai_precond();
+    if (!M) return fail(AFSAI_ENOMEM, "host allocation");
+    cudaGetDevice(&M->device);
+    M->params = *params;
+    const afsai_status s = setup_impl(A, params, maxrow, st, M, sliced);
+    if (s != AFSAI_OK) {
+        const std::string msg = g_last_error;
+        destroy_precond(M, st);
+        g_last_error = msg;
+        return s;
+    }
+    *out = M;
+    return AFSAI_OK;
+}
+
 }  // namespace afsai
 
 using namespace afsai;
@@ -179,26 +201,9 @@ int32_t afsai_spmv_engine(int32_t role, int32_t n, int64_t nnz, int32_t vtype) {
     return spmv_engine_of(role, n, nnz, vtype);
 }
 
+
 afsai_status afsai_setup(const afsai_csr* A, const afsai_params* params, void* stream, afsai_precond** out) {
-    if (!out) return fail(AFSAI_EINVAL, "out is NULL");
-    *out = nullptr;
-    AFSAI_TRY(check_params(params));
-    auto st = static_cast<cudaStream_t>(stream);
-    int32_t maxrow = 0;
-    AFSAI_TRY(validate_csr(A, st, &maxrow));
-    afsai_precond* M = new (std::nothrow) afsai_precond();
-    if (!M) return fail(AFSAI_ENOMEM, "host allocation");
-    cudaGetDevice(&M->device);
-    M->params = *params;
-    const afsai_status s = setup_impl(A, params, maxrow, st, M);
-    if (s != AFSAI_OK) {
-        const std::string msg = g_last_error;
-        destroy_precond(M, st);
-        g_last_error = msg;
-        return s;
-    }
-    *out = M;
-    return AFSAI_OK;
+    return setup_precond(A, params, static_cast<cudaStream_t>(stream), true, out);
 }
 
 afsai_status afsai_apply(const afsai_precond* M, const double* r, double* z, void* stream) {

@@ -611,7 +611,7 @@ afsai_status batch_setup(int32_t nsys, const afsai_csr* A, const afsai_params* p
     if (hbad) return fail(AFSAI_EINVAL, "a system has malformed row pointers");
     afsai_csr packed{static_cast<int32_t>(nrows), nnz_total, prp.p, pcol.p, pval.p};
     afsai_precond* M = nullptr;
-    AFSAI_TRY(afsai_setup(&packed, p, st, &M));
+    AFSAI_TRY(setup_precond(&packed, p, st, false, &M));
     kb_localize<<<blocks, 256, 0, st>>>(nsys, droff.p, M->G.rowptr, nrows, M->G.col);
     kb_localize<<<blocks, 256, 0, st>>>(nsys, droff.p, M->Gt.rowptr, nrows, M->Gt.col);
     AFSAI_CUDA_TRY(cudaGetLastError());

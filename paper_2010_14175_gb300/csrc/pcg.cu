@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <string>
 #include <type_traits>
 
 #include "afsai_internal.cuh"
@@ -161,10 +162,10 @@ template <int MODE>
 __global__ void k_spmv_A_dot(int32_t n, int64_t nnz, const int32_t* __restrict__ rowptr,
                              const int32_t* __restrict__ col, const double* __restrict__ val,
                              const double* __restrict__ p, double* __restrict__ q, Scalars* s, double* partials,
-                             int cap) {
+                             int cap, tiled::SellView sv) {
     if (s->done) return;
     EpiStoreDot<double> epi{q, p, 0.0};
-    if (!tiled::spmv_rows<MODE, double, double, double>(n, nnz, rowptr, col, val, p, cap, &s->err, epi)) {
+    if (!tiled::spmv_rows<MODE, double, double, double>(n, nnz, rowptr, col, val, p, cap, &s->err, epi, sv)) {
         abort_solve(s);
         return;
     }
@@ -233,10 +234,10 @@ __global__ void k_update_xr(int32_t n, double* __restrict__ x, double* __restric
 template <int MODE, typename VT, typename ACC>
 __global__ void k_spmv_G(int32_t n, int64_t nnz, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                          const VT* __restrict__ val, const double* __restrict__ r, ACC* __restrict__ t, Scalars* s,
-                         int cap, int init) {
+                         int cap, int init, tiled::SellView sv) {
     if (!init && s->done) return;
     EpiStore<ACC, ACC> epi{t};
-    if (!tiled::spmv_rows<MODE, VT, double, ACC>(n, nnz, rowptr, col, val, r, cap, &s->err, epi)) abort_solve(s);
+    if (!tiled::spmv_rows<MODE, VT, double, ACC>(n, nnz, rowptr, col, val, r, cap, &s->err, epi, sv)) abort_solve(s);
 }
 
 // ---- z = G^T t, rz' = r.z, beta -------------------------------------------
@@ -244,10 +245,10 @@ template <int MODE, typename VT, typename ACC>
 __global__ void k_spmv_Gt_dot(int32_t n, int64_t nnz, const int32_t* __restrict__ rowptr,
                               const int32_t* __restrict__ col, const VT* __restrict__ val, const ACC* __restrict__ t,
                               const double* __restrict__ r, double* __restrict__ z, Scalars* s, double* partials,
-                              int cap, int init) {
+                              int cap, int init, tiled::SellView sv) {
     if (!init && s->done) return;
     EpiStoreDot<ACC> epi{z, r, 0.0};
-    if (!tiled::spmv_rows<MODE, VT, ACC, ACC>(n, nnz, rowptr, col, val, t, cap, &s->err, epi)) {
+    if (!tiled::spmv_rows<MODE, VT, ACC, ACC>(n, nnz, rowptr, col, val, t, cap, &s->err, epi, sv)) {
         abort_solve(s);
         return;
     }
@@ -343,6 +344,12 @@ bool with_mode(int mode, F f) {
         case 6: f(std::integral_constant<int, 6>{}); return true;
         case 101: f(std::integral_constant<int, 101>{}); return true;
         case 102: f(std::integral_constant<int, 102>{}); return true;
+        case tiled::kModeSliced: f(std::integral_constant<int, tiled::kModeSliced>{}); return true;
+        case tiled::kModeSlicedPipe: f(std::integral_constant<int, tiled::kModeSlicedPipe>{}); return true;
+        case tiled::kModeSlicedPipe8: f(std::integral_constant<int, tiled::kModeSlicedPipe8>{}); return true;
+        case tiled::kModeSlicedPipeIlv: f(std::integral_constant<int, tiled::kModeSlicedPipeIlv>{}); return true;
+        case tiled::kModeSlicedStaged8: f(std::integral_constant<int, tiled::kModeSlicedStaged8>{}); return true;
+        case tiled::kModeSlicedStaged16: f(std::integral_constant<int, tiled::kModeSlicedStaged16>{}); return true;
         default: return false;
     }
 }
@@ -388,7 +395,7 @@ struct Launcher {
         const auto* v = static_cast<const double*>(A->val);
         with_mode(ma.mode, [&](auto Mc) {
             k_spmv_A_dot<decltype(Mc)::value><<<ma.blocks, ma.threads, ma.smem, st>>>(
-                A->n, A->nnz, A->rowptr, A->col, v, p, q, s, partials, ma.cap);
+                A->n, A->nnz, A->rowptr, A->col, v, p, q, s, partials, ma.cap, tiled::sell_view(A->sell));
         });
         AFSAI_CUDA_TRY(cudaGetLastError());
         count_launches(1);
@@ -400,11 +407,13 @@ struct Launcher {
         ACC* tt = reinterpret_cast<ACC*>(t);
         with_mode(mg.mode, [&](auto Mc) {
             k_spmv_G<decltype(Mc)::value, VT, ACC><<<mg.blocks, mg.threads, mg.smem, st>>>(
-                G.n, G.nnz, G.rowptr, G.col, static_cast<const VT*>(G.val), r, tt, s, mg.cap, init);
+                G.n, G.nnz, G.rowptr, G.col, static_cast<const VT*>(G.val), r, tt, s, mg.cap, init,
+                tiled::sell_view(G.sell));
         });
         with_mode(mt.mode, [&](auto Mc) {
             k_spmv_Gt_dot<decltype(Mc)::value, VT, ACC><<<mt.blocks, mt.threads, mt.smem, st>>>(
-                Gt.n, Gt.nnz, Gt.rowptr, Gt.col, static_cast<const VT*>(Gt.val), tt, r, z, s, partials, mt.cap, init);
+                Gt.n, Gt.nnz, Gt.rowptr, Gt.col, static_cast<const VT*>(Gt.val), tt, r, z, s, partials, mt.cap, init,
+                tiled::sell_view(Gt.sell));
         });
     }
 
@@ -451,9 +460,28 @@ int iters_per_graph() {
     return v;
 }
 
-afsai_status pcg_body(const CsrDev& A, const afsai_precond* M, const double* b, double* x, double rtol,
+// A sliced copy of A for one solve, freed when the solve ends.
+struct SlicedA {
+    CsrDev view;
+    cudaStream_t st;
+    ~SlicedA() { free_sell(&view.sell, st); }
+};
+
+afsai_status pcg_body(const CsrDev& Ain, const afsai_precond* M, const double* b, double* x, double rtol,
                       int32_t maxit, cudaStream_t st, cudaEvent_t ev0, cudaEvent_t ev1, pcg_info* info) {
-    const int32_t n = A.n;
+    const int32_t n = Ain.n;
+    // The matrix may change between solves, so its sliced copy is rebuilt
+    // for each solve (one pass over A) unless a CSR engine was chosen for
+    // this shape.  Without room for the copy the CSR engines serve.
+    SlicedA sa{Ain, st};
+    if (spmv_wants_sliced(ROLE_A, Ain)) {
+        const std::string keep = afsai_last_error();
+        if (build_sell(Ain, &sa.view.sell, st) != AFSAI_OK) {
+            cudaGetLastError();  // a failed allocation is not an error of the solve
+            set_error(keep);
+        }
+    }
+    const CsrDev& A = sa.view;
     DevBuf<double> vec, partials, trueres;
     DevBuf<Scalars> sc;
     const size_t vs = (static_cast<size_t>(n) + 31) / 32 * 32;  // 256-byte aligned vector stride

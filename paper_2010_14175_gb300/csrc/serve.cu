@@ -153,7 +153,7 @@ struct ServerImpl {
             if (!m.M) {
                 const auto t0 = Clock::now();
                 afsai_csr A{m.n, m.nnz, m.rowptr, m.col, m.val};
-                const afsai_status s = afsai_setup(&A, &params, st, &m.M);
+                const afsai_status s = setup_precond(&A, &params, st, false, &m.M);
                 if (s != AFSAI_OK) {
                     R.state = Q_FAIL;
                     R.error = afsai_last_error();

@@ -1748,7 +1748,7 @@ int lanes_per_row(int mcap_t, bool chol32) {
 }  // namespace
 
 afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_row_nnz, cudaStream_t st,
-                        afsai_precond* M) {
+                        afsai_precond* M, bool sliced) {
     const int32_t n = A->n;
     const int64_t mcap = 1 + static_cast<int64_t>(p->kiter) * p->s;
     if (mcap > 128) return fail(AFSAI_ENOTSUP, "1 + kiter*s must be <= 128");
@@ -1914,6 +1914,10 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
     }
     AFSAI_CUDA_TRY(cudaMemcpyAsync(&G.max_row, counters.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     AFSAI_TRY(build_transpose(G, &M->Gt, st));
+    if (sliced) {
+        AFSAI_TRY(build_sell(G, &G.sell, st));
+        AFSAI_TRY(build_sell(M->Gt, &M->Gt.sell, st));
+    }
     AFSAI_CUDA_TRY(cudaEventRecord(ev1, st));
     AFSAI_CUDA_TRY(cudaEventSynchronize(ev1));
     float ms = 0.f;

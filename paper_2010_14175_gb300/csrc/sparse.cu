@@ -8,6 +8,7 @@
 // memory coalescing (larger L): short rows (7-point stencils, rows of G) use
 // one lane per row, long rows (elasticity, 81 per row) use small groups.
 #include <algorithm>
+#include <cstdio>
 #include <climits>
 #include <cstdlib>
 #include <array>
@@ -185,12 +186,12 @@ __global__ void sort_rows_rank(int32_t n, const int32_t* __restrict__ rowptr, co
 template <int MODE, typename VT, typename XT, typename ACC, typename YT>
 __global__ void spmv_plain(int32_t n, int64_t nnz, const int32_t* __restrict__ rowptr,
                            const int32_t* __restrict__ col, const VT* __restrict__ val, const XT* __restrict__ x,
-                           YT* __restrict__ y, int cap, int32_t* errflag) {
+                           YT* __restrict__ y, int cap, int32_t* errflag, tiled::SellView sv) {
     struct Epi {
         YT* y;
         __device__ void row(int64_t i, ACC a) { y[i] = static_cast<YT>(a); }
     } epi{y};
-    tiled::spmv_rows<MODE, VT, XT, ACC>(n, nnz, rowptr, col, val, x, cap, errflag, epi);
+    tiled::spmv_rows<MODE, VT, XT, ACC>(n, nnz, rowptr, col, val, x, cap, errflag, epi, sv);
 }
 
 int grid_for(int64_t work_items, int threads) {
@@ -332,8 +333,45 @@ TiledPlan plan_tiled(int32_t n, int64_t nnz, int32_t max_row, size_t val_size, c
 
 namespace {
 
+int smem_per_sm() {
+    static int v = [] {
+        int dev = 0, b = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&b, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        return b > 0 ? b : 228 * 1024;
+    }();
+    return v;
+}
+
 bool make_mode(int mode, const CsrDev& C, SpmvMode* m) {
     m->mode = mode;
+    if (mode == tiled::kModeSlicedStaged8 || mode == tiled::kModeSlicedStaged16) {
+        // persistent: as many blocks of 4 warps as fit on an SM by shared memory
+        if (C.sell.nslices <= 0) return false;
+        const size_t vb = val_bytes(C.vtype);
+        const size_t per_warp = mode == tiled::kModeSlicedStaged8 ? tiled::staged_warp_bytes<8, 3>(vb)
+                                                                   : tiled::staged_warp_bytes<16, 2>(vb);
+        m->threads = 32 * tiled::kStagedWarps;
+        m->smem = per_warp * tiled::kStagedWarps;
+        const int per_sm = static_cast<int>(std::max<size_t>(
+            1, std::min<size_t>(static_cast<size_t>(smem_per_sm()) / (m->smem + 1024), 2048 / m->threads)));
+        m->blocks = static_cast<int>(std::max<int64_t>(
+            1, std::min<int64_t>(static_cast<int64_t>(num_sms()) * per_sm,
+                                 (C.sell.nslices + tiled::kStagedWarps - 1) / tiled::kStagedWarps)));
+        m->cap = 0;
+        return true;
+    }
+    if (mode >= tiled::kModeSliced && mode <= tiled::kModeSlicedPipeIlv) {
+        // one warp per slice; up to 16 blocks of 8 warps per SM, the warps
+        // striding over the slices beyond that
+        if (C.sell.nslices <= 0) return false;
+        m->threads = 256;
+        m->blocks = static_cast<int>(
+            std::max<int64_t>(1, std::min<int64_t>((C.sell.nslices + 7) / 8, static_cast<int64_t>(num_sms()) * 16)));
+        m->smem = 0;
+        m->cap = 0;
+        return true;
+    }
     if (mode > 100) {
         const TiledPlan pl = plan_tiled(C.n, C.nnz, C.max_row, val_bytes(C.vtype), C.col, C.val, mode - 100);
         if (!pl.ok) return false;
@@ -361,7 +399,7 @@ afsai_status launch_plain_mode(const SpmvMode& m, const CsrDev& C, const XT* x, 
     if (m.smem > 0)
         AFSAI_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(m.smem)));
     k<<<m.blocks, m.threads, m.smem, st>>>(C.n, C.nnz, C.rowptr, C.col, static_cast<const VT*>(C.val), x, y, m.cap,
-                                           error_flag());
+                                           error_flag(), tiled::sell_view(C.sell));
     AFSAI_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     return AFSAI_OK;
@@ -378,6 +416,17 @@ afsai_status launch_plain(const SpmvMode& m, const CsrDev& C, const XT* x, YT* y
         case 6: return launch_plain_mode<6, VT, XT, ACC, YT>(m, C, x, y, st);
         case 101: return launch_plain_mode<101, VT, XT, ACC, YT>(m, C, x, y, st);
         case 102: return launch_plain_mode<102, VT, XT, ACC, YT>(m, C, x, y, st);
+        case tiled::kModeSliced: return launch_plain_mode<tiled::kModeSliced, VT, XT, ACC, YT>(m, C, x, y, st);
+        case tiled::kModeSlicedPipe:
+            return launch_plain_mode<tiled::kModeSlicedPipe, VT, XT, ACC, YT>(m, C, x, y, st);
+        case tiled::kModeSlicedPipe8:
+            return launch_plain_mode<tiled::kModeSlicedPipe8, VT, XT, ACC, YT>(m, C, x, y, st);
+        case tiled::kModeSlicedPipeIlv:
+            return launch_plain_mode<tiled::kModeSlicedPipeIlv, VT, XT, ACC, YT>(m, C, x, y, st);
+        case tiled::kModeSlicedStaged8:
+            return launch_plain_mode<tiled::kModeSlicedStaged8, VT, XT, ACC, YT>(m, C, x, y, st);
+        case tiled::kModeSlicedStaged16:
+            return launch_plain_mode<tiled::kModeSlicedStaged16, VT, XT, ACC, YT>(m, C, x, y, st);
         default: return fail(AFSAI_EINVAL, "unknown SpMV mode");
     }
 }
@@ -402,18 +451,35 @@ afsai_status launch_role(int role, const SpmvMode& m, const CsrDev& C, const voi
                                                              static_cast<double*>(y), st);
 }
 
+// sliced: the matrix has a sliced copy (engine 200 is a candidate)
 struct ModeKey {
     int dev, role, vtype;
     int32_t n;
     int64_t nnz;
+    int sliced;
     bool operator<(const ModeKey& o) const {
-        return std::tie(dev, role, vtype, n, nnz) < std::tie(o.dev, o.role, o.vtype, o.n, o.nnz);
+        return std::tie(dev, role, vtype, n, nnz, sliced) < std::tie(o.dev, o.role, o.vtype, o.n, o.nnz, o.sliced);
     }
 };
+
+ModeKey key_of(int role, const CsrDev& C) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return ModeKey{dev, role, C.vtype, C.n, C.nnz, C.sell.nslices > 0 ? 1 : 0};
+}
 
 // engines chosen so far, per device, role and matrix shape
 std::mutex g_mode_mu;
 std::map<ModeKey, int> g_mode_cache;
+
+// AFSAI_SPMV_TUNE_LOG=1 prints each candidate's timing to stderr.
+bool tune_log() {
+    static const bool v = [] {
+        const char* e = std::getenv("AFSAI_SPMV_TUNE_LOG");
+        return e && *e && *e != '0';
+    }();
+    return v;
+}
 
 // Engine pinned by the environment for a role: AFSAI_SPMV_MODES = "a,g,gt"
 // (per role) or AFSAI_SPMV_MODE (all roles); 0 if none.
@@ -445,17 +511,29 @@ int spmv_engine_of(int role, int32_t n, int64_t nnz, int vtype) {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(g_mode_mu);
-    auto it = g_mode_cache.find(ModeKey{dev, role, vtype, n, nnz});
-    return it == g_mode_cache.end() ? 0 : it->second;
+    // the choice with a sliced copy first (the one PCG and apply use)
+    for (int sliced = 1; sliced >= 0; --sliced) {
+        auto it = g_mode_cache.find(ModeKey{dev, role, vtype, n, nnz, sliced});
+        if (it != g_mode_cache.end()) return it->second;
+    }
+    return 0;
+}
+
+bool spmv_wants_sliced(int role, const CsrDev& C) {
+    const int forced = forced_mode(role);
+    if (forced) return forced >= tiled::kModeSliced;
+    ModeKey key = key_of(role, C);
+    key.sliced = 1;
+    std::lock_guard<std::mutex> lock(g_mode_mu);
+    auto it = g_mode_cache.find(key);
+    return it == g_mode_cache.end() || it->second >= tiled::kModeSliced;
 }
 
 afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode* out, bool allow_tuning) {
     auto& mu = g_mode_mu;
     auto& cache = g_mode_cache;
     const int forced = forced_mode(role);
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const ModeKey key{dev, role, C.vtype, C.n, C.nnz};
+    const ModeKey key = key_of(role, C);
     if (forced && make_mode(forced, C, out)) {
         std::lock_guard<std::mutex> lock(mu);
         cache[key] = forced;
@@ -465,6 +543,17 @@ afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode*
         std::lock_guard<std::mutex> lock(mu);
         auto it = cache.find(key);
         if (it != cache.end() && make_mode(it->second, C, out)) return AFSAI_OK;
+        // without a sliced copy, a CSR engine chosen with one is taken as it
+        // is (the same engine, hence the same sums, for every solve)
+        if (!key.sliced) {
+            ModeKey k1 = key;
+            k1.sliced = 1;
+            auto it1 = cache.find(k1);
+            if (it1 != cache.end() && it1->second < tiled::kModeSliced && make_mode(it1->second, C, out)) {
+                cache[key] = it1->second;
+                return AFSAI_OK;
+            }
+        }
     }
     const double avg = C.n > 0 ? static_cast<double>(C.nnz) / C.n : 0.0;
     if (!allow_tuning) {
@@ -474,6 +563,14 @@ afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode*
     // time the candidates on this matrix
     std::vector<int> cand = {2, 3, 4, 6, 8, 101, 102};
     if (avg <= 16.0) cand.insert(cand.begin(), 1);
+    if (C.sell.nslices > 0) {
+        cand.push_back(tiled::kModeSliced);
+        cand.push_back(tiled::kModeSlicedPipe);
+        cand.push_back(tiled::kModeSlicedPipe8);
+        cand.push_back(tiled::kModeSlicedPipeIlv);
+        cand.push_back(tiled::kModeSlicedStaged8);
+        cand.push_back(tiled::kModeSlicedStaged16);
+    }
     DevBuf<double> xb, yb;
     AFSAI_TRY(xb.alloc(static_cast<size_t>(C.n), st));
     AFSAI_TRY(yb.alloc(static_cast<size_t>(C.n), st));
@@ -501,6 +598,9 @@ afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode*
             if (ms < 0.f || t < ms) ms = t;
         }
         if (ms < 0.f) break;
+        if (tune_log())
+            std::fprintf(stderr, "afsai spmv tuning: role %d n %d nnz %lld sliced %d engine %d: %.4f ms per launch\n",
+                         role, C.n, static_cast<long long>(C.nnz), key.sliced, mode, ms / 4.0f);
         if (best < 0 || ms < best_ms) {
             best = mode;
             best_ms = ms;
@@ -537,6 +637,7 @@ afsai_status apply_precond(const afsai_precond* M, const double* r, double* t, d
 }
 
 void free_csr(CsrDev* A, cudaStream_t st) {
+    free_sell(&A->sell, st);
     if (A->rowptr) cudaFreeAsync(A->rowptr, st);
     if (A->col) cudaFreeAsync(A->col, st);
     if (A->val) cudaFreeAsync(A->val, st);

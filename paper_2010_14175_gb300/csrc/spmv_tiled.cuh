@@ -279,14 +279,306 @@ __device__ __forceinline__ void spmv_grouped(int32_t n, const int32_t* __restric
     }
 }
 
+// The sliced copy of a matrix as the kernels see it (SellDev).
+struct SellView {
+    int32_t nslices;
+    int32_t nwin;  // sorting windows
+    const int32_t* kptr;
+    const int2* rowlen;
+    const int32_t* col;
+    const void* val;
+};
+
+inline SellView sell_view(const SellDev& S) {
+    return SellView{S.nslices, (S.nslices + kSellWindowSlices - 1) / kSellWindowSlices, S.kptr, S.rowlen, S.col,
+                    S.val};
+}
+
+// The engines sweep tasks (grid-stride).  In slice order (ILV = false) task
+// t is slice t: neighbouring warps take neighbouring rows, whose gathers
+// share lines of x.  Interleaved (ILV = true), tasks run over
+// 0 .. nwin * 128 - 1 and task t is slice (t mod nwin) * 128 + t / nwin:
+// the windows are taken in turn, so the slices that come first in their
+// window, the longest ones, are handed out first and the short ones fill
+// the end of the sweep (for matrices with uneven rows, such as G^T).  -1
+// marks a position past the end of a partial last window.
+template <bool ILV>
+__device__ __forceinline__ int64_t slice_tasks(const SellView& S) {
+    return ILV ? static_cast<int64_t>(S.nwin) * kSellWindowSlices : static_cast<int64_t>(S.nslices);
+}
+template <bool ILV>
+__device__ __forceinline__ int64_t slice_of(const SellView& S, int64_t t) {
+    if (!ILV) return t;
+    const int64_t sl = (t % S.nwin) * kSellWindowSlices + t / S.nwin;
+    return sl < S.nslices ? sl : -1;
+}
+
+// Sliced rows: one warp per slice of 32 rows, one lane per row, each row
+// summed in CSR order (the plain sequential sum).  Four entries per lane
+// are loaded before their fmas; lanes past their row's length skip both.
+template <typename VT, typename XT, typename ACC, class Epi>
+__device__ __forceinline__ void spmv_sliced(const SellView& S, const XT* __restrict__ x, Epi& epi) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    const VT* __restrict__ sval = static_cast<const VT*>(S.val);
+    const int64_t ntasks = slice_tasks<false>(S);
+    for (int64_t t = w0; t < ntasks; t += nw) {
+        const int64_t sl = slice_of<false>(S, t);
+        if (sl < 0) continue;
+        const int32_t k0 = __ldg(&S.kptr[sl]);
+        const int32_t K = __ldg(&S.kptr[sl + 1]) - k0;
+        const int2 rl = __ldg(&S.rowlen[sl * 32 + lane]);
+        const int32_t* __restrict__ cp = S.col + static_cast<int64_t>(k0) * 32 + lane;
+        const VT* __restrict__ vp = sval + static_cast<int64_t>(k0) * 32 + lane;
+        ACC acc = ACC(0);
+        int32_t k = 0;
+        for (; k + 4 <= K; k += 4) {
+            int32_t c[4];
+            VT v[4];
+            XT xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool on = k + u < rl.y;
+                c[u] = on ? __ldg(cp + static_cast<int64_t>(k + u) * 32) : 0;
+                v[u] = on ? __ldg(vp + static_cast<int64_t>(k + u) * 32) : VT(0.0f);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) xv[u] = (k + u < rl.y) ? __ldg(&x[c[u]]) : XT(0);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (k + u < rl.y) acc = Mul<ACC>::fma_(v[u], xv[u], acc);
+        }
+        for (; k < K; ++k) {
+            if (k < rl.y) {
+                const int64_t o = static_cast<int64_t>(k) * 32;
+                acc = Mul<ACC>::fma_(__ldg(vp + o), __ldg(&x[__ldg(cp + o)]), acc);
+            }
+        }
+        if (rl.x >= 0) epi.row(rl.x, acc);
+    }
+}
+
+// Sliced rows, software-pipelined: the columns and values of the next U
+// entries are loaded while the current U are gathered and multiplied, so
+// each warp keeps its next HBM loads in flight across the dependent gathers
+// of x.  Same sums, in the same order, as spmv_sliced.
+template <int U, bool ILV, typename VT, typename XT, typename ACC, class Epi>
+__device__ __forceinline__ void spmv_sliced_pipe(const SellView& S, const XT* __restrict__ x, Epi& epi) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    const VT* __restrict__ sval = static_cast<const VT*>(S.val);
+    const int64_t ntasks = slice_tasks<ILV>(S);
+    for (int64_t t = w0; t < ntasks; t += nw) {
+        const int64_t sl = slice_of<ILV>(S, t);
+        if (sl < 0) continue;
+        const int32_t k0 = __ldg(&S.kptr[sl]);
+        const int32_t K = __ldg(&S.kptr[sl + 1]) - k0;
+        const int2 rl = __ldg(&S.rowlen[sl * 32 + lane]);
+        const int32_t* __restrict__ cp = S.col + static_cast<int64_t>(k0) * 32 + lane;
+        const VT* __restrict__ vp = sval + static_cast<int64_t>(k0) * 32 + lane;
+        int32_t cn[U];
+        VT vn[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool on = u < rl.y;
+            cn[u] = on ? __ldg(cp + static_cast<int64_t>(u) * 32) : 0;
+            vn[u] = on ? __ldg(vp + static_cast<int64_t>(u) * 32) : VT(0.0f);
+        }
+        ACC acc = ACC(0);
+        for (int32_t k = 0; k < K; k += U) {
+            int32_t c[U];
+            VT v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                c[u] = cn[u];
+                v[u] = vn[u];
+            }
+            if (k + U < K) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const bool on = k + U + u < rl.y;
+                    cn[u] = on ? __ldg(cp + static_cast<int64_t>(k + U + u) * 32) : 0;
+                    vn[u] = on ? __ldg(vp + static_cast<int64_t>(k + U + u) * 32) : VT(0.0f);
+                }
+            }
+            XT xv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) xv[u] = (k + u < rl.y) ? __ldg(&x[c[u]]) : XT(0);
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (k + u < rl.y) acc = Mul<ACC>::fma_(v[u], xv[u], acc);
+        }
+        if (rl.x >= 0) epi.row(rl.x, acc);
+    }
+}
+
+// Sliced rows staged by bulk copies: each warp owns a ring of NST
+// shared-memory stages, each holding CK k-steps of one slice (CK x 32
+// columns, CK x 32 values: two contiguous runs of the sliced arrays, so
+// two cp.async.bulk copies, completion counted on the stage's mbarrier).
+// The warp walks its slices (grid-stride over the tasks) chunk by chunk; lane 0 refills a
+// stage with the chunk NST ahead as soon as the warp has consumed it, so
+// the HBM stream of the next chunks is in flight while the lanes gather x
+// and run the fmas of the current one.  Same sums, in the same order, as
+// spmv_sliced.  Every wait is bounded: on expiry the warp raises the error
+// flag, waits once more (bounded) for each copy it still has in flight and
+// stops; the block then returns false in every thread.
+template <int CK, typename VT>
+struct StagedShape {
+    static constexpr uint32_t kColBytes = CK * 32 * 4;
+    static constexpr uint32_t kValBytes = CK * 32 * sizeof(VT);
+    static constexpr uint32_t kStage = kColBytes + kValBytes;
+    static_assert(CK % 4 == 0 && kStage % 128 == 0, "stage layout");
+};
+
+template <int CK, int NST>
+__host__ __device__ inline size_t staged_warp_bytes(size_t val_size) {
+    return static_cast<size_t>(NST) * (CK * 32 * 4 + CK * 32 * val_size) + 128;
+}
+
+template <int CK, int NST, typename VT, typename XT, typename ACC, class Epi>
+__device__ bool spmv_sliced_staged(const SellView& S, const XT* __restrict__ x, int32_t* errflag, Epi& epi) {
+    using SH = StagedShape<CK, VT>;
+    static_assert(NST >= 1 && NST <= 16, "stages");
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    unsigned char* wbase = smem + static_cast<size_t>(threadIdx.x >> 5) * (NST * SH::kStage + 128);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(wbase + NST * SH::kStage);
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < NST; ++j) mbar_init(&bars[j], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+    const int64_t w0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    const VT* __restrict__ sval = static_cast<const VT*>(S.val);
+
+    // issue cursor: chunk ikb of the slice of task it (warp-uniform)
+    const int64_t ntasks = slice_tasks<false>(S);
+    int64_t it = w0;
+    int32_t ikb = 0, ik0 = 0, iK = 0;
+    auto load_task = [&]() {
+        const int64_t is = it < ntasks ? slice_of<false>(S, it) : -1;
+        ikb = 0;
+        ik0 = is >= 0 ? __ldg(&S.kptr[is]) : 0;
+        iK = is >= 0 ? __ldg(&S.kptr[is + 1]) - ik0 : 0;
+    };
+    load_task();
+    auto issue = [&](int stage) -> bool {
+        while (it < ntasks && ikb >= iK) {
+            it += nw;
+            load_task();
+        }
+        if (it >= ntasks) return false;
+        const int32_t kn = iK - ikb < CK ? iK - ikb : CK;
+        if (lane == 0) {
+            const uint32_t cb = static_cast<uint32_t>(kn) * 128u;
+            const uint32_t vb = static_cast<uint32_t>(kn) * 32u * static_cast<uint32_t>(sizeof(VT));
+            unsigned char* st = wbase + stage * SH::kStage;
+            const int64_t off = (static_cast<int64_t>(ik0) + ikb) * 32;
+            fence_proxy_async();
+            mbar_arrive_expect_tx(&bars[stage], cb + vb);
+            bulk_g2s(st, S.col + off, cb, &bars[stage]);
+            bulk_g2s(st + SH::kColBytes, sval + off, vb, &bars[stage]);
+        }
+        ikb += CK;
+        return true;
+    };
+
+    int inflight = 0;
+    for (int j = 0; j < NST; ++j)
+        if (issue(j)) ++inflight;
+    int stage = 0;
+    uint32_t parity = 0;  // bit j: phase parity awaited on stage j
+    bool ok_warp = true;
+    for (int64_t t = w0; t < ntasks && ok_warp; t += nw) {
+        const int64_t sl = slice_of<false>(S, t);
+        if (sl < 0) continue;
+        const int32_t K = __ldg(&S.kptr[sl + 1]) - __ldg(&S.kptr[sl]);
+        const int2 rl = __ldg(&S.rowlen[sl * 32 + lane]);
+        ACC acc = ACC(0);
+        for (int32_t kb = 0; kb < K; kb += CK) {
+            const bool ok = mbar_wait(&bars[stage], (parity >> stage) & 1u);
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0 && errflag) atomicExch(errflag, 1);
+                // bounded second wait for every copy this warp has in flight
+                for (int t = 0, j = stage; t < inflight; ++t, j = (j + 1) % NST)
+                    mbar_wait(&bars[j], (parity >> j) & 1u);
+                __syncwarp();
+                ok_warp = false;
+                break;
+            }
+            parity ^= 1u << stage;
+            --inflight;
+            const int32_t* sc = reinterpret_cast<const int32_t*>(wbase + stage * SH::kStage);
+            const VT* sv = reinterpret_cast<const VT*>(wbase + stage * SH::kStage + SH::kColBytes);
+#pragma unroll
+            for (int g = 0; g < CK; g += 4) {
+                int32_t c[4];
+                VT v[4];
+                XT xv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const bool on = kb + g + u < rl.y;
+                    c[u] = on ? sc[(g + u) * 32 + lane] : 0;
+                    v[u] = on ? sv[(g + u) * 32 + lane] : VT(0.0f);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) xv[u] = (kb + g + u < rl.y) ? __ldg(&x[c[u]]) : XT(0);
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (kb + g + u < rl.y) acc = Mul<ACC>::fma_(v[u], xv[u], acc);
+            }
+            __syncwarp();  // every lane is done with the stage before it is refilled
+            if (issue(stage)) ++inflight;
+            stage = stage + 1 == NST ? 0 : stage + 1;
+        }
+        if (ok_warp && rl.x >= 0) epi.row(rl.x, acc);
+    }
+    // one block-uniform verdict (the callers' reductions use block barriers)
+    return __syncthreads_and(ok_warp) != 0;
+}
+
+constexpr int kModeSliced = 200;
+constexpr int kModeSlicedPipe = 201;
+constexpr int kModeSlicedPipe8 = 202;
+constexpr int kModeSlicedPipeIlv = 203;   // 201 with the windows interleaved
+constexpr int kModeSlicedStaged8 = 210;   // 8 k-steps per stage, 3 stages
+constexpr int kModeSlicedStaged16 = 211;  // 16 k-steps per stage, 2 stages
+constexpr int kStagedWarps = 4;           // warps per block of the staged engines
+
 // SpMV row engine.  MODE 1, 2, 4, 8: strided with MODE lanes per row;
 // MODE 3, 6: grouped with MODE lanes per row; MODE 101, 102: TMA-staged
-// tiles with MODE - 100 threads per row.
+// tiles with MODE - 100 threads per row; MODE 200 - 203: the sliced copy,
+// one lane per row (201, 202 software-pipelined by 4 and 8 entries, 203 as
+// 201 with the windows interleaved);
+// MODE 210, 211: the sliced copy staged through shared memory by bulk
+// copies (8 k-steps x 3 stages, 16 k-steps x 2 stages per warp).
 template <int MODE, typename VT, typename XT, typename ACC, class Epi>
 __device__ __forceinline__ bool spmv_rows(int32_t n, int64_t nnz, const int32_t* __restrict__ rowptr,
                                           const int32_t* __restrict__ col, const VT* __restrict__ val,
-                                          const XT* __restrict__ x, int cap, int32_t* errflag, Epi& epi) {
-    if constexpr (MODE > 100) {
+                                          const XT* __restrict__ x, int cap, int32_t* errflag, Epi& epi,
+                                          const SellView& sv) {
+    if constexpr (MODE == kModeSliced) {
+        spmv_sliced<VT, XT, ACC>(sv, x, epi);
+        return true;
+    } else if constexpr (MODE == kModeSlicedPipe) {
+        spmv_sliced_pipe<4, false, VT, XT, ACC>(sv, x, epi);
+        return true;
+    } else if constexpr (MODE == kModeSlicedPipe8) {
+        spmv_sliced_pipe<8, false, VT, XT, ACC>(sv, x, epi);
+        return true;
+    } else if constexpr (MODE == kModeSlicedPipeIlv) {
+        spmv_sliced_pipe<4, true, VT, XT, ACC>(sv, x, epi);
+        return true;
+    } else if constexpr (MODE == kModeSlicedStaged8) {
+        return spmv_sliced_staged<8, 3, VT, XT, ACC>(sv, x, errflag, epi);
+    } else if constexpr (MODE == kModeSlicedStaged16) {
+        return spmv_sliced_staged<16, 2, VT, XT, ACC>(sv, x, errflag, epi);
+    } else if constexpr (MODE > 100) {
         return spmv_tiles<MODE - 100, VT, XT, ACC>(n, nnz, rowptr, col, val, x, cap, errflag, epi);
     } else if constexpr (MODE == 3 || MODE == 6) {
         spmv_grouped<MODE, VT, XT, ACC>(n, rowptr, col, val, x, epi);
@@ -317,6 +609,11 @@ enum SpmvRole : int { ROLE_A = 0, ROLE_G = 1, ROLE_GT = 2 };
 // allocated: the cached engine is used if there is one, else a default
 // chosen from the average row length.
 afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode* out, bool allow_tuning = true);
+
+// Whether a sliced copy of C would serve `role`: the engine is pinned to
+// the sliced one, or it has not been chosen yet for this shape with a
+// sliced copy, or the sliced engine was chosen.
+bool spmv_wants_sliced(int role, const CsrDev& C);
 
 // y = C x with the engine `m` and the value/vector types of `role`.
 afsai_status spmv_launch_role(int role, const SpmvMode& m, const CsrDev& C, const void* x, void* y, cudaStream_t st);

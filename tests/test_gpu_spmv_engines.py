@@ -1,0 +1,89 @@
+"""Every SpMV row engine, pinned in turn for A, G and G^T, against the
+CPU oracle through the C ABI.
+
+The engine autotuner picks one engine per matrix shape, so the parity tests
+elsewhere see only the engines it happened to pick.  Here each engine is
+pinned (AFSAI_SPMV_MODE, read once per process, so one subprocess per
+engine) and must give: afsai_apply = G^T (G r) of the oracle within the
+rounding bound of the sums, and PCG at 1e-8 within one iteration of the
+oracle.  Matrices: a 7-point Poisson cube (8,000 rows: two sorting windows
+of the sliced layout), a Laplacian with hub rows coupled to 300 nodes
+(row lengths 4 to ~300, 1,000 rows: a ragged last slice), a small
+elasticity problem, and a 5-row tridiagonal matrix (one partial slice)."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+ENGINES = [1, 2, 3, 4, 6, 8, 101, 102, 200, 201, 202, 203, 210, 211]
+
+_SCRIPT = r'''
+import sys
+sys.path.insert(0, {root!r})
+import numpy as np, scipy.sparse as sp, torch
+import oracle
+from paper_2010_14175_gb300 import afsai, matgen as mg
+
+mode = {mode}
+oracle.build()
+afsai.load()
+
+def hubs(n_side=10, nh=5, deg=300, seed=11):
+    L = mg.poisson7(n_side).to_scipy().tolil()
+    rng = np.random.default_rng(seed)
+    n = L.shape[0]
+    for h in range(nh):
+        for j in rng.choice(n, size=deg, replace=False):
+            if j != h:
+                L[h, j] = L[j, h] = -0.01
+    L = L.tocsr()
+    off = abs(L - sp.diags(L.diagonal())).sum(axis=1).A.ravel()
+    return mg.from_scipy(sp.csr_matrix(L - sp.diags(L.diagonal()) + sp.diags(off + 1.0)))
+
+cases = [("poisson20", mg.poisson7(20), 5, 2), ("hubs", hubs(), 4, 2),
+         ("elast5", mg.elasticity_hex(5, 3), 10, 3), ("tri5", mg.laplace1d(5), 2, 1)]
+for name, A, kiter, s in cases:
+    ref = oracle.afsai_setup(A, kiter, s, 1e-3)
+    Ad = afsai.DeviceCSR.from_host(A)
+    M = afsai.afsai_setup(Ad, afsai.params(kiter, s, 1e-3))
+    r = np.random.default_rng(5).standard_normal(A.n)
+    z = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    afsai.afsai_apply(M, torch.from_numpy(r).cuda(), z)
+    zo = oracle.apply(ref, r)
+    absG = abs(ref.to_scipy())
+    bound = 64 * np.finfo(float).eps * (absG.T @ (absG @ np.abs(r)))
+    err = np.abs(z.cpu().numpy() - zo)
+    assert np.all(err <= bound + 1e-300), (name, float((err - bound).max()))
+    b, _ = mg.rhs(A, mg.BASE_SEED + 5)
+    xo, it_o, _, _ = oracle.pcg(A, ref, b, rtol=1e-8)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    info = afsai.pcg_solve(Ad, M, bd, x, rtol=1e-8, maxit=20000)
+    assert info["converged"] == 1 and abs(info["iters"] - it_o) <= 1, (name, info["iters"], it_o)
+    assert info["relres_true"] <= 1.05e-8, (name, info["relres_true"])
+    if mode in (1, 2, 3, 4, 6, 8, 200, 201, 202, 203, 210, 211):
+        nnz_g = int(ref.rowptr[-1])
+        got = (afsai.spmv_engine(0, A.n, A.nnz), afsai.spmv_engine(1, A.n, nnz_g), afsai.spmv_engine(2, A.n, nnz_g))
+        assert got == (mode, mode, mode), (name, got)
+print("ok")
+'''
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.mark.parametrize("mode", ENGINES)
+def test_engine_pinned(gpu, mode):
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = {k: v for k, v in os.environ.items() if k != "AFSAI_SPMV_MODES"}
+    env["AFSAI_SPMV_MODE"] = str(mode)
+    out = subprocess.run([sys.executable, "-c", _SCRIPT.format(root=root, mode=mode)], env=env,
+                         capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0 and out.stdout.strip().endswith("ok"), (out.stdout[-1000:], out.stderr[-3000:])
