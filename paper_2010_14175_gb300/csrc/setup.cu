@@ -1915,8 +1915,15 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
     AFSAI_CUDA_TRY(cudaMemcpyAsync(&G.max_row, counters.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     AFSAI_TRY(build_transpose(G, &M->Gt, st));
     if (sliced) {
-        AFSAI_TRY(build_sell(G, &G.sell, st));
-        AFSAI_TRY(build_sell(M->Gt, &M->Gt.sell, st));
+        // the sliced copies only serve the sliced SpMV engines: without
+        // room for them the CSR engines serve and the set-up succeeds
+        const std::string keep = afsai_last_error();
+        if (build_sell(G, &G.sell, st) != AFSAI_OK || build_sell(M->Gt, &M->Gt.sell, st) != AFSAI_OK) {
+            free_sell(&G.sell, st);
+            free_sell(&M->Gt.sell, st);
+            cudaGetLastError();
+            set_error(keep);
+        }
     }
     AFSAI_CUDA_TRY(cudaEventRecord(ev1, st));
     AFSAI_CUDA_TRY(cudaEventSynchronize(ev1));
