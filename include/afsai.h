@@ -135,7 +135,10 @@ typedef struct {
  * gradient |(A g_i)_j| (Eq. "grapsi"), solve A[P_i,P_i] g_i = e_m by
  * Cholesky (Eq. "DensSys"), stop after kiter steps or on the exit test
  * (Eq. "exit_crit"), and scale G[i,P_i] = g_i / sqrt(g_i,m) so that
- * diag(G A G^T) = I (Eq. "diagScal").  Then builds G^T.
+ * diag(G A G^T) = I (Eq. "diagScal").  Then builds G^T, and sliced
+ * (SELL-32) copies of G and G^T for the one-lane-per-row SpMV engines
+ * (about twice the memory of G and G^T; skipped, without error, when the
+ * device has no room for them).
  *   A       device pointers; must stay valid during the call only.
  *   params  host pointer.
  *   out     receives a new handle (free with afsai_destroy).
@@ -147,7 +150,8 @@ typedef struct {
 AFSAI_API afsai_status afsai_setup(const afsai_csr* A, const afsai_params* params, void* stream, afsai_precond** out);
 
 /* z = G^T (G r), the preconditioner application M^{-1} r (Eq. "prec"), as
- * two CSR SpMVs (G, then the stored G^T; Section 3 "miniwarp" SpMV).
+ * two SpMVs (G, then the stored G^T; Section 3 "miniwarp" SpMV), on the CSR
+ * or the sliced copies, whichever engine the autotuner chose.
  * r, z: device vectors of n doubles (must not overlap).  Asynchronous. */
 AFSAI_API afsai_status afsai_apply(const afsai_precond* M, const double* r, double* z, void* stream);
 
@@ -180,6 +184,9 @@ AFSAI_API afsai_status afsai_spmv(const afsai_csr* A, const double* x, double* y
  * the recursive residual satisfies ||r_k||_2 <= rtol ||b||_2 (Section 5.2:
  * 8 orders of reduction for rtol = 1e-8) or after maxit iterations.  The
  * iteration runs on the device (CUDA graphs); the host only polls a flag.
+ * When the SpMV engine of A is a sliced one (or not chosen yet), the solve
+ * builds a sliced copy of A for its own use (about the memory of A, freed
+ * before it returns; without room for it the CSR engines serve).
  * Synchronises `stream`.  info (host, may be NULL) receives the outcome.
  * Returns OK, ENOCONV (maxit reached), EINVAL, ENOMEM, ECUDA. */
 AFSAI_API afsai_status pcg_solve(const afsai_csr* A, const afsai_precond* M, const double* b, double* x, double rtol,
