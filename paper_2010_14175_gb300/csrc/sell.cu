@@ -9,6 +9,9 @@
 // vary (the rows of G^T are the column counts of G: 1 to ~80 on 3D
 // problems) while the window bounds how far the rows of a slice lie apart.
 //
+// A copy whose padding would exceed the matrix's own entries is not built
+// (the CSR engines serve such matrices).
+//
 // Build: (1) one block per window sorts its rows by (decreasing length,
 // increasing index) with a bitonic network on 32-bit keys in shared memory;
 // (2) one warp per slice takes the longest row of the slice; (3) an
@@ -134,6 +137,10 @@ afsai_status build_sell(const CsrDev& C, SellDev* S, cudaStream_t st) {
     int64_t kslots = 0;
     AFSAI_TRY(exclusive_scan_i32(kcount.p, kptr.p, nslices, st, &kslots));
     const int64_t nslots = kslots * 32;
+    // a few very long rows (an arrowhead matrix) pad their slices to their
+    // length: past twice the entries the copy is not built
+    if (nslots > 2 * C.nnz + 32 * static_cast<int64_t>(kSellWindowSlices))
+        return fail(AFSAI_ENOTSUP, "sliced copy not built: padding would exceed the matrix entries");
     const size_t vb = val_bytes(C.vtype);
     DevBuf<int32_t> scol;
     DevBuf<unsigned char> sval;
