@@ -8,7 +8,9 @@ rows and seeded random row ranges): their patterns and FP64 values must be
 identical.  The solves are checked by properties that hold at any size:
 convergence to the true residual 1e-8, the oracle's iteration count +-1 for
 the elasticity case (the full oracle solve takes seconds there), and at most
-10% more iterations for the mixed form than for FP64."""
+10% more iterations for the mixed form than for FP64.  For the elasticity
+case the preconditioner application (the engines the solve chose) is also
+compared with the full oracle G^T (G r) within the rounding bound."""
 import numpy as np
 import pytest
 
@@ -65,6 +67,16 @@ def test_elasticity48_full_size(gpu, oracle_mod):
     # full oracle solve (set-up + PCG) for the iteration count
     G = oracle_mod.afsai_setup(A, p["kiter"], p["s"], p["eps"])
     assert G.nnz == M.info()["nnz_G"]
+    # the preconditioner application in the engines the solve used, against
+    # the oracle's G^T (G r) within the rounding bound of the sums
+    import torch
+
+    r = np.random.default_rng(11).standard_normal(A.n)
+    z = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    gpu.afsai_apply(M, torch.from_numpy(r).cuda(), z)
+    absG = abs(G.to_scipy())
+    bound = 64 * np.finfo(float).eps * (absG.T @ (absG @ np.abs(r)))
+    assert np.all(np.abs(z.cpu().numpy() - oracle_mod.apply(G, r)) <= bound + 1e-300)
     _, it_o, _, _ = oracle_mod.pcg(A, G, b, rtol=1e-8, maxit=20000)
     assert abs(info["iters"] - it_o) <= 1, (info["iters"], it_o)
     # mixed form on the same input
