@@ -34,25 +34,47 @@ _lib = None
 OK, EINVAL, ENOMEM, ENOTSPD = 0, 1, 2, 3
 
 
+def _compile(src: str, out: str) -> None:
+    base = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11", "-o", out, src, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle shared library with gcc (OpenMP if available)."""
     os.makedirs(_BUILD, exist_ok=True)
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
         return _LIB
-    base = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11", "-o", _LIB + ".tmp", _SRC, "-lm"]
-    try:
-        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
-    except subprocess.CalledProcessError:
-        subprocess.run(base, check=True, capture_output=True)
+    _compile(_SRC, _LIB + ".tmp")
     os.replace(_LIB + ".tmp", _LIB)
     return _LIB
+
+
+def build_variant(source_text: str, out_dir: str) -> str:
+    """Compile a modified copy of the oracle's C source into out_dir (same
+    flags) and return the library path.  For the tests that plant a mistake
+    in the oracle and check that its pins catch it; such a library is used
+    by a process that sets AFSAI_ORACLE_LIB to its path."""
+    src = os.path.join(out_dir, "afsai_oracle_variant.c")
+    with open(src, "w") as f:
+        f.write(source_text)
+    lib = os.path.join(out_dir, "libafsai_oracle_variant.so")
+    _compile(src, lib)
+    return lib
+
+
+def source_text() -> str:
+    with open(_SRC) as f:
+        return f.read()
 
 
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            path = build()
+            path = os.environ.get("AFSAI_ORACLE_LIB") or build()
             lib = ctypes.CDLL(path)
             P = ctypes.c_void_p
             i32, f64 = ctypes.c_int32, ctypes.c_double
