@@ -88,3 +88,24 @@ int main(void) {
     assert sizes[5] == afsai.Params.chol_prec.offset
     assert sizes[6] == afsai.PcgInfo.solve_ms.offset
     assert sizes[7] == afsai.Params.block_power.offset
+
+
+@pytest.mark.parametrize("bad,status", [
+    (dict(kiter=-1), "EINVAL"), (dict(s=0), "EINVAL"), (dict(eps=-1e-3), "EINVAL"), (dict(eps=float("nan")), "EINVAL"),
+    (dict(exit_mode=2), "EINVAL"), (dict(g_prec=3), "EINVAL"), (dict(chol_prec=2), "EINVAL"),
+    (dict(block_rows=-1), "EINVAL"), (dict(block_power=65), "EINVAL"), (dict(kiter=64, s=2), "ENOTSUP"),
+])
+def test_setup_parameter_checks_before_any_device_call(lib, bad, status):
+    """afsai_setup rejects bad parameters on the host, before it touches the
+    CSR or the device (so this runs without a GPU)."""
+    from paper_2010_14175_gb300 import afsai
+
+    p = dict(kiter=5, s=2, eps=1e-3, exit_mode=0, g_prec=0, chol_prec=0, block_rows=0, block_power=1)
+    p.update(bad)
+    prm = afsai.params(**p)
+    A = afsai.Csr()  # never read: the parameters are checked first
+    out = ctypes.c_void_p()
+    st = lib.afsai_setup(ctypes.byref(A), ctypes.byref(prm), None, ctypes.byref(out))
+    assert st == getattr(afsai, status)
+    assert out.value is None
+    assert lib.afsai_last_error()
