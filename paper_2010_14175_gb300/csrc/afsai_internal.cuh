@@ -123,6 +123,9 @@ namespace afsai {
 // entry points of the translation units
 // ---------------------------------------------------------------------------
 
+// Checks set-up parameters on the host (EINVAL / ENOTSUP with a message).
+afsai_status check_params(const afsai_params* p);
+
 // Validates a device CSR (see afsai.h); synchronises the stream.
 afsai_status validate_csr(const afsai_csr* A, cudaStream_t st, int32_t* max_row_nnz);
 

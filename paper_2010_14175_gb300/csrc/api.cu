@@ -60,19 +60,6 @@ bool is_device_pointer(const void* p) {
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-afsai_status check_params(const afsai_params* p) {
-    if (!p) return fail(AFSAI_EINVAL, "params is NULL");
-    if (p->kiter < 0) return fail(AFSAI_EINVAL, "kiter must be >= 0");
-    if (p->s < 1) return fail(AFSAI_EINVAL, "s must be >= 1");
-    if (!(p->eps >= 0.0)) return fail(AFSAI_EINVAL, "eps must be >= 0");
-    if (p->exit_mode != 0 && p->exit_mode != 1) return fail(AFSAI_EINVAL, "exit_mode must be 0 or 1");
-    if (p->g_prec < 0 || p->g_prec > 2) return fail(AFSAI_EINVAL, "g_prec must be 0, 1 or 2");
-    if (p->chol_prec != 0 && p->chol_prec != 1) return fail(AFSAI_EINVAL, "chol_prec must be 0 or 1");
-    if (1 + static_cast<int64_t>(p->kiter) * p->s > 128) return fail(AFSAI_ENOTSUP, "1 + kiter*s must be <= 128");
-    if (p->block_rows < 0) return fail(AFSAI_EINVAL, "block_rows must be >= 0");
-    if (p->block_power < 0 || p->block_power > 64) return fail(AFSAI_EINVAL, "block_power must be in [0, 64]");
-    return AFSAI_OK;
-}
 
 afsai_status check_csr_shape(const afsai_csr* A) {
     if (!A) return fail(AFSAI_EINVAL, "matrix is NULL");
@@ -159,6 +146,20 @@ afsai_status validate_csr(const afsai_csr* A, cudaStream_t st, int32_t* max_row_
     if (h[0] & 8) return fail(AFSAI_EINVAL, "CSR row without a diagonal entry");
     if (h[0] & 16) return fail(AFSAI_EINVAL, "non-positive diagonal entry (A is not SPD)");
     if (max_row_nnz) *max_row_nnz = h[1];
+    return AFSAI_OK;
+}
+
+afsai_status check_params(const afsai_params* p) {
+    if (!p) return fail(AFSAI_EINVAL, "params is NULL");
+    if (p->kiter < 0) return fail(AFSAI_EINVAL, "kiter must be >= 0");
+    if (p->s < 1) return fail(AFSAI_EINVAL, "s must be >= 1");
+    if (!(p->eps >= 0.0)) return fail(AFSAI_EINVAL, "eps must be >= 0");
+    if (p->exit_mode != 0 && p->exit_mode != 1) return fail(AFSAI_EINVAL, "exit_mode must be 0 or 1");
+    if (p->g_prec < 0 || p->g_prec > 2) return fail(AFSAI_EINVAL, "g_prec must be 0, 1 or 2");
+    if (p->chol_prec != 0 && p->chol_prec != 1) return fail(AFSAI_EINVAL, "chol_prec must be 0 or 1");
+    if (1 + static_cast<int64_t>(p->kiter) * p->s > 128) return fail(AFSAI_ENOTSUP, "1 + kiter*s must be <= 128");
+    if (p->block_rows < 0) return fail(AFSAI_EINVAL, "block_rows must be >= 0");
+    if (p->block_power < 0 || p->block_power > 64) return fail(AFSAI_EINVAL, "block_power must be in [0, 64]");
     return AFSAI_OK;
 }
 

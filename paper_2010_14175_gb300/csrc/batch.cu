@@ -742,6 +742,7 @@ extern "C" afsai_status afsai_batch_solve(int32_t nsys, const afsai_csr* A, cons
                                           const double* const* b, double* const* x, double rtol, int32_t maxit,
                                           void* stream, pcg_info* info, afsai_batch_info* binfo) {
     if (nsys <= 0 || !A || !params || !b || !x) return fail(AFSAI_EINVAL, "invalid batch arguments");
+    AFSAI_TRY(check_params(params));
     if (params->block_rows != 0) return fail(AFSAI_ENOTSUP, "the locality bound applies to single-system set-ups");
     if (maxit < 0 || !(rtol >= 0.0)) return fail(AFSAI_EINVAL, "invalid rtol or maxit");
     for (int32_t k = 0; k < nsys; ++k)

@@ -336,6 +336,7 @@ afsai_status serve_create(size_t mem_budget_bytes, int32_t max_slots, const afsa
     if (!out || !params || max_slots <= 0 || mem_budget_bytes == 0 || maxit <= 0)
         return fail(AFSAI_EINVAL, "invalid server arguments");
     *out = nullptr;
+    AFSAI_TRY(check_params(params));
     if (params->block_rows != 0) return fail(AFSAI_ENOTSUP, "the locality bound applies to single-system set-ups");
     auto* S = new (std::nothrow) afsai_server();
     if (!S) return fail(AFSAI_ENOMEM, "host allocation");

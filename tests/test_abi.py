@@ -109,3 +109,36 @@ def test_setup_parameter_checks_before_any_device_call(lib, bad, status):
     assert st == getattr(afsai, status)
     assert out.value is None
     assert lib.afsai_last_error()
+
+
+def test_batch_and_server_argument_checks_on_the_host(lib):
+    """afsai_batch_solve and the server entry points reject bad arguments
+    and bad set-up parameters on the host, before any device call."""
+    from paper_2010_14175_gb300 import afsai
+
+    good = afsai.params(5, 2, 1e-3)
+    bad = afsai.params(5, 0, 1e-3)  # s < 1
+    bounded = afsai.params(5, 2, 1e-3, block_rows=64)
+    A = afsai.Csr()
+    ptrs = (ctypes.c_void_p * 1)(0x1000)  # never dereferenced: the checks come first
+
+    def batch(nsys, prm, rtol=1e-8, maxit=100):
+        return lib.afsai_batch_solve(nsys, ctypes.addressof(A), ctypes.byref(prm), ctypes.addressof(ptrs),
+                                     ctypes.addressof(ptrs), rtol, maxit, None, None, None)
+
+    assert batch(0, good) == afsai.EINVAL
+    assert batch(1, bad) == afsai.EINVAL
+    assert batch(1, bounded) == afsai.ENOTSUP
+    assert batch(1, good, rtol=-1.0) == afsai.EINVAL
+    assert batch(1, good, maxit=-1) == afsai.EINVAL
+
+    out = ctypes.c_void_p()
+    assert lib.serve_create(0, 8, ctypes.byref(good), 100, 4, ctypes.byref(out)) == afsai.EINVAL
+    assert lib.serve_create(1 << 30, 0, ctypes.byref(good), 100, 4, ctypes.byref(out)) == afsai.EINVAL
+    assert lib.serve_create(1 << 30, 8, ctypes.byref(bad), 100, 4, ctypes.byref(out)) == afsai.EINVAL
+    assert lib.serve_create(1 << 30, 8, ctypes.byref(bounded), 100, 4, ctypes.byref(out)) == afsai.ENOTSUP
+    assert out.value is None
+    mid = ctypes.c_int32()
+    assert lib.serve_register(None, ctypes.byref(A), ctypes.byref(mid)) == afsai.EINVAL
+    ticket = ctypes.c_int64()
+    assert lib.serve_submit(None, 0, None, 1, 1e-8, ctypes.byref(ticket)) == afsai.EINVAL
