@@ -217,7 +217,9 @@ typedef struct {
  *           on entry and the solution on exit.
  *   info    host array of nsys pcg_info (may be NULL); binfo may be NULL.
  * Synchronises `stream`.  Returns OK, ENOCONV (some system reached maxit),
- * EINVAL, ENOTSPD, ENOTSUP, ENOMEM, ECUDA. */
+ * EINVAL (bad arguments or parameters, checked before any device work),
+ * ENOTSPD, ENOTSUP (1 + kiter*s > 128, or the locality bound, which applies
+ * to single-system set-ups only), ENOMEM, ECUDA. */
 AFSAI_API afsai_status afsai_batch_solve(int32_t nsys, const afsai_csr* A, const afsai_params* params,
                                          const double* const* b, double* const* x, double rtol, int32_t maxit,
                                          void* stream, pcg_info* info, afsai_batch_info* binfo);
@@ -251,8 +253,11 @@ typedef struct {
 
 /* Starts a server thread on the current device.  mem_budget_bytes bounds
  * the device memory of matrices + preconditioners + vectors; max_slots
- * bounds the systems on the GPU at once; params applies to every matrix;
- * iters_per_step = PCG iterations per server step (<= 0: 4). */
+ * bounds the systems on the GPU at once; params applies to every matrix
+ * (checked here as by afsai_setup: EINVAL or ENOTSUP; the locality bound
+ * block_rows > 0 is ENOTSUP); iters_per_step = PCG iterations per server
+ * step (<= 0: 4).  Errors: EINVAL (NULL out or params, max_slots <= 0, a
+ * zero budget, maxit <= 0, bad parameters), ENOTSUP, ENOMEM, ECUDA. */
 AFSAI_API afsai_status serve_create(size_t mem_budget_bytes, int32_t max_slots, const afsai_params* params,
                                     int32_t maxit, int32_t iters_per_step, afsai_server** out);
 /* Copies A (host or device CSR) to the device; *matrix_id names it in
