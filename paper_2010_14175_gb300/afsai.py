@@ -189,8 +189,22 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _ptr(t):
-    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+def _device_array(t, dtype_name, n, what):
+    """Device address of a contiguous CUDA tensor of n entries of the given
+    dtype.  The library reads and writes these addresses from its kernels,
+    so a host tensor, another dtype or a shorter tensor is refused here,
+    before the call (there is no CPU path)."""
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{what}: a CUDA tensor is required (the library has no CPU path)")
+    if str(t.dtype) != "torch." + dtype_name:
+        raise ValueError(f"{what}: dtype {dtype_name} expected, got {t.dtype}")
+    if not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"{what}: a contiguous tensor of {n} entries expected (got {t.numel()})")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _vec(t, n, what):
+    return _device_array(t, "float64", n, what)
 
 
 class DeviceCSR:
@@ -210,7 +224,10 @@ class DeviceCSR:
                    torch.from_numpy(np.ascontiguousarray(A.val, dtype=np.float64)).to(device))
 
     def c(self) -> Csr:
-        return Csr(self.n, self.nnz, self.rowptr.data_ptr(), self.col.data_ptr(), self.val.data_ptr())
+        rp = _device_array(self.rowptr, "int32", self.n + 1, "rowptr")
+        ci = _device_array(self.col, "int32", self.nnz, "col")
+        va = _device_array(self.val, "float64", self.nnz, "val")
+        return Csr(self.n, self.nnz, rp.value, ci.value, va.value)
 
 
 def params(kiter, s, eps, exit_mode=0, g_prec=0, chol_prec=0, block_rows=0, block_power=1) -> Params:
@@ -223,10 +240,17 @@ class Precond:
 
     def __init__(self, handle):
         self._h = handle
+        self._n = None
 
     @property
     def handle(self):
         return self._h
+
+    @property
+    def n(self) -> int:
+        if self._n is None:
+            self._n = self.info()["n"]
+        return self._n
 
     def info(self) -> dict:
         inf = Info()
@@ -275,24 +299,26 @@ def afsai_setup(A: DeviceCSR, prm: Params, stream=None) -> Precond:
 
 
 def afsai_apply(M: Precond, r, z, stream=None):
-    _check(load().afsai_apply(M.handle, _ptr(r), _ptr(z), _stream(stream)))
+    n = M.n
+    _check(load().afsai_apply(M.handle, _vec(r, n, "r"), _vec(z, n, "z"), _stream(stream)))
 
 
 def afsai_apply_static(M: Precond, r, z, stream=None):
     """z = G^T (G r) without any device allocation (n <= 2^20)."""
-    _check(load().afsai_apply_static(M.handle, _ptr(r), _ptr(z), _stream(stream)))
+    n = M.n
+    _check(load().afsai_apply_static(M.handle, _vec(r, n, "r"), _vec(z, n, "z"), _stream(stream)))
 
 
 def afsai_spmv(A: DeviceCSR, x, y, stream=None):
     csr = A.c()
-    _check(load().afsai_spmv(ctypes.byref(csr), _ptr(x), _ptr(y), _stream(stream)))
+    _check(load().afsai_spmv(ctypes.byref(csr), _vec(x, A.n, "x"), _vec(y, A.n, "y"), _stream(stream)))
 
 
 def pcg_solve(A: DeviceCSR, M, b, x, rtol=1e-8, maxit=10000, stream=None, raise_on_noconv=True) -> dict:
     inf = PcgInfo()
     csr = A.c()
-    st = load().pcg_solve(ctypes.byref(csr), M.handle if M is not None else None, _ptr(b), _ptr(x), float(rtol),
-                          int(maxit), _stream(stream), ctypes.byref(inf))
+    st = load().pcg_solve(ctypes.byref(csr), M.handle if M is not None else None, _vec(b, A.n, "b"),
+                          _vec(x, A.n, "x"), float(rtol), int(maxit), _stream(stream), ctypes.byref(inf))
     if st != OK and not (st == ENOCONV and not raise_on_noconv):
         _check(st)
     out = _as_dict(inf)
@@ -306,8 +332,8 @@ def afsai_batch_solve(As, prm: Params, bs, xs, rtol=1e-8, maxit=10000, stream=No
     Returns (list of per-system info dicts, batch info dict)."""
     n = len(As)
     csrs = (Csr * n)(*[A.c() for A in As])
-    bp = (ctypes.c_void_p * n)(*[b.data_ptr() for b in bs])
-    xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    bp = (ctypes.c_void_p * n)(*[_vec(b, A.n, f"b[{k}]").value for k, (A, b) in enumerate(zip(As, bs))])
+    xp = (ctypes.c_void_p * n)(*[_vec(x, A.n, f"x[{k}]").value for k, (A, x) in enumerate(zip(As, xs))])
     infos = (PcgInfo * n)()
     binfo = BatchInfo()
     st = load().afsai_batch_solve(n, ctypes.cast(csrs, ctypes.c_void_p), ctypes.byref(prm),
