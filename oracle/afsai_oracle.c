@@ -43,7 +43,9 @@
  *       ascending order, each row of A in CSR (ascending column) order,
  *       acc = fma(a_rj, g_r, acc) starting from acc = 0.
  *   R9  PCG: x0 = 0, stop when ||r_k||_2 <= rtol ||b||_2 for the recursive
- *       residual (Section 5.2: "reduce the initial residual of 8 orders").
+ *       residual (Section 5.2: "reduce the initial residual of 8 orders")
+ *       and the true residual ||b - A x_k||_2 meets the same tolerance;
+ *       while it does not, the iteration continues.
  *   R13 locality bound (Section 4): stripes are runs of block_rows
  *       consecutive rows (the last one may be shorter); Ahat includes the
  *       diagonal blocks; power 0 keeps each row inside its own stripe;
@@ -477,11 +479,25 @@ static double dot_seq(int32_t n, const double* a, const double* b) {
     return s;
 }
 
+/* ||b - A x||_2 (q: n entries of scratch). */
+static double true_residual_norm(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val,
+                                 const double* b, const double* x, double* q) {
+    oracle_spmv(n, rowptr, col, val, x, q);
+    for (int32_t i = 0; i < n; ++i) q[i] = b[i] - q[i];
+    return sqrt(dot_seq(n, q, q));
+}
+
 /*
  * Preconditioned conjugate gradients with M^{-1} = G^T G (reading R9).
  * x: output (x0 = 0).  G given in CSR (lower triangular).  Returns the
  * iteration count in *iters (maxit+1 if not converged), the recursive and
  * the true relative residual.  Dot products are plain sequential sums.
+ * Stopping rule (R9, Section 5.2 "8 orders" of residual reduction): once
+ * the recursive residual meets ||r_k|| <= rtol ||b||, the true residual
+ * ||b - A x_k|| is computed; the solve ends when it meets the same
+ * tolerance, otherwise the recurrence goes on (the extra iterations are
+ * counted) and the true residual is checked again after every iteration
+ * whose recursive residual meets the tolerance.
  */
 int oracle_pcg(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val, const int32_t* Grp,
                const int32_t* Gcol, const double* Gval, const double* b, double* x, double rtol, int32_t maxit,
@@ -517,7 +533,8 @@ int oracle_pcg(int32_t n, const int32_t* rowptr, const int32_t* col, const doubl
                 r[i] = fma(-alpha, q[i], r[i]);
             }
             rnorm = sqrt(dot_seq(n, r, r));
-            if (rnorm <= rtol * bnorm) {
+            if (rnorm <= rtol * bnorm &&
+                true_residual_norm(n, rowptr, col, val, b, x, q) <= rtol * bnorm) {
                 converged = 1;
                 break;
             }
@@ -530,9 +547,7 @@ int oracle_pcg(int32_t n, const int32_t* rowptr, const int32_t* col, const doubl
     }
     *iters = converged ? it : maxit + 1;
     *relres_rec = (bnorm > 0.0) ? rnorm / bnorm : 0.0;
-    oracle_spmv(n, rowptr, col, val, x, q);
-    for (int32_t i = 0; i < n; ++i) q[i] = b[i] - q[i];
-    *relres_true = (bnorm > 0.0) ? sqrt(dot_seq(n, q, q)) / bnorm : 0.0;
+    *relres_true = (bnorm > 0.0) ? true_residual_norm(n, rowptr, col, val, b, x, q) / bnorm : 0.0;
     free(r); free(z); free(p); free(q); free(t);
     return ORC_OK;
 }

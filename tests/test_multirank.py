@@ -56,15 +56,3 @@ def test_gloo_barrier_and_max_over_ranks(world):
         assert p.exitcode == 0
     assert sorted(r[0] for r in res) == list(range(world))
     assert all(r[1] == 10.0 * world for r in res)
-
-
-def test_replicas_value_is_units_over_max_time():
-    sys.path.insert(0, ROOT)
-    import bench
-
-    # value = max-over-ranks time / (steps * ranks): with 2 ranks each doing
-    # 5 solves in 1.0 s and 1.2 s, the job does 10 solves in 1.2 s
-    ms_total = max(1000.0, 1200.0)
-    steps, world = 5, 2
-    assert ms_total / 1e3 / (steps * world) == pytest.approx(0.12)
-    assert bench.max_over_ranks(3.0, 1) == 3.0

@@ -4,7 +4,8 @@ gradient, candidates from the wrong triangle, a reversed ranking or
 tie-break, a transposed operand in the Cholesky update, a missing square
 root, the wrong triangle in the back substitution, the printed scaling
 without its square root, an inverted exit test, an unsorted pattern, an
-inverted alpha or beta in PCG, G instead of G^T in the application, a
+inverted alpha or beta in PCG, a PCG that stops on the recursive residual
+alone, G instead of G^T in the application, a
 gather that drops the off-diagonal entries, a locality bound one power too
 wide), compiles it, and runs the pins of test_oracle_pins.py and
 test_oracle_locality.py against it in a child process.
@@ -67,6 +68,9 @@ MUTANTS = [
     ("PCG alpha inverted",
      "double alpha = rz / pq;",
      "double alpha = pq / rz;"),
+    ("PCG stops on the recursive residual alone",
+     "if (rnorm <= rtol * bnorm &&\n                true_residual_norm(n, rowptr, col, val, b, x, q) <= rtol * bnorm) {",
+     "if (rnorm <= rtol * bnorm) {"),
     ("locality bound one power too high",
      "for (int32_t t = 0; t < power; ++t) {",
      "for (int32_t t = 0; t <= power; ++t) {"),

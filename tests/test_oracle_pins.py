@@ -238,6 +238,47 @@ def test_pcg_matches_scipy_cg_with_afsai(oracle_mod):
     assert it < it0
 
 
+def _scaled_poisson_smooth_solution(N=10, decades=8):
+    """D A D for the 7-point Poisson matrix A and a diagonal D spanning
+    `decades` orders of magnitude, with b = (D A D) x* for a smooth x* in
+    the scaled variables: ||D A D|| ||x*|| / ||b|| is large, so the true
+    residual ||b - A x_k|| of CG stagnates near 5e-15 while the recursive
+    one keeps falling (a textbook property of finite-precision CG)."""
+    import scipy.sparse as sp
+
+    A0 = mg.poisson7(N).to_scipy()
+    n = A0.shape[0]
+    d = np.logspace(-decades / 2, decades / 2, n)
+    np.random.default_rng(3).shuffle(d)
+    S = sp.csr_matrix(sp.diags(d) @ A0 @ sp.diags(d))
+    S.sort_indices()
+    g = np.arange(1, N + 1)
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    mode = (np.sin(np.pi * X / (N + 1)) * np.sin(np.pi * Y / (N + 1)) * np.sin(np.pi * Z / (N + 1))).ravel(order="F")
+    return mg.from_scipy(S), S @ (mode / d)
+
+
+def test_pcg_stops_on_the_true_residual(oracle_mod):
+    """Reading R9 (Section 5.2, 8 orders of reduction of the residual): a
+    solve is converged only when the true residual meets the tolerance.
+    Below the attainable accuracy the recursive residual meets it while the
+    true one cannot, and the oracle must report no convergence; above it,
+    every converged solve has a true residual within the tolerance.  The
+    true residual is recomputed here with scipy, independently."""
+    A, b = _scaled_poisson_smooth_solution()
+    S = A.to_scipy()
+    G = oracle_mod.afsai_setup(A, 0, 1, 1e-3)  # Jacobi
+    bn = np.linalg.norm(b)
+    x, it, rr, rt = oracle_mod.pcg(A, G, b, rtol=1e-15, maxit=200)
+    assert it == 201, it  # maxit + 1: not converged
+    assert rr <= 1e-15 and rt > 1e-15
+    assert rt == pytest.approx(np.linalg.norm(b - S @ x) / bn, rel=1e-6)
+    for rtol in (1e-14, 3e-14, 1e-12, 1e-8):
+        x, it, rr, rt = oracle_mod.pcg(A, G, b, rtol=rtol, maxit=200)
+        assert it <= 200
+        assert np.linalg.norm(b - S @ x) / bn <= rtol
+
+
 def test_apply_is_gt_g(oracle_mod):
     A = mg.random_spd(50, 0.1, 31)
     G = oracle_mod.afsai_setup(A, 4, 2, 1e-3)
