@@ -1,27 +1,31 @@
 """Benchmark: aFSAI set-up + PCG to relative residual 1e-8 on one GB300.
 
-Workload (default): FP64 aFSAI-PCG on 3D linear elasticity, trilinear hex
-elements on a 48^3 grid, 3 dofs per node (n = 352,947, ~27M nonzeros),
-Young's modulus lognormal (sigma 1) per element, Poisson ratio 0.3, z = 0
-face clamped; kiter = 10, s = 3, eps = 1e-3; seeded right-hand side
-b = A x*, x* ~ U[-1, 1].  A step is one whole solve: aFSAI set-up (pattern
-search, gather, Cholesky, scaling, G^T) followed by PCG from x = 0 until
-||r|| <= 1e-8 ||b||, with A and b resident in device memory.  The metric is
-seconds per solve (lower is better).
+Workload (default): heterogeneous diffusion, cell-centred 7-point stencil on
+a 256^3 grid (n = 16,777,216, 117,047,296 nonzeros), lognormal coefficient
+(sigma 2, smoothed over 8 cells), harmonic face means; aFSAI kiter = 5,
+s = 2, eps = 1e-3; seeded right-hand side b = A x*, x* ~ U[-1, 1].  A step
+is one whole solve in the FP64 form: aFSAI set-up (pattern search, gather,
+Cholesky, scaling, G^T) followed by PCG from x = 0 until ||r|| <= 1e-8 ||b||
+(and the true residual too), with A and b resident in device memory.  The
+metric is seconds per solve (lower is better).  --workload elast48 runs the
+48^3 elasticity problem instead.
 
 Other keys of the JSON line:
+  forms        the other precision forms on the same input (FP32 G, BF16 G,
+               the mixed form with FP32 Cholesky + one FP64 refinement step,
+               and Jacobi), seconds per solve, iterations and the error of
+               their G against the FP64 G
   e2e          the same solve through afsai_solve_host from pinned host
                buffers (H2D of A and b, D2H of x inside the timed region)
-  mixed        the precision form on the same input (FP32 G, FP32 Cholesky
-               with one FP64 refinement step), seconds per solve
   roofline     the dominant kernel against its roof (measured with CUDA
                events on the launching stream inside the timed region)
   cpu_baseline the FP64 CPU oracle on a bounded sample of the same solve,
-               scaled to seconds per solve
+               at all cores and at one thread, scaled to seconds per solve
   clocks       SM clocks and throttle reasons sampled during the timed region
 
 --impl reference times the CPU oracle (the only reference this method has:
-the paper's code is not public) on the host cores for the same workload.
+the paper's code is not public) on the host cores: its timed steps add up
+to one whole oracle solve of the workload.
 Multi-GPU (--gpus N under torchrun): every rank solves its own copy of the
 workload (independent problems, no collective on the data path); value is
 the max-over-ranks time divided by the number of solves of all ranks.
@@ -100,7 +104,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the other precision forms")
-    ap.add_argument("--workload", default="elast48",
+    ap.add_argument("--workload", default="hetero256",
                     choices=["elast48", "hetero256", "poisson20", "batch512", "serve", "poisson_sweep"])
     ap.add_argument("--requests", type=int, default=2000, help="timed requests of the serve workload")
     ap.add_argument("--warm-requests", type=int, default=200)
@@ -291,52 +295,121 @@ def make_workload(name, scale):
     return A, b, p
 
 
-def cpu_oracle_estimate(A, b, p, iters, pcg_iters=10):
-    """The CPU oracle on a bounded sample of one solve: its full FP64 set-up
-    (timed) plus `pcg_iters` oracle PCG iterations with that G (timed),
-    scaled to `iters` iterations."""
+def job_value(ms_total, steps, world):
+    """Seconds per solve of the whole job: the max-over-ranks time of the
+    timed region divided by the solves of all ranks (each rank solves its
+    own copy of the workload: replicas, weak scaling)."""
+    return ms_total / 1e3 / (steps * world)
+
+
+def _cpu_model():
+    try:
+        for line in subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
+def _middle_rows(n, frac):
+    k = max(1, int(n * frac))
+    r0 = max(0, n // 2 - k // 2)
+    return r0, min(n, r0 + k)
+
+
+def cpu_oracle_sample(A, b, p, iters, setup_frac_1t=1 / 32, pcg_iters_all=2, pcg_iters_1t=1):
+    """The CPU oracle (as it stands) on a bounded sample of one solve, at
+    all cores and at one thread, scaled to seconds per solve:
+      all cores  the full oracle set-up (timed; its G serves the PCG
+                 timings) + `pcg_iters_all` oracle PCG iterations (timed),
+                 scaled to `iters` iterations;
+      one thread the set-up of a block of rows from the middle of the
+                 matrix (`setup_frac_1t` of the rows; rows are independent)
+                 scaled to all rows + `pcg_iters_1t` PCG iterations scaled
+                 to `iters`.
+    `iters` is the FP64 iteration count of the solve being compared."""
     import oracle
 
+    cores = oracle.num_threads()
     t0 = time.perf_counter()
     G = oracle.afsai_setup(A, p["kiter"], p["s"], p["eps"])
     t_setup = time.perf_counter() - t0
     t0 = time.perf_counter()
-    oracle.pcg(A, G, b, rtol=1e-300, maxit=pcg_iters)
-    t_it = (time.perf_counter() - t0) / pcg_iters
-    return t_setup + t_it * iters, oracle.num_threads(), (
-        f"full oracle set-up ({t_setup:.2f} s) + {pcg_iters} oracle PCG iterations "
-        f"({t_it * 1e3:.1f} ms each) scaled to {iters} iterations")
+    oracle.pcg(A, G, b, rtol=1e-300, maxit=pcg_iters_all)
+    t_it = (time.perf_counter() - t0) / pcg_iters_all
+    all_cores = t_setup + t_it * iters
+    before = oracle.set_threads(1)
+    try:
+        r0, r1 = _middle_rows(A.n, setup_frac_1t)
+        t0 = time.perf_counter()
+        oracle.afsai_setup(A, p["kiter"], p["s"], p["eps"], rows=(r0, r1), nthreads=1)
+        t_setup1 = (time.perf_counter() - t0) * A.n / (r1 - r0)
+        t0 = time.perf_counter()
+        oracle.pcg(A, G, b, rtol=1e-300, maxit=pcg_iters_1t)
+        t_it1 = (time.perf_counter() - t0) / pcg_iters_1t
+    finally:
+        oracle.set_threads(before)
+    one = t_setup1 + t_it1 * iters
+    return {
+        "value": all_cores, "unit": "s/solve", "cores": cores, "kind": "oracle", "cpu": _cpu_model(),
+        "sample": (f"all {cores} cores: full oracle set-up ({t_setup:.2f} s, measured) + {pcg_iters_all} oracle PCG "
+                   f"iterations ({t_it * 1e3:.0f} ms each) scaled to {iters} iterations; the iteration count is "
+                   f"that of the FP64 solve timed on the GPU"),
+        "one_thread": {"value": one, "unit": "s/solve", "cores": 1,
+                       "sample": (f"set-up of rows [{r0}, {r1}) at one thread ({t_setup1:.1f} s scaled to all "
+                                  f"{A.n} rows) + {pcg_iters_1t} PCG iteration(s) at one thread "
+                                  f"({t_it1 * 1e3:.0f} ms each) scaled to {iters} iterations")},
+        "extrapolated": True,
+    }
 
 
 def run_reference(args, rank, world):
-    """--impl reference: the CPU oracle on the host cores (rank 0 only)."""
+    """--impl reference: the CPU oracle, as it stands, on the host cores
+    (rank 0 only; the other ranks return at once).  The K timed steps
+    together make up ONE whole oracle solve of the workload, measured and
+    not extrapolated: step k runs the oracle set-up of the k-th of K row
+    blocks (rows are independent, so the blocks add up to the full
+    set-up), and step 0 also runs the oracle's PCG from x = 0 to the 1e-8
+    stopping rule with the full G (built once before the timed steps).
+    value = the sum of the K step times = seconds for one whole solve."""
     if rank != 0:
-        return
+        return None
     import oracle
 
     A, b, p = make_workload(args.workload, args.scale)
-    # iteration count of the oracle's own full solve (measured once)
-    G = oracle.afsai_setup(A, p["kiter"], p["s"], p["eps"])
-    _, iters, _, rt = oracle.pcg(A, G, b, rtol=1e-8, maxit=20000)
-    del G
-    for _ in range(args.warmup):
-        cpu_oracle_estimate(A, b, p, iters)
-    vals = []
-    for _ in range(args.steps):
-        v, cores, sample = cpu_oracle_estimate(A, b, p, iters)
-        vals.append(v)
-    value = float(np.median(vals))
+    K = max(1, args.steps)
+    G = oracle.afsai_setup(A, p["kiter"], p["s"], p["eps"])  # the PCG's G (untimed)
+    bounds = [(A.n * k) // K for k in range(K + 1)]
+    for w in range(args.warmup):  # a small block each
+        r0, r1 = _middle_rows(A.n, min(0.01, 1.0 / K))
+        oracle.afsai_setup(A, p["kiter"], p["s"], p["eps"], rows=(r0, r1))
+    times, iters, rt = [], None, None
+    for k in range(K):
+        t0 = time.perf_counter()
+        if bounds[k + 1] > bounds[k]:
+            oracle.afsai_setup(A, p["kiter"], p["s"], p["eps"], rows=(bounds[k], bounds[k + 1]))
+        if k == 0:
+            _, iters, _, rt = oracle.pcg(A, G, b, rtol=1e-8, maxit=20000)
+        times.append(time.perf_counter() - t0)
+    value = float(sum(times))
+    cores = oracle.num_threads()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s/solve", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+        "steps": K, "warmup": args.warmup, "ms_per_step": value * 1e3 / K, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
         "config": {"workload": WORKLOAD_NAMES[args.workload] + "_fp64", "n": A.n, "nnz": A.nnz,
                    "kiter": p["kiter"], "s": p["s"], "eps": p["eps"], "rtol": 1e-8, "oracle_iters": iters,
                    "oracle_relres_true": rt},
-        "cpu_baseline": {"value": value, "unit": "s/solve", "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "s/solve", "cores": cores, "kind": "oracle", "cpu": _cpu_model(),
+                         "extrapolated": False,
+                         "sample": (f"one whole oracle solve split over the {K} timed steps: the set-up of "
+                                    f"{K} row blocks (one per step) and the PCG to 1e-8 ({iters} iterations, "
+                                    f"in step 0)")},
         "e2e": {"value": value, "unit": "s/solve", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+    return line
 
 
 def run_batch(args, rank, world, local):
@@ -717,7 +790,7 @@ def main():
     ms_total = ev0.elapsed_time(ev1)
     ms_total = max_over_ranks(ms_total, world, dev)
     M, sinfo, pinfo = last
-    value = ms_total / 1e3 / (args.steps * world)
+    value = job_value(ms_total, args.steps, world)
 
     # dominant kernel: the set-up's pattern-search kernels, timed together
     # with CUDA events around their launches (one set-up: the fused kernel,
@@ -812,8 +885,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, sample = cpu_oracle_estimate(A, b, p, int(np.median(iters)))
-        cpu = {"value": v, "unit": "s/solve", "cores": cores, "kind": "oracle", "sample": sample}
+        cpu = cpu_oracle_sample(A, b, p, int(np.median(iters)))
 
     if rank == 0:
         n_it = int(np.median(iters))

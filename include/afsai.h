@@ -138,7 +138,9 @@ typedef struct {
  * diag(G A G^T) = I (Eq. "diagScal").  Then builds G^T, and sliced
  * (SELL-32) copies of G and G^T for the one-lane-per-row SpMV engines
  * (about twice the memory of G and G^T; skipped, without error, when the
- * device has no room for them).
+ * device has no room for them).  The first successful set-up on a device
+ * also loads the 8 MiB device array of afsai_apply_static there (once per
+ * device, held until the process exits).
  *   A       device pointers; must stay valid during the call only.
  *   params  host pointer.
  *   out     receives a new handle (free with afsai_destroy).
@@ -162,11 +164,21 @@ AFSAI_API afsai_status afsai_apply(const afsai_precond* M, const double* r, doub
  * synchronise the device.  The paper has no counterpart; this is a service
  * entry point of the library.
  *   - Allocates nothing: the intermediate G r is kept in a fixed device
- *     array of 2^20 doubles (8 MiB) that every GPU which loads the library
- *     holds until the process exits.  n > 2^20 returns AFSAI_EINVAL.
- *   - The first call on a device looks up that array's device address
- *     (cudaGetSymbolAddress) with the device current; make this first call
- *     before any stream capture.
+ *     array of 2^20 doubles (8 MiB).  n > 2^20 returns AFSAI_EINVAL.
+ *   - The array is loaded into a device's memory when the library's
+ *     module that holds it is first used on that device (CUDA loads
+ *     modules lazily); afsai_setup does that, so after a successful
+ *     afsai_setup on a device the array is in place and stays until the
+ *     process exits or the device is reset.  If the set-up could not load
+ *     it (no device memory left at that moment), the first
+ *     afsai_apply_static on that device tries again and returns
+ *     AFSAI_ENOMEM if it still cannot; if that first attempt happens
+ *     during a stream capture, it returns AFSAI_EINVAL instead (loading is
+ *     not allowed during a capture).
+ *   - The array's device address is cached per device: after
+ *     cudaDeviceReset every handle of this library is invalid, and so is
+ *     that cached address; calls after a reset are not supported.
+ *   - M must belong to the current device (else AFSAI_EINVAL).
  *   - All calls share the array and it keeps the last call's contents;
  *     calls that overlap on the GPU (different streams, no ordering) race
  *     on it and give wrong results.  Calls on one stream are safe.

@@ -110,6 +110,22 @@ def num_threads() -> int:
     return int(_load().oracle_num_threads())
 
 
+def set_threads(k: int) -> int:
+    """Sets the OpenMP thread count of the oracle's parallel loops (the SpMV
+    of PCG, the set-up without an explicit ``nthreads``); returns the count
+    that was in effect.  For timing the oracle at one thread and at all
+    cores; no effect on any result (rows and SpMV rows are independent)."""
+    before = num_threads()
+    import ctypes.util
+
+    name = ctypes.util.find_library("gomp") or "libgomp.so.1"
+    try:
+        ctypes.CDLL(name).omp_set_num_threads(int(k))
+    except OSError:
+        pass
+    return before
+
+
 class OracleG:
     """Result of the oracle set-up: G in CSR (sorted columns) plus per-row
     psi (final Kaporin row measure) and number of enlargement steps."""

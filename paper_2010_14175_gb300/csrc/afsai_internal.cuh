@@ -155,6 +155,10 @@ afsai_status apply_precond(const afsai_precond* M, const double* r, double* t, d
 void free_csr(CsrDev* A, cudaStream_t st);
 int32_t* error_flag();  // device flag set by a bounded device-side wait that ran out
 
+// Loads the device array of afsai_apply_static on the current device
+// (apply_static.cu); best effort, called by afsai_setup.
+void static_apply_preload(cudaStream_t st);
+
 // PCG (pcg.cu).
 afsai_status pcg_impl(const afsai_csr* A, const afsai_precond* M, const double* b, double* x, double rtol,
                       int32_t maxit, cudaStream_t st, pcg_info* info);

@@ -181,6 +181,7 @@ afsai_status setup_precond(const afsai_csr* A, const afsai_params* params, cudaS
         g_last_error = msg;
         return s;
     }
+    if (sliced) static_apply_preload(st);
     *out = M;
     return AFSAI_OK;
 }

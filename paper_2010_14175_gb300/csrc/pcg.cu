@@ -18,6 +18,13 @@
 //
 // Residual, dot products, alpha and beta are FP64 whatever the precision of
 // G; with an FP32/BF16 G the two triangular products run in FP32.
+//
+// Stopping rule (Section 5.2, an 8-order reduction): the loop stops when
+// the recursive residual meets ||r_k|| <= rtol ||b|| (the same comparison
+// of square roots as the plain definition); the host then computes the
+// true residual ||b - A x_k||; if that is above rtol ||b|| the recurrence
+// continues one iteration at a time, with the true residual checked after
+// each, until it meets the tolerance or maxit is reached.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -39,7 +46,7 @@ struct Scalars {
     double beta;
     double rr;
     double bb;
-    double tol2;
+    double tolr;  // rtol ||b||
     int32_t done;  // 0 running, 1 converged, 2 maxit reached, 3 device wait expired
     int32_t iters;
     int32_t maxit;
@@ -121,9 +128,9 @@ __global__ void k_init_residual(int32_t n, const double* __restrict__ b, const d
     if (grid_sum<2>(v, partials, &s->ticket[0]) && threadIdx.x == 0) {
         s->rr = v[0];
         s->bb = v[1];
-        s->tol2 = rtol * rtol * v[1];
+        s->tolr = rtol * sqrt(v[1]);
         s->iters = 0;
-        s->done = (v[0] <= s->tol2) ? 1 : 0;
+        s->done = (sqrt(v[0]) <= s->tolr) ? 1 : 0;
     }
 }
 
@@ -162,10 +169,10 @@ template <int MODE>
 __global__ void k_spmv_A_dot(int32_t n, int64_t nnz, const int32_t* __restrict__ rowptr,
                              const int32_t* __restrict__ col, const double* __restrict__ val,
                              const double* __restrict__ p, double* __restrict__ q, Scalars* s, double* partials,
-                             int cap, tiled::SellView sv) {
+                             int cap, tiled::SellView sv, long long wait) {
     if (s->done) return;
     EpiStoreDot<double> epi{q, p, 0.0};
-    if (!tiled::spmv_rows<MODE, double, double, double>(n, nnz, rowptr, col, val, p, cap, &s->err, epi, sv)) {
+    if (!tiled::spmv_rows<MODE, double, double, double>(n, nnz, rowptr, col, val, p, cap, &s->err, epi, sv, wait)) {
         abort_solve(s);
         return;
     }
@@ -223,7 +230,7 @@ __global__ void k_update_xr(int32_t n, double* __restrict__ x, double* __restric
     if (grid_sum<1>(v, partials, &s->ticket[3]) && threadIdx.x == 0) {
         s->rr = v[0];
         s->iters += 1;
-        if (v[0] <= s->tol2)
+        if (sqrt(v[0]) <= s->tolr)
             s->done = 1;
         else if (s->iters >= s->maxit)
             s->done = 2;
@@ -234,10 +241,11 @@ __global__ void k_update_xr(int32_t n, double* __restrict__ x, double* __restric
 template <int MODE, typename VT, typename ACC>
 __global__ void k_spmv_G(int32_t n, int64_t nnz, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                          const VT* __restrict__ val, const double* __restrict__ r, ACC* __restrict__ t, Scalars* s,
-                         int cap, int init, tiled::SellView sv) {
+                         int cap, int init, tiled::SellView sv, long long wait) {
     if (!init && s->done) return;
     EpiStore<ACC, ACC> epi{t};
-    if (!tiled::spmv_rows<MODE, VT, double, ACC>(n, nnz, rowptr, col, val, r, cap, &s->err, epi, sv)) abort_solve(s);
+    if (!tiled::spmv_rows<MODE, VT, double, ACC>(n, nnz, rowptr, col, val, r, cap, &s->err, epi, sv, wait))
+        abort_solve(s);
 }
 
 // ---- z = G^T t, rz' = r.z, beta -------------------------------------------
@@ -245,10 +253,10 @@ template <int MODE, typename VT, typename ACC>
 __global__ void k_spmv_Gt_dot(int32_t n, int64_t nnz, const int32_t* __restrict__ rowptr,
                               const int32_t* __restrict__ col, const VT* __restrict__ val, const ACC* __restrict__ t,
                               const double* __restrict__ r, double* __restrict__ z, Scalars* s, double* partials,
-                              int cap, int init, tiled::SellView sv) {
+                              int cap, int init, tiled::SellView sv, long long wait) {
     if (!init && s->done) return;
     EpiStoreDot<ACC> epi{z, r, 0.0};
-    if (!tiled::spmv_rows<MODE, VT, ACC, ACC>(n, nnz, rowptr, col, val, t, cap, &s->err, epi, sv)) {
+    if (!tiled::spmv_rows<MODE, VT, ACC, ACC>(n, nnz, rowptr, col, val, t, cap, &s->err, epi, sv, wait)) {
         abort_solve(s);
         return;
     }
@@ -364,6 +372,7 @@ struct Launcher {
     double* partials;
     cudaStream_t st;
     SpmvMode ma, mg, mt;
+    long long wait;  // cycles a tile's copies may take before the solve gives up
 
     // engine choice and shared-memory limits, before any stream capture
     afsai_status plan() {
@@ -395,7 +404,7 @@ struct Launcher {
         const auto* v = static_cast<const double*>(A->val);
         with_mode(ma.mode, [&](auto Mc) {
             k_spmv_A_dot<decltype(Mc)::value><<<ma.blocks, ma.threads, ma.smem, st>>>(
-                A->n, A->nnz, A->rowptr, A->col, v, p, q, s, partials, ma.cap, tiled::sell_view(A->sell));
+                A->n, A->nnz, A->rowptr, A->col, v, p, q, s, partials, ma.cap, tiled::sell_view(A->sell), wait);
         });
         AFSAI_CUDA_TRY(cudaGetLastError());
         count_launches(1);
@@ -408,12 +417,12 @@ struct Launcher {
         with_mode(mg.mode, [&](auto Mc) {
             k_spmv_G<decltype(Mc)::value, VT, ACC><<<mg.blocks, mg.threads, mg.smem, st>>>(
                 G.n, G.nnz, G.rowptr, G.col, static_cast<const VT*>(G.val), r, tt, s, mg.cap, init,
-                tiled::sell_view(G.sell));
+                tiled::sell_view(G.sell), wait);
         });
         with_mode(mt.mode, [&](auto Mc) {
             k_spmv_Gt_dot<decltype(Mc)::value, VT, ACC><<<mt.blocks, mt.threads, mt.smem, st>>>(
                 Gt.n, Gt.nnz, Gt.rowptr, Gt.col, static_cast<const VT*>(Gt.val), tt, r, z, s, partials, mt.cap, init,
-                tiled::sell_view(Gt.sell));
+                tiled::sell_view(Gt.sell), wait);
         });
     }
 
@@ -438,18 +447,40 @@ struct Launcher {
         return AFSAI_OK;
     }
 
-    afsai_status iteration() {
+    // first half of an iteration: q = A p, alpha, x and r, the recursive test
+    afsai_status head() {
         AFSAI_TRY(spmv_A_dot());
         k_update_xr<<<vec_blocks(n), kThreads, 0, st>>>(n, x, r, p, q, s, partials);
         AFSAI_CUDA_TRY(cudaGetLastError());
         count_launches(1);
+        return AFSAI_OK;
+    }
+    // second half: z = M r, beta, p
+    afsai_status tail() {
         AFSAI_TRY(precond_dot(0));
         k_update_p<<<vec_blocks(n), kThreads, 0, st>>>(n, z, p, s);
         AFSAI_CUDA_TRY(cudaGetLastError());
         count_launches(1);
         return AFSAI_OK;
     }
+    afsai_status iteration() {
+        AFSAI_TRY(head());
+        return tail();
+    }
 };
+
+// Cycle limit of the first wait for a tile's bulk copies in the staged SpMV
+// engines of the PCG (AFSAI_WAIT_CYCLES, default ~2 s at 2 GHz); a wait that
+// runs out ends the solve with AFSAI_ETIMEOUT.  The wait that lets a
+// block's copies in flight land after an expiry keeps the full bound.
+long long first_wait_cycles() {
+    static const long long v = [] {
+        const char* e = std::getenv("AFSAI_WAIT_CYCLES");
+        const long long k = e ? std::atoll(e) : 0;
+        return k > 0 ? k : tiled::kWaitCycles;
+    }();
+    return v;
+}
 
 int iters_per_graph() {
     static int v = [] {
@@ -506,6 +537,7 @@ afsai_status pcg_body(const CsrDev& Ain, const afsai_precond* M, const double* b
     L.s = sc.p;
     L.partials = partials.p;
     L.st = st;
+    L.wait = first_wait_cycles();
     AFSAI_TRY(L.plan());
     // partials hold one value per block of the largest grid (2 per block for K = 2)
     if (std::max({L.ma.blocks, L.mg.blocks, L.mt.blocks, vec_blocks(n)}) * 2 > num_sms() * 64)
@@ -540,46 +572,96 @@ afsai_status pcg_body(const CsrDev& Ain, const afsai_precond* M, const double* b
     const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     AFSAI_CUDA_TRY(ie);
-    int32_t* done_host = nullptr;
-    cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&done_host), sizeof(int32_t));
+    Scalars* hs_pinned = nullptr;
+    cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&hs_pinned), sizeof(Scalars));
+    bool true_ok = false;
+    double tr2 = 0.0;
     if (e == cudaSuccess) {
-        *done_host = 0;
+        // the scalars after the initial residual (done = 1: x0 already meets the tolerance)
+        e = cudaMemcpyAsync(hs_pinned, sc.p, sizeof(Scalars), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         const int64_t max_launches = maxit > 0 ? (static_cast<int64_t>(maxit) + K - 1) / K + 1 : 0;
-        for (int64_t l = 0; l < max_launches && e == cudaSuccess; ++l) {
+        // graph launches until the recursive test (or maxit, or a wait) ends the loop
+        for (int64_t l = 0; l < max_launches && e == cudaSuccess && hs_pinned->done == 0; ++l) {
             e = cudaGraphLaunch(exec, st);
             if (e == cudaSuccess) count_launches(per_graph);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(done_host, &sc.p->done, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hs_pinned, sc.p, sizeof(Scalars), cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e == cudaSuccess && *done_host) break;
+            if (e == cudaSuccess && hs_pinned->done) break;
         }
-        cudaFreeHost(done_host);
+        // the recursive residual met the tolerance: check the true one, and
+        // continue the recurrence one iteration at a time while it is above
+        while (e == cudaSuccess && hs_pinned->done == 1) {
+            afsai_status ts = spmv_csr(A, x, L.q, st);
+            if (ts == AFSAI_OK) {
+                k_true_residual<<<vec_blocks(n), kThreads, 0, st>>>(n, b, L.q, sc.p, partials.p, trueres.p);
+                count_launches(1);
+                e = cudaMemcpyAsync(&tr2, trueres.p, sizeof(double), cudaMemcpyDeviceToHost, st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            } else {
+                e = cudaErrorUnknown;
+            }
+            if (e != cudaSuccess) break;
+            if (std::sqrt(tr2) <= hs_pinned->tolr) {
+                true_ok = true;
+                break;
+            }
+            if (hs_pinned->iters >= maxit) {
+                hs_pinned->done = 2;
+                break;
+            }
+            const int32_t zero = 0;
+            e = cudaMemcpyAsync(&sc.p->done, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) break;
+            if (L.tail() != AFSAI_OK || L.head() != AFSAI_OK) {
+                e = cudaErrorUnknown;
+                break;
+            }
+            e = cudaMemcpyAsync(hs_pinned, sc.p, sizeof(Scalars), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            // a recursive residual above the tolerance again: back to the graph
+            if (e == cudaSuccess && hs_pinned->done == 0) {
+                for (int64_t l = 0; l < max_launches && e == cudaSuccess; ++l) {
+                    e = cudaGraphLaunch(exec, st);
+                    if (e == cudaSuccess) count_launches(per_graph);
+                    if (e == cudaSuccess)
+                        e = cudaMemcpyAsync(hs_pinned, sc.p, sizeof(Scalars), cudaMemcpyDeviceToHost, st);
+                    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+                    if (e == cudaSuccess && hs_pinned->done) break;
+                }
+            }
+        }
+    }
+    Scalars hs{};
+    if (hs_pinned) {
+        hs = *hs_pinned;
+        cudaFreeHost(hs_pinned);
     }
     cudaGraphExecDestroy(exec);
     AFSAI_CUDA_TRY(e);
     AFSAI_CUDA_TRY(cudaEventRecord(ev1, st));
-    // true residual
-    AFSAI_TRY(spmv_csr(A, x, L.q, st));
-    k_true_residual<<<vec_blocks(n), kThreads, 0, st>>>(n, b, L.q, sc.p, partials.p, trueres.p);
-    AFSAI_CUDA_TRY(cudaGetLastError());
-    count_launches(1);
-    Scalars hs{};
-    double tr2 = 0.0;
-    AFSAI_CUDA_TRY(cudaMemcpyAsync(&hs, sc.p, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
-    AFSAI_CUDA_TRY(cudaMemcpyAsync(&tr2, trueres.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (!true_ok) {
+        // true residual at exit (maxit, an expired wait, or no iterations)
+        AFSAI_TRY(spmv_csr(A, x, L.q, st));
+        k_true_residual<<<vec_blocks(n), kThreads, 0, st>>>(n, b, L.q, sc.p, partials.p, trueres.p);
+        AFSAI_CUDA_TRY(cudaGetLastError());
+        count_launches(1);
+        AFSAI_CUDA_TRY(cudaMemcpyAsync(&tr2, trueres.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
     AFSAI_CUDA_TRY(cudaStreamSynchronize(st));
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev0, ev1);
     const double bn = std::sqrt(hs.bb);
+    const bool converged = true_ok || (hs.done == 1 && std::sqrt(tr2) <= hs.tolr);
     if (info) {
         info->iters = hs.iters;
-        info->converged = (hs.done == 1 || (hs.done == 0 && hs.iters == 0)) ? 1 : 0;
+        info->converged = converged ? 1 : 0;
         info->relres_rec = bn > 0 ? std::sqrt(hs.rr) / bn : 0.0;
         info->relres_true = bn > 0 ? std::sqrt(tr2) / bn : 0.0;
         info->solve_ms = ms;
     }
     if (hs.done == 3 || hs.err) return fail(AFSAI_ETIMEOUT, "a bounded device wait ran out during PCG");
-    if (hs.done == 2) return fail(AFSAI_ENOCONV, "PCG reached maxit without convergence");
+    if (!converged) return fail(AFSAI_ENOCONV, "PCG reached maxit without convergence");
     return AFSAI_OK;
 }
 

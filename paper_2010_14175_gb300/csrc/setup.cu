@@ -167,7 +167,7 @@ __device__ __forceinline__ int table_claim(int32_t* key, int log2, int32_t j, bo
 // sends the row to the retry pass with a larger table (bounded probing).
 __device__ __forceinline__ void table_append(int32_t* list, int slot, bool fresh, bool failed, int& nk, bool& full,
                                              int log2, unsigned gmask) {
-    const unsigned bal = __ballot_sync(gmask, fresh);
+    const unsigned bal = __ballot_sync(gmask, fresh) & gmask;
     if (fresh) list[nk + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u))] = slot;
     nk += __popc(bal);
     const int ht = 1 << log2;
@@ -909,7 +909,7 @@ __global__ void step_init(StepArgs a) {
             if (a.col[e] == i) aii = a.val[e];
         a.P[i * a.mc] = static_cast<int32_t>(i);
         a.g[i * a.mc] = 1.0 / aii;
-        a.M[i * a.tmc] = aii;  // the 1 x 1 system, extended incrementally
+        if (a.M) a.M[i * a.tmc] = aii;  // the 1 x 1 system, extended incrementally
         a.m[i] = 1;
         a.steps[i] = 0;
         a.psi[i] = aii;
@@ -946,18 +946,26 @@ struct GatherWs {
 // raw triangle is read back from a.M, moved to the new positions, and only
 // the rows of the new indices of A are read), as in the fused kernel; else
 // A[P,P] is gathered in full from the rows of P.
-template <int MC, int HT, bool INC>
+// GL lanes per row (32 / GL rows per warp, each group with its own
+// workspace and candidate table): the work of one row is small next to a
+// warp (the 7-point rows of a pattern of at most 11 entries give at most 77
+// candidate entries per step), so packing rows shares the per-row fixed
+// cost of every warp instruction.  Groups of one warp take consecutive
+// rows, whose patterns have the same shape on a structured grid.
+template <int MC, int HT, bool INC, int GL = 32>
 __global__ void __launch_bounds__(256) step_gather(StepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     using WS = GatherWs<MC, HT>;
-    constexpr int GL = 32;
-    const int warp = threadIdx.x >> 5;
-    const int sub = threadIdx.x & 31;
-    const unsigned gmask = 0xffffffffu;
-    WS& w = reinterpret_cast<WS*>(smem_raw)[warp];
-    constexpr int log2 = (HT == 256) ? 8 : 9;
-    const int64_t gw = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + warp;
-    const int64_t nw = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+    static_assert(GL == 4 || GL == 8 || GL == 16 || GL == 32, "lanes per row");
+    const int group = threadIdx.x / GL;
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & (GL - 1);
+    const unsigned gmask = (GL == 32) ? 0xffffffffu : (((1u << GL) - 1u) << (lane & ~(GL - 1)));
+    WS& w = reinterpret_cast<WS*>(smem_raw)[group];
+    constexpr int log2 = HT == 64 ? 6 : (HT == 128 ? 7 : (HT == 256 ? 8 : 9));
+    static_assert((1 << log2) == HT, "table size");
+    const int64_t gw = static_cast<int64_t>(blockIdx.x) * (blockDim.x / GL) + group;
+    const int64_t nw = static_cast<int64_t>(gridDim.x) * (blockDim.x / GL);
     for (int64_t ii = gw; ii < a.n; ii += nw) {
         if (a.st[ii] != kStActive) continue;
         const int32_t i = static_cast<int32_t>(ii);
@@ -973,7 +981,7 @@ __global__ void __launch_bounds__(256) step_gather(StepArgs a) {
             w.val[t] = 0.0;
         }
         int nkr = 0;  // keys in the table, equal in every lane
-        __syncwarp();
+        __syncwarp(gmask);
         // ---- Kaporin gradient over j < i (Eq. "grapsi") ----
         bool ovf = false;
         {
@@ -984,25 +992,25 @@ __global__ void __launch_bounds__(256) step_gather(StepArgs a) {
                 if (t + 1 < m) prefetch_row<GL, NPF>(RB, a.col, a.val, w.rb[t + 1], w.re[t + 1], sub);
                 accumulate_row<GL, NPF>(RA, a.col, a.val, w.rb[t], w.re[t], i, w.g[t], w.key, w.val, w.list, log2,
                                         nkr, ovf, sub, gmask);
-                __syncwarp();
+                __syncwarp(gmask);
                 if (t + 1 < m) {
                     if (t + 2 < m) prefetch_row<GL, NPF>(RA, a.col, a.val, w.rb[t + 2], w.re[t + 2], sub);
                     accumulate_row<GL, NPF>(RB, a.col, a.val, w.rb[t + 1], w.re[t + 1], i, w.g[t + 1], w.key, w.val,
                                             w.list, log2, nkr, ovf, sub, gmask);
-                    __syncwarp();
+                    __syncwarp(gmask);
                 }
             }
         }
         if (__any_sync(gmask, ovf)) {
             if (sub == 0) a.st[i] = kRowOverflow;
-            __syncwarp();
+            __syncwarp(gmask);
             continue;
         }
         for (int t = sub; t < m - 1; t += GL) {
             const int slot = table_find(w.key, log2, w.P[t]);
             if (slot >= 0) w.val[slot] = 0.0;
         }
-        __syncwarp();
+        __syncwarp(gmask);
         const int nk = nkr;
         apply_stripe_bound(stripe_bound(a.reach, a.reach_words, a.stripe_magic, a.stripe_shift, i), w.key, w.val,
                            w.list, nk, sub, GL, gmask);
@@ -1010,7 +1018,7 @@ __global__ void __launch_bounds__(256) step_gather(StepArgs a) {
         const int npick = select_top_s<GL>(w.key, w.val, w.list, nk, a.s, sub, gmask, w.newj);
         if (npick == 0) {
             if (sub == 0) a.st[i] = kStStop;
-            __syncwarp();
+            __syncwarp(gmask);
             continue;
         }
         // ---- merge into the sorted pattern ----
@@ -1039,7 +1047,7 @@ __global__ void __launch_bounds__(256) step_gather(StepArgs a) {
             w.isnew[lo + below] = 1;
         }
         m = mold + npick;
-        __syncwarp();
+        __syncwarp(gmask);
         for (int t = sub; t < m; t += GL) {
             const int32_t pt = w.Pn[t];
             w.P[t] = pt;
@@ -1049,7 +1057,7 @@ __global__ void __launch_bounds__(256) step_gather(StepArgs a) {
         }
         const int tm = tri(m);
         for (int t = sub; t < tm; t += GL) w.Mw[t] = 0.0;
-        __syncwarp();
+        __syncwarp(gmask);
         if (INC) {
             // ---- systems gather, incremental: old entries to their new
             // positions, then the rows of the new indices (A symmetric) ----
@@ -1061,7 +1069,7 @@ __global__ void __launch_bounds__(256) step_gather(StepArgs a) {
                 const int q = t - tri(r);
                 w.Mw[tri(w.opos[r]) + w.opos[q]] = a.M[ii * a.tmc + t];
             }
-            __syncwarp();
+            __syncwarp(gmask);
             for (int pj = 0; pj < m; ++pj) {
                 if (!w.isnew[pj]) continue;
                 for (int32_t e = w.rb[pj] + sub; e < w.re[pj]; e += GL) {
@@ -1088,14 +1096,231 @@ __global__ void __launch_bounds__(256) step_gather(StepArgs a) {
                 }
             }
         }
-        __syncwarp();
+        __syncwarp(gmask);
         for (int t = sub; t < tm; t += GL) a.M[ii * a.tmc + t] = w.Mw[t];
         if (sub == 0) {
             a.m[i] = m;
             a.steps[i] += 1;
             a.st[i] = kStSolve;
         }
-        __syncwarp();
+        __syncwarp(gmask);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gather kernel for small stencils: one lane per row, 32 rows per warp.
+// For rows of A with at most kLaneRowMax entries and patterns of at most 12
+// entries (7-point and 5-point stencils with s <= 4), a row's step touches
+// at most 11 x 8 entries of A and a few dozen distinct candidates, far too
+// little work for a warp; here every warp instruction serves 32 rows.  Each
+// lane owns a 64-slot open-addressing table in shared memory (lane-
+// interleaved, so a warp's accesses fall in distinct banks) with its
+// occupancy kept as a 64-bit mask in registers: no atomics, no clearing.
+// Gradient, selection and merge are those of step_gather (same operation
+// order: rows r in P ascending, each row in CSR order, acc = fma(a_rj, g_r,
+// acc) from 0); the gathered system is not built here: the solve kernel
+// reads A[P,P] from A itself (GATHER), so no system goes through HBM.
+// A row whose candidates exceed 7/8 of the table is marked for the retry
+// pass, as in the other kernels.
+// ---------------------------------------------------------------------------
+constexpr int kLaneHT = 64;
+constexpr int kLaneRowMax = 8;
+
+__device__ __forceinline__ bool occ_test(uint64_t occ, uint32_t h) { return (occ >> h) & 1ull; }
+
+template <int MC>
+__global__ void __launch_bounds__(128) step_gather_lane(StepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int HT = kLaneHT;
+    constexpr int LOG2 = 6;
+    static_assert((1 << LOG2) == HT, "table size");
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int nwb = blockDim.x >> 5;
+    unsigned char* wbase = smem_raw + static_cast<size_t>(warp) * (HT + MC) * 32 * 12;
+    double* sv = reinterpret_cast<double*>(wbase);                      // val[HT], g[MC]
+    int32_t* sk = reinterpret_cast<int32_t*>(wbase + (HT + MC) * 32 * 8);  // key[HT], P[MC]
+#define TV(h) sv[(h) * 32 + lane]
+#define TG(t) sv[(HT + (t)) * 32 + lane]
+#define TK(h) sk[(h) * 32 + lane]
+#define TP(t) sk[(HT + (t)) * 32 + lane]
+    const int64_t ngroups = (static_cast<int64_t>(a.n) + 31) / 32;
+    for (int64_t grp = static_cast<int64_t>(blockIdx.x) * nwb + warp; grp < ngroups;
+         grp += static_cast<int64_t>(gridDim.x) * nwb) {
+        const int64_t ii = grp * 32 + lane;
+        if (ii >= a.n || a.st[ii] != kStActive) continue;
+        const int32_t i = static_cast<int32_t>(ii);
+        const int m = a.m[ii];
+        for (int t = 0; t < m; ++t) {
+            TP(t) = a.P[ii * a.mc + t];
+            TG(t) = a.g[ii * a.mc + t];
+        }
+        // ---- Kaporin gradient over j < i (Eq. "grapsi"); row t + 1 of A
+        // is loaded while row t is accumulated ----
+        uint64_t occ = 0ull;
+        int nk = 0;
+        int32_t c0[kLaneRowMax], c1[kLaneRowMax];
+        double v0[kLaneRowMax], v1[kLaneRowMax];
+        auto load_row = [&](int t, int32_t (&c)[kLaneRowMax], double (&v)[kLaneRowMax]) {
+            const int32_t r = TP(t);
+            const int32_t rb = __ldg(&a.rowptr[r]), re = __ldg(&a.rowptr[r + 1]);
+#pragma unroll
+            for (int q = 0; q < kLaneRowMax; ++q) {
+                const bool on = rb + q < re;
+                c[q] = on ? __ldg(&a.col[rb + q]) : INT_MAX;
+                v[q] = on ? __ldg(&a.val[rb + q]) : 0.0;
+            }
+        };
+        load_row(0, c0, v0);
+        for (int t = 0; t < m; ++t) {
+            if (t + 1 < m) load_row(t + 1, c1, v1);
+            const double gr = TG(t);
+#pragma unroll
+            for (int q = 0; q < kLaneRowMax; ++q) {
+                const int32_t j = c0[q];
+                if (j < i) {
+                    uint32_t h = slot_of(j, LOG2);
+                    for (int probe = 0; probe < HT; ++probe) {
+                        if (!occ_test(occ, h)) {
+                            occ |= 1ull << h;
+                            TK(h) = j;
+                            TV(h) = 0.0;
+                            ++nk;
+                            break;
+                        }
+                        if (TK(h) == j) break;
+                        h = (h + 1) & (HT - 1);
+                    }
+                    TV(h) = fma(v0[q], gr, TV(h));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kLaneRowMax; ++q) {
+                c0[q] = c1[q];
+                v0[q] = v1[q];
+            }
+            if (nk > HT - (HT >> 3)) break;
+        }
+        if (nk > HT - (HT >> 3)) {
+            a.st[ii] = kRowOverflow;
+            continue;
+        }
+        // members of P are not eligible (i itself is never a candidate)
+        for (int t = 0; t < m - 1; ++t) {
+            const int32_t pj = TP(t);
+            uint32_t h = slot_of(pj, LOG2);
+            for (int probe = 0; probe < HT && occ_test(occ, h); ++probe) {
+                if (TK(h) == pj) {
+                    TV(h) = 0.0;
+                    break;
+                }
+                h = (h + 1) & (HT - 1);
+            }
+        }
+        // locality bound (Section 4): candidates outside the allowed stripes
+        const StripeBound bd = stripe_bound(a.reach, a.reach_words, a.stripe_magic, a.stripe_shift, i);
+        if (bd.row != nullptr) {
+            for (uint64_t mm = occ; mm; mm &= mm - 1) {
+                const uint32_t h = static_cast<uint32_t>(__ffsll(static_cast<long long>(mm)) - 1);
+                if (!bd.allows(TK(h))) TV(h) = 0.0;
+            }
+        }
+        // ---- the s (<= 4) largest |gradient|, ties to the smaller column ----
+        unsigned long long kb[4] = {0ull, 0ull, 0ull, 0ull};
+        int32_t kj[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
+        for (uint64_t mm = occ; mm; mm &= mm - 1) {
+            const uint32_t h = static_cast<uint32_t>(__ffsll(static_cast<long long>(mm)) - 1);
+            const unsigned long long ab =
+                static_cast<unsigned long long>(__double_as_longlong(TV(h))) & 0x7fffffffffffffffull;
+            if (ab == 0ull || ab > 0x7ff0000000000000ull) continue;  // zero or NaN
+            const int32_t j = TK(h);
+            if (!cand_better(ab, j, kb[3], kj[3])) continue;
+            kb[3] = ab;
+            kj[3] = j;
+#pragma unroll
+            for (int q = 3; q > 0; --q) {
+                if (cand_better(kb[q], kj[q], kb[q - 1], kj[q - 1])) {
+                    const unsigned long long tb = kb[q];
+                    kb[q] = kb[q - 1];
+                    kb[q - 1] = tb;
+                    const int32_t tj = kj[q];
+                    kj[q] = kj[q - 1];
+                    kj[q - 1] = tj;
+                }
+            }
+        }
+        int npick = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (q < a.s && kb[q] != 0ull) ++npick;
+        if (npick == 0) {
+            a.st[ii] = kStStop;
+            continue;
+        }
+        // picks in ascending column order (INT_MAX past npick)
+        int32_t p0 = kj[0], p1 = npick > 1 ? kj[1] : INT_MAX, p2 = npick > 2 ? kj[2] : INT_MAX,
+                p3 = npick > 3 ? kj[3] : INT_MAX;
+#define CSWAP(x, y)                  \
+    if ((y) < (x)) {                 \
+        const int32_t t_ = (x);      \
+        (x) = (y);                   \
+        (y) = t_;                    \
+    }
+        CSWAP(p0, p1) CSWAP(p2, p3) CSWAP(p0, p2) CSWAP(p1, p3) CSWAP(p1, p2)
+#undef CSWAP
+        // ---- merge into the sorted pattern (i stays last) ----
+        int ip = 0;
+        const int mnew = m + npick;
+        for (int o = 0; o < mnew; ++o) {
+            const int32_t pa = ip < m ? TP(ip) : INT_MAX;
+            int32_t out;
+            if (p0 < pa) {
+                out = p0;
+                p0 = p1;
+                p1 = p2;
+                p2 = p3;
+                p3 = INT_MAX;
+            } else {
+                out = pa;
+                ++ip;
+            }
+            a.P[ii * a.mc + o] = out;
+        }
+        a.m[ii] = mnew;
+        a.steps[ii] += 1;
+        a.st[ii] = kStSolve;
+    }
+#undef TV
+#undef TG
+#undef TK
+#undef TP
+}
+
+// A[P,P], lower triangle, of one row's system, gathered from the rows of
+// its pattern: entry (P_t, c) of A with c <= P_t and c in P goes to packed
+// position tri(t) + pos(c) (the gather of the plain definition; only the
+// lower part of each row is read).  The LPR lanes of the row split the
+// rows of P; rows of A have at most kLaneRowMax entries here.
+template <int LPR, typename F>
+__device__ __forceinline__ void gather_rows_lower(const StepArgs& a, const int32_t* Ps, int m, int sub, F&& put) {
+    for (int t = sub; t < m; t += LPR) {
+        const int32_t pr = Ps[t];
+        const int32_t rb = __ldg(&a.rowptr[pr]), re = __ldg(&a.rowptr[pr + 1]);
+        int32_t c[kLaneRowMax];
+        double v[kLaneRowMax];
+#pragma unroll
+        for (int q = 0; q < kLaneRowMax; ++q) {
+            const bool on = rb + q < re;
+            c[q] = on ? __ldg(&a.col[rb + q]) : INT_MAX;
+            v[q] = on ? __ldg(&a.val[rb + q]) : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < kLaneRowMax; ++q) {
+            if (c[q] <= pr) {
+                const int pc = find_sorted(Ps, t + 1, c[q]);
+                if (pc >= 0) put(tri(t) + pc, v[q]);
+            }
+        }
     }
 }
 
@@ -1185,12 +1410,16 @@ __global__ void __launch_bounds__(64) step_solve(StepArgs a) {
 // instructions cost more issue slots than the FP64 pipe time it saves).
 // Each pivot's reciprocal is prepared once and kept for the back
 // substitution.
-template <int MC, int LPR>
+// GATHER: the row's system is gathered here from A (gather_rows_lower)
+// instead of being read from the gather kernel's slot; the pattern is then
+// kept in the row's area too.
+template <int MC, int LPR, bool GATHER = false>
 __global__ void __launch_bounds__(128) step_solve_wide(StepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int TMC = MC * (MC + 1) / 2;
     constexpr int RPW = 32 / LPR;            // rows per warp
-    constexpr int RS = (TMC + 2 * MC) | 1;   // doubles per row (odd): L, g, prepared reciprocals
+    // doubles per row (odd): L, g, prepared reciprocals (+ the pattern)
+    constexpr int RS = (TMC + 2 * MC + (GATHER ? (MC + 1) / 2 : 0)) | 1;
     constexpr size_t kPairBytes = (sizeof(uint16_t) * TMC + 15) / 16 * 16;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -1214,12 +1443,22 @@ __global__ void __launch_bounds__(128) step_solve_wide(StepArgs a) {
         const int64_t ii = r0 + grp;
         const bool row = ii < a.n && a.st[ii] == kStSolve;
         const int m = row ? a.m[ii] : 0;
-        // load the warp's triangles, one row at a time with all lanes
-        for (int q = 0; q < RPW; ++q) {
-            const int mq = __shfl_sync(0xffffffffu, m, q * LPR);
-            const int tq = tri(mq);
-            double* Mq = wbase + q * RS;
-            for (int t = lane; t < tq; t += 32) Mq[t] = a.M[(r0 + q) * a.tmc + t];
+        if constexpr (GATHER) {
+            int32_t* Ps = reinterpret_cast<int32_t*>(V + MC);
+            if (row) {
+                for (int t = sub; t < m; t += LPR) Ps[t] = a.P[ii * a.mc + t];
+                for (int t = sub; t < tri(m); t += LPR) M[t] = 0.0;
+            }
+            __syncwarp();
+            if (row) gather_rows_lower<LPR>(a, Ps, m, sub, [&](int idx, double v) { M[idx] = v; });
+        } else {
+            // load the warp's triangles, one row at a time with all lanes
+            for (int q = 0; q < RPW; ++q) {
+                const int mq = __shfl_sync(0xffffffffu, m, q * LPR);
+                const int tq = tri(mq);
+                double* Mq = wbase + q * RS;
+                for (int t = lane; t < tq; t += 32) Mq[t] = a.M[(r0 + q) * a.tmc + t];
+            }
         }
         int mmax = m;
 #pragma unroll
@@ -1295,13 +1534,14 @@ __global__ void __launch_bounds__(128) step_solve_wide(StepArgs a) {
 // refinement step res = e_m - A[P,P] g (FP64, from the raw triangle),
 // L L^T d = res (FP32), g += d (FP64).  Same lanes and layout as
 // step_solve_wide; each row keeps its raw FP64 triangle for the residual.
-template <int MC, int LPR>
+template <int MC, int LPR, bool GATHER = false>
 __global__ void __launch_bounds__(128) step_solve_wide32(StepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int TMC = MC * (MC + 1) / 2;
     constexpr int RPW = 32 / LPR;
-    // per row: raw triangle (double) + g (double) | factor (float) + x (float)
-    constexpr int RSD = (TMC + MC) | 1;          // doubles
+    // per row: raw triangle (double) + g (double) (+ the pattern) | factor
+    // (float) + x (float)
+    constexpr int RSD = (TMC + MC + (GATHER ? (MC + 1) / 2 : 0)) | 1;  // doubles
     constexpr int RSF = ((TMC + MC) | 1) + 1;    // floats (even count keeps 8-byte alignment)
     constexpr size_t kRowBytes = RSD * sizeof(double) + RSF * sizeof(float);
     constexpr size_t kPairBytes = (sizeof(uint16_t) * TMC + 15) / 16 * 16;
@@ -1328,15 +1568,32 @@ __global__ void __launch_bounds__(128) step_solve_wide32(StepArgs a) {
         const int64_t ii = r0 + grp;
         const bool row = ii < a.n && a.st[ii] == kStSolve;
         const int m = row ? a.m[ii] : 0;
-        for (int q = 0; q < RPW; ++q) {
-            const int mq = __shfl_sync(0xffffffffu, m, q * LPR);
-            const int tq = tri(mq);
-            double* Mq = reinterpret_cast<double*>(wbase + q * kRowBytes);
-            float* Lq = reinterpret_cast<float*>(Mq + RSD);
-            for (int t = lane; t < tq; t += 32) {
-                const double v = a.M[(r0 + q) * a.tmc + t];
-                Mq[t] = v;
-                Lq[t] = static_cast<float>(v);
+        if constexpr (GATHER) {
+            int32_t* Ps = reinterpret_cast<int32_t*>(g + MC);
+            if (row) {
+                for (int t = sub; t < m; t += LPR) Ps[t] = a.P[ii * a.mc + t];
+                for (int t = sub; t < tri(m); t += LPR) {
+                    M[t] = 0.0;
+                    L[t] = 0.0f;
+                }
+            }
+            __syncwarp();
+            if (row)
+                gather_rows_lower<LPR>(a, Ps, m, sub, [&](int idx, double v) {
+                    M[idx] = v;
+                    L[idx] = static_cast<float>(v);
+                });
+        } else {
+            for (int q = 0; q < RPW; ++q) {
+                const int mq = __shfl_sync(0xffffffffu, m, q * LPR);
+                const int tq = tri(mq);
+                double* Mq = reinterpret_cast<double*>(wbase + q * kRowBytes);
+                float* Lq = reinterpret_cast<float*>(Mq + RSD);
+                for (int t = lane; t < tq; t += 32) {
+                    const double v = a.M[(r0 + q) * a.tmc + t];
+                    Mq[t] = v;
+                    Lq[t] = static_cast<float>(v);
+                }
             }
         }
         int mmax = m;
@@ -1493,7 +1750,7 @@ __global__ void k_setup_diagonal(SetupArgs o) {
 
 // LPR = 0: lane-per-row solve kernel (step_solve); LPR > 0: step_solve_wide
 // with LPR lanes per row (FP64 only).  INC: incremental gather.
-template <int MC, int HT, bool CHOL32, bool INC = false, int LPR = 0>
+template <int MC, int HT, bool CHOL32, bool INC = false, int LPR = 0, int GGL = 32>
 afsai_status run_stepwise_t(const SetupArgs& o, int32_t kiter, cudaStream_t st) {
     const int32_t n = o.n;
     constexpr int TMC = MC * (MC + 1) / 2;
@@ -1533,13 +1790,14 @@ afsai_status run_stepwise_t(const SetupArgs& o, int32_t kiter, cudaStream_t st) 
     step_init<<<vec_blocks, 256, 0, st>>>(a);
     AFSAI_CUDA_TRY(cudaGetLastError());
     count_launches(1);
-    // gather kernel: 8 warps per block
-    auto kg = step_gather<MC, HT, INC>;
-    const size_t smem_g = sizeof(GatherWs<MC, HT>) * 8;
+    // gather kernel: 8 warps per block, GGL lanes per row
+    auto kg = step_gather<MC, HT, INC, GGL>;
+    constexpr int kGroupsBlk = 256 / GGL;
+    const size_t smem_g = sizeof(GatherWs<MC, HT>) * kGroupsBlk;
     AFSAI_CUDA_TRY(cudaFuncSetAttribute(kg, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_g)));
     int per_sm_g = 0;
     AFSAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_g, kg, 256, smem_g));
-    const int blocks_g = std::max(1, std::min(per_sm_g * num_sms(), ceil_div(n, 8)));
+    const int blocks_g = std::max(1, std::min(per_sm_g * num_sms(), ceil_div(n, kGroupsBlk)));
     // solve kernel: lane-interleaved systems, 1 or 2 warps per block (or the
     // several-lanes-per-row kernel)
     static_assert(LPR > 0 || !CHOL32, "the one-lane-per-row solve is FP64 only");
@@ -1588,6 +1846,102 @@ afsai_status run_stepwise_t(const SetupArgs& o, int32_t kiter, cudaStream_t st) 
     return AFSAI_OK;
 }
 
+// Small stencils (rows of A with at most kLaneRowMax entries, patterns of
+// at most MC entries, s <= 4): the lane-per-row gather kernel and the
+// LPR-lanes-per-row solve kernel that gathers its system from A.  No
+// per-row system slot is allocated.
+template <int MC, int LPR, bool CHOL32>
+afsai_status run_stepwise_lane(const SetupArgs& o, int32_t kiter, cudaStream_t st) {
+    const int32_t n = o.n;
+    constexpr int TMC = MC * (MC + 1) / 2;
+    DevBuf<int32_t> P, mm, steps, stt;
+    DevBuf<double> g, psi, psi0;
+    AFSAI_TRY(P.alloc(static_cast<size_t>(n) * MC, st));
+    AFSAI_TRY(g.alloc(static_cast<size_t>(n) * MC, st));
+    AFSAI_TRY(mm.alloc(n, st));
+    AFSAI_TRY(steps.alloc(n, st));
+    AFSAI_TRY(stt.alloc(n, st));
+    AFSAI_TRY(psi.alloc(n, st));
+    AFSAI_TRY(psi0.alloc(n, st));
+    StepArgs a{};
+    a.n = n;
+    a.rowptr = o.rowptr;
+    a.col = o.col;
+    a.val = o.val;
+    a.s = o.s;
+    a.exit_mode = o.exit_mode;
+    a.eps = o.eps;
+    a.mc = MC;
+    a.tmc = TMC;
+    a.P = P.p;
+    a.g = g.p;
+    a.M = nullptr;
+    a.m = mm.p;
+    a.steps = steps.p;
+    a.st = stt.p;
+    a.psi = psi.p;
+    a.psi0 = psi0.p;
+    a.reach = o.reach;
+    a.reach_words = o.reach_words;
+    a.stripe_shift = o.stripe_shift;
+    a.stripe_magic = o.stripe_magic;
+    const int vec_blocks = std::max(1, std::min(ceil_div(n, 256), num_sms() * 8));
+    step_init<<<vec_blocks, 256, 0, st>>>(a);
+    AFSAI_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    // warps per block (1, 2 or 4) that maximise resident warps per SM
+    auto best_wpb = [](size_t per_warp, size_t fixed) {
+        int wpb = 1, best = 0;
+        for (int cand = 1; cand <= 4; cand *= 2) {
+            const size_t blk = per_warp * cand + fixed + 1024;
+            if (blk > 200u * 1024u) break;
+            const int warps = static_cast<int>((227u * 1024u) / blk) * cand;
+            if (warps > best) {
+                best = warps;
+                wpb = cand;
+            }
+        }
+        return wpb;
+    };
+    auto kg = step_gather_lane<MC>;
+    const size_t per_warp_g = static_cast<size_t>(kLaneHT + MC) * 32 * 12;
+    const int wpb_g = best_wpb(per_warp_g, 0);
+    const size_t smem_g = per_warp_g * wpb_g;
+    AFSAI_CUDA_TRY(cudaFuncSetAttribute(kg, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_g)));
+    int per_sm_g = 0;
+    AFSAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_g, kg, 32 * wpb_g, smem_g));
+    auto ks = [] {
+        if constexpr (CHOL32)
+            return step_solve_wide32<MC, LPR, true>;
+        else
+            return step_solve_wide<MC, LPR, true>;
+    }();
+    constexpr int RPW = 32 / LPR;
+    const size_t per_row = CHOL32 ? ((TMC + MC + (MC + 1) / 2) | 1) * sizeof(double) +
+                                        (((TMC + MC) | 1) + 1) * sizeof(float)
+                                  : ((TMC + 2 * MC + (MC + 1) / 2) | 1) * sizeof(double);
+    const size_t per_warp_s = per_row * RPW;
+    const size_t pair_bytes = (sizeof(uint16_t) * TMC + 15) / 16 * 16;
+    const int wpb_s = best_wpb(per_warp_s, pair_bytes);
+    const size_t smem_s = per_warp_s * wpb_s + pair_bytes;
+    AFSAI_CUDA_TRY(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_s)));
+    int per_sm_s = 0;
+    AFSAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, ks, 32 * wpb_s, smem_s));
+    if (per_sm_s < 1 || per_sm_g < 1) return fail(AFSAI_ENOTSUP, "stepwise set-up does not fit in shared memory");
+    const int blocks_g = std::max(1, std::min(per_sm_g * num_sms(), ceil_div(ceil_div(n, 32), wpb_g)));
+    const int blocks_s = std::max(1, std::min(per_sm_s * num_sms(), ceil_div(ceil_div(n, RPW), wpb_s)));
+    for (int32_t k = 1; k <= kiter; ++k) {
+        kg<<<blocks_g, 32 * wpb_g, smem_g, st>>>(a);
+        ks<<<blocks_s, 32 * wpb_s, smem_s, st>>>(a);
+        AFSAI_CUDA_TRY(cudaGetLastError());
+        count_launches(2);
+    }
+    step_finish<<<vec_blocks, 256, 0, st>>>(a, o);
+    AFSAI_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return AFSAI_OK;
+}
+
 // Pattern capacities served by the small-pattern stepwise path (21 to 32
 // entries: run_stepwise_wide).
 bool stepwise_supported(int64_t mcap) { return mcap <= 20; }
@@ -1605,7 +1959,30 @@ afsai_status run_stepwise_wide(const SetupArgs& o, int ht, int lpr, int32_t kite
                      : run_stepwise_t<32, 512, false, true, 4>(o, kiter, st);
 }
 
-afsai_status run_stepwise(const SetupArgs& o, int64_t mcap, int ht, int32_t kiter, bool chol32, cudaStream_t st) {
+// Patterns of up to 12 entries whose candidates fit a 128-slot table
+// (at most 112 keys): the gather kernel packs rows, GGL lanes per row.
+template <int LPR>
+afsai_status run_stepwise_packed(const SetupArgs& o, int ggl, int32_t kiter, cudaStream_t st) {
+    switch (ggl) {
+        case 4: return run_stepwise_t<12, 128, false, true, LPR, 4>(o, kiter, st);
+        case 8: return run_stepwise_t<12, 128, false, true, LPR, 8>(o, kiter, st);
+        case 16: return run_stepwise_t<12, 128, false, true, LPR, 16>(o, kiter, st);
+        default: return run_stepwise_t<12, 128, false, true, LPR, 32>(o, kiter, st);
+    }
+}
+
+// Whether the lane-per-row gather serves this set-up (AFSAI_GATHER_LANE=0
+// turns it off).
+bool lane_gather_applies(int64_t mcap, int32_t s, int32_t max_row_nnz) {
+    static const bool on = [] {
+        const char* e = std::getenv("AFSAI_GATHER_LANE");
+        return !e || std::atoi(e) != 0;
+    }();
+    return on && mcap <= 12 && s <= 4 && max_row_nnz <= kLaneRowMax;
+}
+
+afsai_status run_stepwise(const SetupArgs& o, int64_t mcap, int ht, int32_t kiter, bool chol32, cudaStream_t st,
+                          int64_t cand_bound) {
     // FP64: several lanes per row in the solve (measured best: 2 lanes for
     // patterns of up to 12 entries, 4 up to 20); AFSAI_STEPWISE_SMALL_LPR =
     // 1 selects the one-lane-per-row solve kernel, 2 or 4 force a width
@@ -1613,7 +1990,15 @@ afsai_status run_stepwise(const SetupArgs& o, int64_t mcap, int ht, int32_t kite
         const char* e = std::getenv("AFSAI_STEPWISE_SMALL_LPR");
         return e ? std::atoi(e) : 0;
     }();
+    // lanes per row of the gather kernel for small candidate sets
+    // (AFSAI_GATHER_GL = 4, 8, 16 or 32)
+    static const int gather_gl = [] {
+        const char* e = std::getenv("AFSAI_GATHER_GL");
+        return e ? std::atoi(e) : 32;
+    }();
     const int lpr = small_lpr != 0 ? small_lpr : (mcap <= 12 ? 2 : 4);
+    if (!chol32 && mcap <= 12 && cand_bound * 8 <= 128 * 7 && gather_gl != 32 && (lpr == 2 || lpr == 4))
+        return lpr == 4 ? run_stepwise_packed<4>(o, gather_gl, kiter, st) : run_stepwise_packed<2>(o, gather_gl, kiter, st);
     if (!chol32 && mcap <= 20 && (lpr == 2 || lpr == 4)) {
         if (mcap <= 12)
             return lpr == 4 ? (ht == 256 ? run_stepwise_t<12, 256, false, true, 4>(o, kiter, st)
@@ -1831,8 +2216,14 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
         k_setup_diagonal<<<blocks, 256, 0, st>>>(a);
         AFSAI_CUDA_TRY(cudaGetLastError());
         count_launches(1);
+    } else if (!fused_only && lane_gather_applies(mcap, p->s, max_row_nnz)) {
+        // small stencils: lane-per-row gather, 2 lanes per row in the solve
+        if (chol32)
+            AFSAI_TRY((run_stepwise_lane<12, 2, true>(a, p->kiter, st)));
+        else
+            AFSAI_TRY((run_stepwise_lane<12, 2, false>(a, p->kiter, st)));
     } else if (!fused_only && stepwise_supported(mcap) && !chol32)
-        AFSAI_TRY(run_stepwise(a, mcap, ht, p->kiter, chol32, st));
+        AFSAI_TRY(run_stepwise(a, mcap, ht, p->kiter, chol32, st, cand_bound));
     else if (!fused_only && (wide_lpr == 4 || wide_lpr == 8) && mcap > 20 && mcap <= 32 && (!chol32 || wide_mixed))
         AFSAI_TRY(run_stepwise_wide(a, ht, wide_lpr, p->kiter, chol32, st));
     else

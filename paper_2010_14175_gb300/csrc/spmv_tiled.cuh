@@ -63,11 +63,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
     return ok != 0;
 }
 
-// Bounded wait for the given phase parity; false if the deadline passed.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
+// Bounded wait for the given phase parity; false if `limit` cycles passed.
+// The waits for a tile's copies take the caller's limit (the PCG passes a
+// shorter one when asked to, so that the expiry path can be exercised);
+// the second wait after an expiry, which lets the block's copies in flight
+// land before it returns, always takes the full bound.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, long long limit = kWaitCycles) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, phase)) {
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
     return true;
 }
@@ -161,7 +165,7 @@ __device__ __forceinline__ void tile_rows(int64_t r0, int64_t r1, const int32_t*
 template <int TPR, typename VT, typename XT, typename ACC, class Epi>
 __device__ bool spmv_tiles(int32_t n, int64_t nnz, const int32_t* __restrict__ rowptr,
                            const int32_t* __restrict__ col, const VT* __restrict__ val, const XT* __restrict__ x,
-                           int cap, int32_t* errflag, Epi& epi) {
+                           int cap, int32_t* errflag, Epi& epi, long long wait) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     int32_t* scol = reinterpret_cast<int32_t*>(smem + 128);
@@ -201,7 +205,7 @@ __device__ bool spmv_tiles(int32_t n, int64_t nnz, const int32_t* __restrict__ r
             for (int64_t e = ct + threadIdx.x; e < e1; e += blockDim.x) scol[e - c_lo] = col[e];
             const int64_t vt = v_hi > v_lo ? v_hi : v_lo;
             for (int64_t e = vt + threadIdx.x; e < e1; e += blockDim.x) sval[e - v_lo] = val[e];
-            const bool ok = mbar_wait(bar, phase);
+            const bool ok = mbar_wait(bar, phase, wait);
             if (!__syncthreads_and(ok)) {
                 if (threadIdx.x == 0) {
                     if (errflag) atomicExch(errflag, 1);
@@ -439,7 +443,8 @@ __host__ __device__ inline size_t staged_warp_bytes(size_t val_size) {
 }
 
 template <int CK, int NST, typename VT, typename XT, typename ACC, class Epi>
-__device__ bool spmv_sliced_staged(const SellView& S, const XT* __restrict__ x, int32_t* errflag, Epi& epi) {
+__device__ bool spmv_sliced_staged(const SellView& S, const XT* __restrict__ x, int32_t* errflag, Epi& epi,
+                                   long long wait) {
     using SH = StagedShape<CK, VT>;
     static_assert(NST >= 1 && NST <= 16, "stages");
     extern __shared__ __align__(128) unsigned char smem[];
@@ -501,7 +506,7 @@ __device__ bool spmv_sliced_staged(const SellView& S, const XT* __restrict__ x, 
         const int2 rl = __ldg(&S.rowlen[sl * 32 + lane]);
         ACC acc = ACC(0);
         for (int32_t kb = 0; kb < K; kb += CK) {
-            const bool ok = mbar_wait(&bars[stage], (parity >> stage) & 1u);
+            const bool ok = mbar_wait(&bars[stage], (parity >> stage) & 1u, wait);
             if (!__all_sync(0xffffffffu, ok)) {
                 if (lane == 0 && errflag) atomicExch(errflag, 1);
                 // bounded second wait for every copy this warp has in flight
@@ -561,7 +566,7 @@ template <int MODE, typename VT, typename XT, typename ACC, class Epi>
 __device__ __forceinline__ bool spmv_rows(int32_t n, int64_t nnz, const int32_t* __restrict__ rowptr,
                                           const int32_t* __restrict__ col, const VT* __restrict__ val,
                                           const XT* __restrict__ x, int cap, int32_t* errflag, Epi& epi,
-                                          const SellView& sv) {
+                                          const SellView& sv, long long wait = kWaitCycles) {
     if constexpr (MODE == kModeSliced) {
         spmv_sliced<VT, XT, ACC>(sv, x, epi);
         return true;
@@ -575,11 +580,11 @@ __device__ __forceinline__ bool spmv_rows(int32_t n, int64_t nnz, const int32_t*
         spmv_sliced_pipe<4, true, VT, XT, ACC>(sv, x, epi);
         return true;
     } else if constexpr (MODE == kModeSlicedStaged8) {
-        return spmv_sliced_staged<8, 3, VT, XT, ACC>(sv, x, errflag, epi);
+        return spmv_sliced_staged<8, 3, VT, XT, ACC>(sv, x, errflag, epi, wait);
     } else if constexpr (MODE == kModeSlicedStaged16) {
-        return spmv_sliced_staged<16, 2, VT, XT, ACC>(sv, x, errflag, epi);
+        return spmv_sliced_staged<16, 2, VT, XT, ACC>(sv, x, errflag, epi, wait);
     } else if constexpr (MODE > 100) {
-        return spmv_tiles<MODE - 100, VT, XT, ACC>(n, nnz, rowptr, col, val, x, cap, errflag, epi);
+        return spmv_tiles<MODE - 100, VT, XT, ACC>(n, nnz, rowptr, col, val, x, cap, errflag, epi, wait);
     } else if constexpr (MODE == 3 || MODE == 6) {
         spmv_grouped<MODE, VT, XT, ACC>(n, rowptr, col, val, x, epi);
         return true;

@@ -5,9 +5,13 @@ the intermediate G r in a fixed 2^20-double device array instead of
 allocating.  This file is collected last on purpose.
 
 Checks, through the C ABI: two calls in a row give the same z as
-afsai_apply (within the rounding bound the apply tests use), the first call
-works in a fresh process (it looks up the array's address), and n above the
-array's size is rejected with EINVAL."""
+afsai_apply (within the rounding bound the apply tests use); the second
+call changes neither the device's free memory nor the use of its default
+stream-ordered memory pool (read from the CUDA driver, so an allocation by
+any route would show); the first call works in a fresh process (the array
+was loaded by afsai_setup); n above the array's size is rejected with
+EINVAL."""
+import ctypes
 import numpy as np
 import pytest
 
@@ -25,6 +29,30 @@ def gpu():
 
     afsai.load()
     return afsai
+
+
+class _DriverMemory:
+    """Free device memory (cuMemGetInfo) and the bytes in use in the current
+    device's default memory pool (cuMemPoolGetAttribute), read through the
+    CUDA driver library for the context torch made current."""
+
+    USED_MEM_CURRENT = 0x7  # CU_MEMPOOL_ATTR_USED_MEM_CURRENT
+    RESERVED_MEM_CURRENT = 0x5  # CU_MEMPOOL_ATTR_RESERVED_MEM_CURRENT
+
+    def __init__(self, device):
+        self.cu = ctypes.CDLL("libcuda.so.1")
+        dev = ctypes.c_int()
+        assert self.cu.cuDeviceGet(ctypes.byref(dev), device) == 0
+        self.pool = ctypes.c_void_p()
+        assert self.cu.cuDeviceGetDefaultMemPool(ctypes.byref(self.pool), dev) == 0
+
+    def snapshot(self):
+        free, total = ctypes.c_size_t(), ctypes.c_size_t()
+        assert self.cu.cuMemGetInfo_v2(ctypes.byref(free), ctypes.byref(total)) == 0
+        used, reserved = ctypes.c_uint64(), ctypes.c_uint64()
+        assert self.cu.cuMemPoolGetAttribute(self.pool, self.USED_MEM_CURRENT, ctypes.byref(used)) == 0
+        assert self.cu.cuMemPoolGetAttribute(self.pool, self.RESERVED_MEM_CURRENT, ctypes.byref(reserved)) == 0
+        return {"free": free.value, "pool_used": used.value, "pool_reserved": reserved.value}
 
 
 def _bound(G, r):
@@ -48,12 +76,19 @@ def test_static_apply_matches_apply_twice(gpu, name, make, kiter, s, eps, g_prec
     rp, ci, va = M.export()
     G = (va, ci, rp)
     rng = np.random.default_rng(5)
+    mem = _DriverMemory(torch.cuda.current_device())
     for call in range(2):  # the array keeps the previous call's contents
         r = rng.standard_normal(A.n)
         rd = torch.from_numpy(r).cuda()
         z_static = torch.full((A.n,), np.nan, dtype=torch.float64, device="cuda")
-        afsai.afsai_apply_static(M, rd, z_static)
         z_ref = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        before = mem.snapshot()
+        afsai.afsai_apply_static(M, rd, z_static)
+        torch.cuda.synchronize()
+        after = mem.snapshot()
+        if call == 1:
+            assert after == before, (before, after)
         afsai.afsai_apply(M, rd, z_ref)
         torch.cuda.synchronize()
         zs, zr = z_static.cpu().numpy(), z_ref.cpu().numpy()
