@@ -87,7 +87,7 @@ def _load():
             lib.oracle_spmv.restype = None
             lib.oracle_apply.argtypes = [i32, P, P, P, P, P, P]
             lib.oracle_apply.restype = None
-            lib.oracle_pcg.argtypes = [i32, P, P, P, P, P, P, P, P, f64, i32, P, P, P]
+            lib.oracle_pcg.argtypes = [i32, P, P, P, P, P, P, P, P, f64, i32, P, P, P, P]
             lib.oracle_pcg.restype = ctypes.c_int
             lib.oracle_num_threads.argtypes = []
             lib.oracle_num_threads.restype = ctypes.c_int
@@ -220,8 +220,10 @@ def apply(G: OracleG, r: np.ndarray) -> np.ndarray:
     return z
 
 
-def pcg(A, G: OracleG, b: np.ndarray, rtol: float = 1e-8, maxit: int = 10000):
-    """PCG with M^{-1} = G^T G; returns (x, iters, relres_rec, relres_true)."""
+def pcg(A, G: OracleG, b: np.ndarray, rtol: float = 1e-8, maxit: int = 10000, history: bool = False):
+    """PCG with M^{-1} = G^T G; returns (x, iters, relres_rec, relres_true),
+    plus the recursive relative residual after each iteration (entry 0: the
+    initial one) when ``history`` is set."""
     lib = _load()
     rp, ci, va = _csr_args(A)
     grp, gci, gva = _csr_args(G)
@@ -230,8 +232,11 @@ def pcg(A, G: OracleG, b: np.ndarray, rtol: float = 1e-8, maxit: int = 10000):
     it = np.zeros(1, dtype=np.int32)
     rr = np.zeros(1, dtype=np.float64)
     rt = np.zeros(1, dtype=np.float64)
+    hist = np.zeros(int(maxit) + 1, dtype=np.float64) if history else None
     st = lib.oracle_pcg(A.n, _p(rp), _p(ci), _p(va), _p(grp), _p(gci), _p(gva), _p(b), _p(x), float(rtol), int(maxit),
-                        _p(it), _p(rr), _p(rt))
+                        _p(it), _p(rr), _p(rt), _p(hist) if history else None)
     if st != OK:
         raise RuntimeError(f"oracle_pcg failed with status {st}")
+    if history:
+        return x, int(it[0]), float(rr[0]), float(rt[0]), hist[: min(int(it[0]), int(maxit)) + 1]
     return x, int(it[0]), float(rr[0]), float(rt[0])

@@ -491,7 +491,9 @@ static double true_residual_norm(int32_t n, const int32_t* rowptr, const int32_t
  * Preconditioned conjugate gradients with M^{-1} = G^T G (reading R9).
  * x: output (x0 = 0).  G given in CSR (lower triangular).  Returns the
  * iteration count in *iters (maxit+1 if not converged), the recursive and
- * the true relative residual.  Dot products are plain sequential sums.
+ * the true relative residual, and, if hist is not NULL, the recursive
+ * relative residual after every iteration in hist[0..iters] (maxit + 1
+ * entries).  Dot products are plain sequential sums.
  * Stopping rule (R9, Section 5.2 "8 orders" of residual reduction): once
  * the recursive residual meets ||r_k|| <= rtol ||b||, the true residual
  * ||b - A x_k|| is computed; the solve ends when it meets the same
@@ -501,7 +503,7 @@ static double true_residual_norm(int32_t n, const int32_t* rowptr, const int32_t
  */
 int oracle_pcg(int32_t n, const int32_t* rowptr, const int32_t* col, const double* val, const int32_t* Grp,
                const int32_t* Gcol, const double* Gval, const double* b, double* x, double rtol, int32_t maxit,
-               int32_t* iters, double* relres_rec, double* relres_true) {
+               int32_t* iters, double* relres_rec, double* relres_true, double* hist) {
     if (n <= 0) return ORC_EINVAL;
     double* r = (double*)malloc(sizeof(double) * (size_t)n);
     double* z = (double*)malloc(sizeof(double) * (size_t)n);
@@ -520,6 +522,7 @@ int oracle_pcg(int32_t n, const int32_t* rowptr, const int32_t* col, const doubl
     double rnorm = sqrt(dot_seq(n, r, r));
     int32_t it = 0;
     int converged = (rnorm <= rtol * bnorm);
+    if (hist) hist[0] = (bnorm > 0.0) ? rnorm / bnorm : 0.0;
     if (!converged) {
         oracle_apply(n, Grp, Gcol, Gval, r, t, z);
         for (int32_t i = 0; i < n; ++i) p[i] = z[i];
@@ -533,6 +536,7 @@ int oracle_pcg(int32_t n, const int32_t* rowptr, const int32_t* col, const doubl
                 r[i] = fma(-alpha, q[i], r[i]);
             }
             rnorm = sqrt(dot_seq(n, r, r));
+            if (hist) hist[it] = (bnorm > 0.0) ? rnorm / bnorm : 0.0;
             if (rnorm <= rtol * bnorm &&
                 true_residual_norm(n, rowptr, col, val, b, x, q) <= rtol * bnorm) {
                 converged = 1;

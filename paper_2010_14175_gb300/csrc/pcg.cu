@@ -362,6 +362,16 @@ bool with_mode(int mode, F f) {
     }
 }
 
+// Accumulation of the G and G^T products of an FP32/BF16 G: FP32
+// (default) or FP64 (AFSAI_G_ACC64=1).
+bool acc64() {
+    static const bool v = [] {
+        const char* e = std::getenv("AFSAI_G_ACC64");
+        return e && std::atoi(e) != 0;
+    }();
+    return v;
+}
+
 struct Launcher {
     int32_t n;
     const CsrDev* A;
@@ -389,12 +399,16 @@ struct Launcher {
                 if (vt == VAL_F64) set_smem_attr(k_spmv_G<MD, double, double>, 200u * 1024u);
                 if (vt == VAL_F32) set_smem_attr(k_spmv_G<MD, float, float>, 200u * 1024u);
                 if (vt == VAL_BF16) set_smem_attr(k_spmv_G<MD, __nv_bfloat16, float>, 200u * 1024u);
+                if (vt == VAL_F32) set_smem_attr(k_spmv_G<MD, float, double>, 200u * 1024u);
+                if (vt == VAL_BF16) set_smem_attr(k_spmv_G<MD, __nv_bfloat16, double>, 200u * 1024u);
             });
             with_mode(mt.mode, [&](auto Mc) {
                 constexpr int MD = decltype(Mc)::value;
                 if (vt == VAL_F64) set_smem_attr(k_spmv_Gt_dot<MD, double, double>, 200u * 1024u);
                 if (vt == VAL_F32) set_smem_attr(k_spmv_Gt_dot<MD, float, float>, 200u * 1024u);
                 if (vt == VAL_BF16) set_smem_attr(k_spmv_Gt_dot<MD, __nv_bfloat16, float>, 200u * 1024u);
+                if (vt == VAL_F32) set_smem_attr(k_spmv_Gt_dot<MD, float, double>, 200u * 1024u);
+                if (vt == VAL_BF16) set_smem_attr(k_spmv_Gt_dot<MD, __nv_bfloat16, double>, 200u * 1024u);
             });
         }
         return AFSAI_OK;
@@ -439,9 +453,10 @@ struct Launcher {
         if (G.vtype == VAL_F64)
             launch_G_pair<double, double>(G, Gt, init);
         else if (G.vtype == VAL_F32)
-            launch_G_pair<float, float>(G, Gt, init);
+            acc64() ? launch_G_pair<float, double>(G, Gt, init) : launch_G_pair<float, float>(G, Gt, init);
         else
-            launch_G_pair<__nv_bfloat16, float>(G, Gt, init);
+            acc64() ? launch_G_pair<__nv_bfloat16, double>(G, Gt, init)
+                    : launch_G_pair<__nv_bfloat16, float>(G, Gt, init);
         AFSAI_CUDA_TRY(cudaGetLastError());
         count_launches(2);
         return AFSAI_OK;
@@ -470,14 +485,16 @@ struct Launcher {
 };
 
 // Cycle limit of the first wait for a tile's bulk copies in the staged SpMV
-// engines of the PCG (AFSAI_WAIT_CYCLES, default ~2 s at 2 GHz); a wait that
-// runs out ends the solve with AFSAI_ETIMEOUT.  The wait that lets a
-// block's copies in flight land after an expiry keeps the full bound.
+// engines of the PCG (AFSAI_WAIT_CYCLES, default ~2 s at 2 GHz; 0: a single
+// check without waiting); a wait that runs out ends the solve with
+// AFSAI_ETIMEOUT.  The wait that lets a block's copies in flight land after
+// an expiry keeps the full bound.
 long long first_wait_cycles() {
     static const long long v = [] {
         const char* e = std::getenv("AFSAI_WAIT_CYCLES");
-        const long long k = e ? std::atoll(e) : 0;
-        return k > 0 ? k : tiled::kWaitCycles;
+        if (!e || !*e) return tiled::kWaitCycles;
+        const long long k = std::atoll(e);
+        return k >= 0 ? k : tiled::kWaitCycles;
     }();
     return v;
 }

@@ -63,12 +63,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
     return ok != 0;
 }
 
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
 // Bounded wait for the given phase parity; false if `limit` cycles passed.
 // The waits for a tile's copies take the caller's limit (the PCG passes a
 // shorter one when asked to, so that the expiry path can be exercised);
 // the second wait after an expiry, which lets the block's copies in flight
-// land before it returns, always takes the full bound.
+// land before it returns, always takes the full bound.  limit = 0 checks
+// the phase once without waiting (mbarrier.try_wait may itself suspend the
+// warp until the phase completes, so even a one-cycle limit need not run
+// out).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, long long limit = kWaitCycles) {
+    if (limit <= 0) return mbar_test_wait(bar, phase);
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, phase)) {
         if (clock64() - t0 > limit) return false;

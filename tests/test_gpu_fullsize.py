@@ -1,15 +1,18 @@
 """Full-size parity in the benchmark's launch configuration.
 
-The elasticity 48^3 solve (the benchmark workload) and the 256^3
-heterogeneous diffusion solve run at full size through the C ABI as
-bench.py runs them.  The oracle cannot redo every row at these sizes in a
-test, so it recomputes sampled rows one by one (the first rows, the last
-rows and seeded random row ranges): their patterns and FP64 values must be
-identical.  The solves are checked by properties that hold at any size:
-convergence to the true residual 1e-8, the oracle's iteration count +-1 for
-the elasticity case (the full oracle solve takes seconds there), and at most
-10% more iterations for the mixed form than for FP64.  For the elasticity
-case the preconditioner application (the engines the solve chose) is also
+The 256^3 heterogeneous diffusion solve (the benchmark workload) and the
+elasticity 48^3 solve run at full size through the C ABI as bench.py runs
+them.  The oracle cannot redo every row at these sizes in a test, so it
+recomputes sampled rows one by one (the first rows, the last rows and
+seeded random row ranges): their patterns and FP64 values must be
+identical.  The oracle's whole PCG runs at full size too (its G from its own
+full set-up): the GPU's FP64 solve must stop after exactly its iteration
+count (the oracle's recursive residual is clear of 1e-8 on both sides of
+its stopping iteration, so rounding cannot move the stop) with a true
+residual at most 1e-8.  The precision forms must reach the same true
+residual: FP32 G within 10% more iterations than FP64, BF16 G within 20%
+(it misses the 10% bar on the diffusion problem).  For the elasticity case
+the preconditioner application (the engines the solve chose) is also
 compared with the full oracle G^T (G r) within the rounding bound."""
 import numpy as np
 import pytest
@@ -57,13 +60,17 @@ def _solve(afsai, A, b, p, g_prec=0, chol_prec=0):
     return M, info, x
 
 
+def _clear_of_tolerance(hist, rtol=1e-8, margin=1e-6):
+    return hist[-1] < rtol * (1 - margin) and hist[-2] > rtol * (1 + margin)
+
+
 def test_elasticity48_full_size(gpu, oracle_mod):
     A, b, xs, p = mg.workload("elast48")
     M, info, x = _solve(gpu, A, b, p)
     rp, ci, va = M.export()
     psi, steps = M.rows()
     _check_rows(oracle_mod, A, p, rp, ci, va, psi, steps, _sample_ranges(A.n, 1))
-    assert info["converged"] == 1 and info["relres_true"] <= 1.05e-8
+    assert info["converged"] == 1 and info["relres_true"] <= 1e-8
     # full oracle solve (set-up + PCG) for the iteration count
     G = oracle_mod.afsai_setup(A, p["kiter"], p["s"], p["eps"])
     assert G.nnz == M.info()["nnz_G"]
@@ -77,11 +84,12 @@ def test_elasticity48_full_size(gpu, oracle_mod):
     absG = abs(G.to_scipy())
     bound = 64 * np.finfo(float).eps * (absG.T @ (absG @ np.abs(r)))
     assert np.all(np.abs(z.cpu().numpy() - oracle_mod.apply(G, r)) <= bound + 1e-300)
-    _, it_o, _, _ = oracle_mod.pcg(A, G, b, rtol=1e-8, maxit=20000)
-    assert abs(info["iters"] - it_o) <= 1, (info["iters"], it_o)
+    _, it_o, _, _, hist = oracle_mod.pcg(A, G, b, rtol=1e-8, maxit=20000, history=True)
+    assert _clear_of_tolerance(hist), hist[-2:]
+    assert info["iters"] == it_o, (info["iters"], it_o)
     # mixed form on the same input
     _, im, _ = _solve(gpu, A, b, p, 1, 1)
-    assert im["relres_true"] <= 1.05e-8 and im["iters"] <= int(np.ceil(1.10 * info["iters"]))
+    assert im["relres_true"] <= 1e-8 and im["iters"] <= int(np.ceil(1.10 * info["iters"]))
 
 
 def test_hetero256_full_size(gpu, oracle_mod):
@@ -90,9 +98,16 @@ def test_hetero256_full_size(gpu, oracle_mod):
     rp, ci, va = M.export()
     psi, steps = M.rows()
     _check_rows(oracle_mod, A, p, rp, ci, va, psi, steps, _sample_ranges(A.n, 2, count=8, width=256))
-    assert info["converged"] == 1 and info["relres_true"] <= 1.05e-8
+    assert info["converged"] == 1 and info["relres_true"] <= 1e-8
     M.close()
-    for g_prec, chol_prec in ((1, 1), (1, 0)):
+    G = oracle_mod.afsai_setup(A, p["kiter"], p["s"], p["eps"])
+    assert G.nnz == len(ci)
+    _, it_o, _, _, hist = oracle_mod.pcg(A, G, b, rtol=1e-8, maxit=20000, history=True)
+    assert _clear_of_tolerance(hist), hist[-2:]
+    assert info["iters"] == it_o, (info["iters"], it_o)
+    del G
+    for g_prec, chol_prec in ((1, 1), (1, 0), (2, 1), (2, 0)):
         _, im, _ = _solve(gpu, A, b, p, g_prec, chol_prec)
-        assert im["relres_true"] <= 1.05e-8
-        assert im["iters"] <= int(np.ceil(1.10 * info["iters"])), (g_prec, chol_prec, im["iters"], info["iters"])
+        bar = 1.10 if g_prec == 1 else 1.20
+        assert im["converged"] == 1 and im["relres_true"] <= 1e-8
+        assert im["iters"] <= int(np.ceil(bar * info["iters"])), (g_prec, chol_prec, im["iters"], info["iters"])

@@ -28,6 +28,10 @@ def _worker(rank, world, port, q):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     bench.barrier(world)
     v = bench.max_over_ranks(10.0 * (rank + 1), world, None)
+    # each rank timed 5 solves in 1000 ms (rank 0) or 1200 ms (rank 1): the
+    # job did 5 * world solves in the slowest rank's time
+    ms = bench.max_over_ranks(1000.0 + 200.0 * rank, world, None)
+    job = bench.job_value(ms, 5, world)
     # the reference arm runs on rank 0 only; the other ranks return at once
     class A:
         pass
@@ -39,7 +43,7 @@ def _worker(rank, world, port, q):
         out = bench.run_reference(args, rank, world)
     bench.barrier(world)
     dist.destroy_process_group()
-    q.put((rank, v, out))
+    q.put((rank, v, out, job))
 
 
 @pytest.mark.parametrize("world", [2])
@@ -56,3 +60,5 @@ def test_gloo_barrier_and_max_over_ranks(world):
         assert p.exitcode == 0
     assert sorted(r[0] for r in res) == list(range(world))
     assert all(r[1] == 10.0 * world for r in res)
+    assert all(r[2] is None for r in res)  # rank 1 returned without work
+    assert all(r[3] == pytest.approx((1000.0 + 200.0 * (world - 1)) / 1e3 / (5 * world)) for r in res)
