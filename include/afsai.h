@@ -124,10 +124,15 @@ typedef struct {
 
 typedef struct {
     int32_t iters;       /* PCG iterations performed */
-    int32_t converged;   /* 1 if ||r_k|| <= rtol ||b|| was reached */
+    int32_t converged;   /* 1 if both ||r_k|| and ||b - A x_k|| reached rtol ||b|| */
     double relres_rec;   /* recursive ||r_k|| / ||b|| at exit */
     double relres_true;  /* ||b - A x|| / ||b|| recomputed at exit */
     double solve_ms;     /* device time of the solve (CUDA events) */
+    double kernel_ms[5]; /* pcg_solve with a preconditioner: device time of each
+                            kernel of one iteration (q = A p with p.q; the x, r
+                            update with r.r; t = G r; z = G^T t with r.z; the
+                            p update), from CUDA events around the first
+                            iteration of the first graph launch; else 0 */
 } pcg_info;
 
 /* Builds the aFSAI preconditioner of A (Section 2): for every row i, grow
@@ -317,6 +322,21 @@ AFSAI_API const char* afsai_last_error(void);
 /* Number of CUDA kernels this library has launched in the process so far
  * (kernels inside CUDA graph launches included). */
 AFSAI_API int64_t afsai_kernel_launches(void);
+
+/* Device memory pool of the library (no counterpart in the paper).  Every
+ * device allocation of the library (set-up temporaries, G and G^T, PCG
+ * vectors, batch and server tables) comes from a stream-ordered memory
+ * pool that the library creates on each device at first use; memory freed
+ * by the library stays in that pool for its next call instead of being
+ * returned to the device (the environment variable AFSAI_POOL=0 makes the
+ * library use the device's default pool instead).
+ * afsai_trim_pool returns the unused memory of the current device's pool
+ * to the device (cudaMemPoolTrimTo); memory of live handles stays.
+ * afsai_pool_stats writes the bytes in use and the bytes reserved by the
+ * current device's pool (either pointer may be NULL, not both; 0 and 0
+ * without a pool).  Both return AFSAI_OK, AFSAI_EINVAL or AFSAI_ECUDA. */
+AFSAI_API afsai_status afsai_trim_pool(void);
+AFSAI_API afsai_status afsai_pool_stats(int64_t* used_bytes, int64_t* reserved_bytes);
 
 /* Library version string. */
 AFSAI_API const char* afsai_version(void);

@@ -32,6 +32,7 @@ EXPORTS = (
     "afsai_export_G", "afsai_export_Gt", "afsai_export_rows", "afsai_destroy", "afsai_last_error", "afsai_version",
     "afsai_kernel_launches", "afsai_apply_static", "afsai_batch_solve", "serve_create", "serve_register",
     "serve_submit", "serve_poll", "serve_get_stats", "serve_destroy", "afsai_spmv_engine", "afsai_check_arith",
+    "afsai_trim_pool", "afsai_pool_stats",
 )
 
 
@@ -77,11 +78,15 @@ class ServeStats(ctypes.Structure):
 
 class PcgInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("converged", ctypes.c_int32), ("relres_rec", ctypes.c_double),
-                ("relres_true", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+                ("relres_true", ctypes.c_double), ("solve_ms", ctypes.c_double), ("kernel_ms", ctypes.c_double * 5)]
 
 
 def _as_dict(s):
-    return {k: getattr(s, k) for k, _ in s._fields_}
+    out = {}
+    for k, _ in s._fields_:
+        v = getattr(s, k)
+        out[k] = list(v) if isinstance(v, ctypes.Array) else v
+    return out
 
 
 def library_path() -> str:
@@ -152,6 +157,10 @@ def load(build_if_missing: bool = True):
         lib.afsai_check_arith.restype = ctypes.c_int
         lib.afsai_kernel_launches.argtypes = []
         lib.afsai_kernel_launches.restype = ctypes.c_int64
+        lib.afsai_trim_pool.argtypes = []
+        lib.afsai_trim_pool.restype = ctypes.c_int
+        lib.afsai_pool_stats.argtypes = [P, P]
+        lib.afsai_pool_stats.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -174,6 +183,20 @@ def check_arith(n: int, seed: int = 1, stream=None):
 def kernel_launches() -> int:
     """Kernels launched by the library so far in this process."""
     return int(load().afsai_kernel_launches())
+
+
+def pool_stats():
+    """(bytes in use, bytes reserved) of the library's memory pool on the
+    current device."""
+    used, reserved = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().afsai_pool_stats(ctypes.cast(ctypes.byref(used), ctypes.c_void_p),
+                                   ctypes.cast(ctypes.byref(reserved), ctypes.c_void_p)))
+    return int(used.value), int(reserved.value)
+
+
+def trim_pool():
+    """Returns the unused memory of the library's pool on the current device."""
+    _check(load().afsai_trim_pool())
 
 
 def _check(status):

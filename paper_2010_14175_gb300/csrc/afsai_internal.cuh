@@ -33,6 +33,21 @@ afsai_status fail(afsai_status st, const std::string& msg);
     } while (0)
 
 // ---------------------------------------------------------------------------
+// device memory: the library's own stream-ordered pool per device
+// ---------------------------------------------------------------------------
+// Stream-ordered allocation from a pool that the library owns on each
+// device (created at first use on the current device).  Freed blocks stay
+// in the pool for the next call instead of being unmapped and mapped again
+// (a set-up of the 256^3 problem allocates and frees several GB of
+// temporaries); afsai_trim_pool returns them to the device.  With
+// AFSAI_POOL=0 the device's default pool is used instead.
+cudaMemPool_t lib_pool();
+inline cudaError_t lib_malloc_async(void** p, size_t bytes, cudaStream_t st) {
+    cudaMemPool_t pool = lib_pool();
+    return pool ? cudaMallocFromPoolAsync(p, bytes, pool, st) : cudaMallocAsync(p, bytes, st);
+}
+
+// ---------------------------------------------------------------------------
 // device buffers (stream-ordered allocation)
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -49,7 +64,7 @@ struct DevBuf {
         st = s;
         n = count;
         if (count == 0) return AFSAI_OK;
-        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&p), count * sizeof(T), s);
+        cudaError_t e = lib_malloc_async(reinterpret_cast<void**>(&p), count * sizeof(T), s);
         if (e != cudaSuccess) {
             p = nullptr;
             n = 0;

@@ -3,6 +3,8 @@
 #include <atomic>
 #include <cstring>
 #include <new>
+#include <mutex>
+#include <cstdlib>
 #include <string>
 
 #include "afsai_internal.cuh"
@@ -118,6 +120,39 @@ afsai_status export_csr(const CsrDev& C, int32_t* rowptr, int32_t* col, double* 
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+namespace {
+constexpr int kPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kPoolDevices] = {};
+bool g_pool_failed[kPoolDevices] = {};
+}  // namespace
+
+cudaMemPool_t lib_pool() {
+    static const bool enabled = [] {
+        const char* e = std::getenv("AFSAI_POOL");
+        return !e || std::atoi(e) != 0;
+    }();
+    if (!enabled) return nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kPoolDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (g_pools[dev] || g_pool_failed[dev]) return g_pools[dev];
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        g_pool_failed[dev] = true;  // the default pool serves
+        return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[dev] = pool;
+    return pool;
+}
+
 void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 void set_launches(int64_t v) { g_launches.store(v, std::memory_order_relaxed); }
@@ -197,6 +232,26 @@ const char* afsai_last_error(void) { return g_last_error.c_str(); }
 const char* afsai_version(void) { return "afsai-gb300 0.1 (sm_103a)"; }
 
 int64_t afsai_kernel_launches(void) { return launches_so_far(); }
+
+afsai_status afsai_trim_pool(void) {
+    cudaMemPool_t pool = lib_pool();
+    if (!pool) return AFSAI_OK;
+    AFSAI_CUDA_TRY(cudaMemPoolTrimTo(pool, 0));
+    return AFSAI_OK;
+}
+
+afsai_status afsai_pool_stats(int64_t* used_bytes, int64_t* reserved_bytes) {
+    if (!used_bytes && !reserved_bytes) return fail(AFSAI_EINVAL, "NULL arguments");
+    uint64_t used = 0, reserved = 0;
+    cudaMemPool_t pool = lib_pool();
+    if (pool) {
+        AFSAI_CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+        AFSAI_CUDA_TRY(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved));
+    }
+    if (used_bytes) *used_bytes = static_cast<int64_t>(used);
+    if (reserved_bytes) *reserved_bytes = static_cast<int64_t>(reserved);
+    return AFSAI_OK;
+}
 
 int32_t afsai_spmv_engine(int32_t role, int32_t n, int64_t nnz, int32_t vtype) {
     if (role < 0 || role > 2) return 0;

@@ -384,12 +384,12 @@ afsai_status BatchEngine::reserve(int32_t max_sys, int64_t max_chunks, cudaStrea
     release(st);
     cap_sys = std::max<int32_t>(max_sys, 1);
     cap_chunks = std::max<int64_t>(max_chunks, 1);
-    AFSAI_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_sys), sizeof(BSys) * cap_sys, st));
-    AFSAI_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_sc), sizeof(BScal) * cap_sys, st));
-    AFSAI_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_chunks), sizeof(BChunk) * cap_chunks, st));
-    AFSAI_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_partials), sizeof(double) * cap_chunks, st));
-    AFSAI_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_partials2), sizeof(double) * cap_chunks, st));
-    AFSAI_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&d_counts), sizeof(int32_t) * 4, st));
+    AFSAI_CUDA_TRY(lib_malloc_async(reinterpret_cast<void**>(&d_sys), sizeof(BSys) * cap_sys, st));
+    AFSAI_CUDA_TRY(lib_malloc_async(reinterpret_cast<void**>(&d_sc), sizeof(BScal) * cap_sys, st));
+    AFSAI_CUDA_TRY(lib_malloc_async(reinterpret_cast<void**>(&d_chunks), sizeof(BChunk) * cap_chunks, st));
+    AFSAI_CUDA_TRY(lib_malloc_async(reinterpret_cast<void**>(&d_partials), sizeof(double) * cap_chunks, st));
+    AFSAI_CUDA_TRY(lib_malloc_async(reinterpret_cast<void**>(&d_partials2), sizeof(double) * cap_chunks, st));
+    AFSAI_CUDA_TRY(lib_malloc_async(reinterpret_cast<void**>(&d_counts), sizeof(int32_t) * 4, st));
     AFSAI_CUDA_TRY(cudaMemsetAsync(d_counts, 0, sizeof(int32_t) * 4, st));
     AFSAI_CUDA_TRY(cudaMallocHost(reinterpret_cast<void**>(&h_counts), sizeof(int32_t) * 4));
     return AFSAI_OK;
@@ -704,6 +704,7 @@ afsai_status batch_solve_impl(int32_t nsys, const afsai_csr* A, const afsai_para
             for (int32_t k = 0; k < nsys; ++k) {
                 const double bn = std::sqrt(out[k].bb);
                 if (info) {
+                    info[k] = pcg_info{};
                     info[k].iters = out[k].iters;
                     info[k].converged = out[k].done == 1 ? 1 : 0;
                     info[k].relres_rec = bn > 0 ? std::sqrt(out[k].rr) / bn : 0.0;

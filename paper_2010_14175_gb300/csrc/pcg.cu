@@ -383,6 +383,12 @@ struct Launcher {
     cudaStream_t st;
     SpmvMode ma, mg, mt;
     long long wait;  // cycles a tile's copies may take before the solve gives up
+    // timestamps between the kernels of one iteration (6 events, recorded as
+    // event nodes of the captured graph), or nullptr
+    cudaEvent_t* marks = nullptr;
+    void mark(int k) {
+        if (marks) cudaEventRecordWithFlags(marks[k], st, cudaEventRecordExternal);
+    }
 
     // engine choice and shared-memory limits, before any stream capture
     afsai_status plan() {
@@ -415,6 +421,7 @@ struct Launcher {
     }
 
     afsai_status spmv_A_dot() {
+        mark(0);
         const auto* v = static_cast<const double*>(A->val);
         with_mode(ma.mode, [&](auto Mc) {
             k_spmv_A_dot<decltype(Mc)::value><<<ma.blocks, ma.threads, ma.smem, st>>>(
@@ -433,6 +440,7 @@ struct Launcher {
                 G.n, G.nnz, G.rowptr, G.col, static_cast<const VT*>(G.val), r, tt, s, mg.cap, init,
                 tiled::sell_view(G.sell), wait);
         });
+        mark(3);
         with_mode(mt.mode, [&](auto Mc) {
             k_spmv_Gt_dot<decltype(Mc)::value, VT, ACC><<<mt.blocks, mt.threads, mt.smem, st>>>(
                 Gt.n, Gt.nnz, Gt.rowptr, Gt.col, static_cast<const VT*>(Gt.val), tt, r, z, s, partials, mt.cap, init,
@@ -465,17 +473,21 @@ struct Launcher {
     // first half of an iteration: q = A p, alpha, x and r, the recursive test
     afsai_status head() {
         AFSAI_TRY(spmv_A_dot());
+        mark(1);
         k_update_xr<<<vec_blocks(n), kThreads, 0, st>>>(n, x, r, p, q, s, partials);
         AFSAI_CUDA_TRY(cudaGetLastError());
         count_launches(1);
+        mark(2);
         return AFSAI_OK;
     }
     // second half: z = M r, beta, p
     afsai_status tail() {
         AFSAI_TRY(precond_dot(0));
+        mark(4);
         k_update_p<<<vec_blocks(n), kThreads, 0, st>>>(n, z, p, s);
         AFSAI_CUDA_TRY(cudaGetLastError());
         count_launches(1);
+        mark(5);
         return AFSAI_OK;
     }
     afsai_status iteration() {
@@ -576,7 +588,24 @@ afsai_status pcg_body(const CsrDev& Ain, const afsai_precond* M, const double* b
     AFSAI_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     const int64_t before_capture = launches_so_far();
     afsai_status cap = AFSAI_OK;
-    for (int k = 0; k < K && cap == AFSAI_OK; ++k) cap = L.iteration();
+    // the kernels of the graph's first iteration are timed (event nodes)
+    cudaEvent_t marks[6] = {};
+    bool have_marks = info != nullptr && M != nullptr;
+    for (int k = 0; k < 6 && have_marks; ++k)
+        if (cudaEventCreate(&marks[k]) != cudaSuccess) have_marks = false;
+    if (!have_marks) cudaGetLastError();
+    for (int k = 0; k < K && cap == AFSAI_OK; ++k) {
+        L.marks = (k == 0 && have_marks) ? marks : nullptr;
+        cap = L.iteration();
+    }
+    L.marks = nullptr;
+    struct MarkGuard {
+        cudaEvent_t* m;
+        ~MarkGuard() {
+            for (int k = 0; k < 6; ++k)
+                if (m[k]) cudaEventDestroy(m[k]);
+        }
+    } mark_guard{marks};
     const cudaError_t ce = cudaStreamEndCapture(st, &graph);
     const int64_t per_graph = launches_so_far() - before_capture;  // kernel nodes of one graph
     set_launches(before_capture);
@@ -589,6 +618,7 @@ afsai_status pcg_body(const CsrDev& Ain, const afsai_precond* M, const double* b
     const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     AFSAI_CUDA_TRY(ie);
+    double kernel_ms[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     Scalars* hs_pinned = nullptr;
     cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&hs_pinned), sizeof(Scalars));
     bool true_ok = false;
@@ -604,6 +634,11 @@ afsai_status pcg_body(const CsrDev& Ain, const afsai_precond* M, const double* b
             if (e == cudaSuccess) count_launches(per_graph);
             if (e == cudaSuccess) e = cudaMemcpyAsync(hs_pinned, sc.p, sizeof(Scalars), cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e == cudaSuccess && l == 0 && have_marks)
+                for (int k = 0; k < 5; ++k) {
+                    float km = 0.f;
+                    if (cudaEventElapsedTime(&km, marks[k], marks[k + 1]) == cudaSuccess) kernel_ms[k] = km;
+                }
             if (e == cudaSuccess && hs_pinned->done) break;
         }
         // the recursive residual met the tolerance: check the true one, and
@@ -676,6 +711,7 @@ afsai_status pcg_body(const CsrDev& Ain, const afsai_precond* M, const double* b
         info->relres_rec = bn > 0 ? std::sqrt(hs.rr) / bn : 0.0;
         info->relres_true = bn > 0 ? std::sqrt(tr2) / bn : 0.0;
         info->solve_ms = ms;
+        for (int k = 0; k < 5; ++k) info->kernel_ms[k] = kernel_ms[k];
     }
     if (hs.done == 3 || hs.err) return fail(AFSAI_ETIMEOUT, "a bounded device wait ran out during PCG");
     if (!converged) return fail(AFSAI_ENOCONV, "PCG reached maxit without convergence");

@@ -174,7 +174,7 @@ struct ServerImpl {
                 while (slots[slot].used) ++slot;
                 Slot& S = slots[slot];
                 const int64_t bytes = vec_bytes(m.n);
-                if (cudaMallocAsync(reinterpret_cast<void**>(&S.vec), bytes, st) != cudaSuccess) {
+                if (lib_malloc_async(reinterpret_cast<void**>(&S.vec), bytes, st) != cudaSuccess) {
                     *err = fail(AFSAI_ENOMEM, "vectors of a served system");
                     return changed;
                 }
@@ -377,9 +377,9 @@ afsai_status serve_register(afsai_server* S, const afsai_csr* A, int32_t* matrix
     cudaStream_t cs;
     AFSAI_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     afsai_status st = AFSAI_OK;
-    if (cudaMallocAsync(reinterpret_cast<void**>(&m->rowptr), 4 * (A->n + 1L), cs) != cudaSuccess ||
-        cudaMallocAsync(reinterpret_cast<void**>(&m->col), 4 * A->nnz, cs) != cudaSuccess ||
-        cudaMallocAsync(reinterpret_cast<void**>(&m->val), 8 * A->nnz, cs) != cudaSuccess)
+    if (lib_malloc_async(reinterpret_cast<void**>(&m->rowptr), 4 * (A->n + 1L), cs) != cudaSuccess ||
+        lib_malloc_async(reinterpret_cast<void**>(&m->col), 4 * A->nnz, cs) != cudaSuccess ||
+        lib_malloc_async(reinterpret_cast<void**>(&m->val), 8 * A->nnz, cs) != cudaSuccess)
         st = fail(AFSAI_ENOMEM, "matrix copy");
     if (st == AFSAI_OK &&
         (cudaMemcpyAsync(m->rowptr, A->rowptr, 4 * (A->n + 1L), cudaMemcpyDefault, cs) != cudaSuccess ||

@@ -53,6 +53,7 @@
 
 #include "afsai_internal.cuh"
 #include "fp64_rn.cuh"
+#include "spmv_tiled.cuh"
 
 namespace afsai {
 namespace {
@@ -1128,20 +1129,18 @@ constexpr int kLaneRowMax = 8;
 
 __device__ __forceinline__ bool occ_test(uint64_t occ, uint32_t h) { return (occ >> h) & 1ull; }
 
-template <int MC>
+template <int MC, int HT>
 __global__ void __launch_bounds__(128) step_gather_lane(StepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int HT = kLaneHT;
-    constexpr int LOG2 = 6;
-    static_assert((1 << LOG2) == HT, "table size");
+    constexpr int LOG2 = HT == 32 ? 5 : 6;
+    static_assert((1 << LOG2) == HT && HT <= 64, "table size");
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int nwb = blockDim.x >> 5;
-    unsigned char* wbase = smem_raw + static_cast<size_t>(warp) * (HT + MC) * 32 * 12;
-    double* sv = reinterpret_cast<double*>(wbase);                      // val[HT], g[MC]
-    int32_t* sk = reinterpret_cast<int32_t*>(wbase + (HT + MC) * 32 * 8);  // key[HT], P[MC]
+    unsigned char* wbase = smem_raw + static_cast<size_t>(warp) * (HT * 12 + MC * 4) * 32;
+    double* sv = reinterpret_cast<double*>(wbase);                    // val[HT]
+    int32_t* sk = reinterpret_cast<int32_t*>(wbase + HT * 32 * 8);   // key[HT], P[MC]
 #define TV(h) sv[(h) * 32 + lane]
-#define TG(t) sv[(HT + (t)) * 32 + lane]
 #define TK(h) sk[(h) * 32 + lane]
 #define TP(t) sk[(HT + (t)) * 32 + lane]
     const int64_t ngroups = (static_cast<int64_t>(a.n) + 31) / 32;
@@ -1151,17 +1150,16 @@ __global__ void __launch_bounds__(128) step_gather_lane(StepArgs a) {
         if (ii >= a.n || a.st[ii] != kStActive) continue;
         const int32_t i = static_cast<int32_t>(ii);
         const int m = a.m[ii];
-        for (int t = 0; t < m; ++t) {
-            TP(t) = a.P[ii * a.mc + t];
-            TG(t) = a.g[ii * a.mc + t];
-        }
+        for (int t = 0; t < m; ++t) TP(t) = a.P[ii * a.mc + t];
         // ---- Kaporin gradient over j < i (Eq. "grapsi"); row t + 1 of A
         // is loaded while row t is accumulated ----
         uint64_t occ = 0ull;
         int nk = 0;
         int32_t c0[kLaneRowMax], c1[kLaneRowMax];
         double v0[kLaneRowMax], v1[kLaneRowMax];
-        auto load_row = [&](int t, int32_t (&c)[kLaneRowMax], double (&v)[kLaneRowMax]) {
+        double g0 = 0.0, g1 = 0.0;  // g_r of the current and the next row
+        auto load_row = [&](int t, int32_t (&c)[kLaneRowMax], double (&v)[kLaneRowMax], double& gt) {
+            gt = a.g[ii * a.mc + t];
             const int32_t r = TP(t);
             const int32_t rb = __ldg(&a.rowptr[r]), re = __ldg(&a.rowptr[r + 1]);
 #pragma unroll
@@ -1171,10 +1169,10 @@ __global__ void __launch_bounds__(128) step_gather_lane(StepArgs a) {
                 v[q] = on ? __ldg(&a.val[rb + q]) : 0.0;
             }
         };
-        load_row(0, c0, v0);
+        load_row(0, c0, v0, g0);
         for (int t = 0; t < m; ++t) {
-            if (t + 1 < m) load_row(t + 1, c1, v1);
-            const double gr = TG(t);
+            if (t + 1 < m) load_row(t + 1, c1, v1, g1);
+            const double gr = g0;
 #pragma unroll
             for (int q = 0; q < kLaneRowMax; ++q) {
                 const int32_t j = c0[q];
@@ -1199,6 +1197,7 @@ __global__ void __launch_bounds__(128) step_gather_lane(StepArgs a) {
                 c0[q] = c1[q];
                 v0[q] = v1[q];
             }
+            g0 = g1;
             if (nk > HT - (HT >> 3)) break;
         }
         if (nk > HT - (HT >> 3)) {
@@ -1291,7 +1290,6 @@ __global__ void __launch_bounds__(128) step_gather_lane(StepArgs a) {
         a.st[ii] = kStSolve;
     }
 #undef TV
-#undef TG
 #undef TK
 #undef TP
 }
@@ -1413,7 +1411,9 @@ __global__ void __launch_bounds__(64) step_solve(StepArgs a) {
 // GATHER: the row's system is gathered here from A (gather_rows_lower)
 // instead of being read from the gather kernel's slot; the pattern is then
 // kept in the row's area too.
-template <int MC, int LPR, bool GATHER = false>
+// SQRT_INT: the per-column square root on the integer pipes too (rn::);
+// with 16 rows per warp the FP64 pipe, not issue, binds the kernel.
+template <int MC, int LPR, bool GATHER = false, bool SQRT_INT = false>
 __global__ void __launch_bounds__(128) step_solve_wide(StepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int TMC = MC * (MC + 1) / 2;
@@ -1469,7 +1469,8 @@ __global__ void __launch_bounds__(128) step_solve_wide(StepArgs a) {
             const bool act = spd && c < m;
             const double piv = act ? M[tri(c) + c] : 1.0;
             if (act && !positive(piv)) spd = false;
-            const double d = sqrt(piv);  // one warp operation for all rows (IEEE; the FP64 pipe has room)
+            // one warp operation for all rows
+            const double d = SQRT_INT ? rn::sqrt_rn(piv) : sqrt(piv);
             const rn::Divisor dv = rn::make_divisor(d);
             if (act && spd)
                 for (int r = c + 1 + sub; r < m; r += LPR) M[tri(r) + c] = rn::div_rn(M[tri(r) + c], dv);
@@ -1850,7 +1851,7 @@ afsai_status run_stepwise_t(const SetupArgs& o, int32_t kiter, cudaStream_t st) 
 // at most MC entries, s <= 4): the lane-per-row gather kernel and the
 // LPR-lanes-per-row solve kernel that gathers its system from A.  No
 // per-row system slot is allocated.
-template <int MC, int LPR, bool CHOL32>
+template <int MC, int LPR, bool CHOL32, int HT = kLaneHT, bool SQRT_INT = false>
 afsai_status run_stepwise_lane(const SetupArgs& o, int32_t kiter, cudaStream_t st) {
     const int32_t n = o.n;
     constexpr int TMC = MC * (MC + 1) / 2;
@@ -1903,8 +1904,8 @@ afsai_status run_stepwise_lane(const SetupArgs& o, int32_t kiter, cudaStream_t s
         }
         return wpb;
     };
-    auto kg = step_gather_lane<MC>;
-    const size_t per_warp_g = static_cast<size_t>(kLaneHT + MC) * 32 * 12;
+    auto kg = step_gather_lane<MC, HT>;
+    const size_t per_warp_g = static_cast<size_t>(HT * 12 + MC * 4) * 32;
     const int wpb_g = best_wpb(per_warp_g, 0);
     const size_t smem_g = per_warp_g * wpb_g;
     AFSAI_CUDA_TRY(cudaFuncSetAttribute(kg, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_g)));
@@ -1914,7 +1915,7 @@ afsai_status run_stepwise_lane(const SetupArgs& o, int32_t kiter, cudaStream_t s
         if constexpr (CHOL32)
             return step_solve_wide32<MC, LPR, true>;
         else
-            return step_solve_wide<MC, LPR, true>;
+            return step_solve_wide<MC, LPR, true, SQRT_INT>;
     }();
     constexpr int RPW = 32 / LPR;
     const size_t per_row = CHOL32 ? ((TMC + MC + (MC + 1) / 2) | 1) * sizeof(double) +
@@ -2162,8 +2163,8 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
     AFSAI_TRY(retry.alloc(n, st));
     AFSAI_TRY(counters.alloc(4, st));
     AFSAI_CUDA_TRY(cudaMemsetAsync(counters.p, 0, 4 * sizeof(int32_t), st));
-    AFSAI_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&M->psi), sizeof(double) * n, st));
-    AFSAI_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&M->steps), sizeof(int32_t) * n, st));
+    AFSAI_CUDA_TRY(lib_malloc_async(reinterpret_cast<void**>(&M->psi), sizeof(double) * n, st));
+    AFSAI_CUDA_TRY(lib_malloc_async(reinterpret_cast<void**>(&M->steps), sizeof(int32_t) * n, st));
 
     SetupArgs a{};
     a.n = n;
@@ -2218,10 +2219,25 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
         count_launches(1);
     } else if (!fused_only && lane_gather_applies(mcap, p->s, max_row_nnz)) {
         // small stencils: lane-per-row gather, 2 lanes per row in the solve
+        // (AFSAI_LANE_HT = 32 or 64 table slots per row; AFSAI_SOLVE_SQRT =
+        // 0 IEEE FP64 or 1 integer-pipe square roots)
+        static const int lane_ht = [] {
+            const char* e = std::getenv("AFSAI_LANE_HT");
+            return e && std::atoi(e) == 32 ? 32 : 64;
+        }();
+        static const bool sqrt_int = [] {
+            const char* e = std::getenv("AFSAI_SOLVE_SQRT");
+            return e && std::atoi(e) == 1;
+        }();
         if (chol32)
-            AFSAI_TRY((run_stepwise_lane<12, 2, true>(a, p->kiter, st)));
+            AFSAI_TRY(lane_ht == 32 ? (run_stepwise_lane<12, 2, true, 32>(a, p->kiter, st))
+                                    : (run_stepwise_lane<12, 2, true, 64>(a, p->kiter, st)));
+        else if (sqrt_int)
+            AFSAI_TRY(lane_ht == 32 ? (run_stepwise_lane<12, 2, false, 32, true>(a, p->kiter, st))
+                                    : (run_stepwise_lane<12, 2, false, 64, true>(a, p->kiter, st)));
         else
-            AFSAI_TRY((run_stepwise_lane<12, 2, false>(a, p->kiter, st)));
+            AFSAI_TRY(lane_ht == 32 ? (run_stepwise_lane<12, 2, false, 32>(a, p->kiter, st))
+                                    : (run_stepwise_lane<12, 2, false, 64>(a, p->kiter, st)));
     } else if (!fused_only && stepwise_supported(mcap) && !chol32)
         AFSAI_TRY(run_stepwise(a, mcap, ht, p->kiter, chol32, st, cand_bound));
     else if (!fused_only && (wide_lpr == 4 || wide_lpr == 8) && mcap > 20 && mcap <= 32 && (!chol32 || wide_mixed))
@@ -2277,12 +2293,12 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
     CsrDev& G = M->G;
     G.n = n;
     G.vtype = p->g_prec;
-    AFSAI_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&G.rowptr), sizeof(int32_t) * (n + 1), st));
+    AFSAI_CUDA_TRY(lib_malloc_async(reinterpret_cast<void**>(&G.rowptr), sizeof(int32_t) * (n + 1), st));
     int64_t nnz = 0;
     AFSAI_TRY(exclusive_scan_i32(len.p, G.rowptr, n, st, &nnz));
     G.nnz = nnz;
-    AFSAI_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&G.col), sizeof(int32_t) * std::max<int64_t>(nnz, 1), st));
-    AFSAI_CUDA_TRY(cudaMallocAsync(&G.val, val_bytes(G.vtype) * std::max<int64_t>(nnz, 1), st));
+    AFSAI_CUDA_TRY(lib_malloc_async(reinterpret_cast<void**>(&G.col), sizeof(int32_t) * std::max<int64_t>(nnz, 1), st));
+    AFSAI_CUDA_TRY(lib_malloc_async(&G.val, val_bytes(G.vtype) * std::max<int64_t>(nnz, 1), st));
     DevBuf<int32_t> colcount;
     AFSAI_TRY(colcount.alloc(static_cast<size_t>(n) + 1, st));
     AFSAI_CUDA_TRY(cudaMemsetAsync(colcount.p, 0, sizeof(int32_t) * (n + 1), st));
@@ -2306,10 +2322,14 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
     AFSAI_CUDA_TRY(cudaMemcpyAsync(&G.max_row, counters.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     AFSAI_TRY(build_transpose(G, &M->Gt, st));
     if (sliced) {
-        // the sliced copies only serve the sliced SpMV engines: without
-        // room for them the CSR engines serve and the set-up succeeds
+        // the sliced copies only serve the sliced SpMV engines: they are
+        // built for a role whose engine is sliced or not chosen yet for this
+        // shape; without room for them the CSR engines serve and the set-up
+        // succeeds
         const std::string keep = afsai_last_error();
-        if (build_sell(G, &G.sell, st) != AFSAI_OK || build_sell(M->Gt, &M->Gt.sell, st) != AFSAI_OK) {
+        const bool want_g = spmv_wants_sliced(ROLE_G, G), want_gt = spmv_wants_sliced(ROLE_GT, M->Gt);
+        if ((want_g && build_sell(G, &G.sell, st) != AFSAI_OK) ||
+            (want_gt && build_sell(M->Gt, &M->Gt.sell, st) != AFSAI_OK)) {
             free_sell(&G.sell, st);
             free_sell(&M->Gt.sell, st);
             cudaGetLastError();

@@ -274,9 +274,9 @@ static afsai_status transpose_typed(const CsrDev& G, CsrDev* Gt, cudaStream_t st
     Gt->n = n;
     Gt->nnz = G.nnz;
     Gt->vtype = G.vtype;
-    AFSAI_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&Gt->rowptr), sizeof(int32_t) * (n + 1), st));
-    AFSAI_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&Gt->col), sizeof(int32_t) * std::max<int64_t>(G.nnz, 1), st));
-    AFSAI_CUDA_TRY(cudaMallocAsync(&Gt->val, sizeof(VT) * std::max<int64_t>(G.nnz, 1), st));
+    AFSAI_CUDA_TRY(lib_malloc_async(reinterpret_cast<void**>(&Gt->rowptr), sizeof(int32_t) * (n + 1), st));
+    AFSAI_CUDA_TRY(lib_malloc_async(reinterpret_cast<void**>(&Gt->col), sizeof(int32_t) * std::max<int64_t>(G.nnz, 1), st));
+    AFSAI_CUDA_TRY(lib_malloc_async(&Gt->val, sizeof(VT) * std::max<int64_t>(G.nnz, 1), st));
     int64_t tot = 0;
     AFSAI_TRY(exclusive_scan_i32(cnt.p, Gt->rowptr, n, st, &tot));
     AFSAI_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * (n + 1), st));

@@ -6,9 +6,9 @@ allocating.  This file is collected last on purpose.
 
 Checks, through the C ABI: two calls in a row give the same z as
 afsai_apply (within the rounding bound the apply tests use); the second
-call changes neither the device's free memory nor the use of its default
-stream-ordered memory pool (read from the CUDA driver, so an allocation by
-any route would show); the first call works in a fresh process (the array
+call changes neither the device's free memory, nor the use of its default
+stream-ordered memory pool (both read from the CUDA driver), nor the use of
+the library's own memory pool (afsai_pool_stats); the first call works in a fresh process (the array
 was loaded by afsai_setup); n above the array's size is rejected with
 EINVAL."""
 import ctypes
@@ -83,10 +83,10 @@ def test_static_apply_matches_apply_twice(gpu, name, make, kiter, s, eps, g_prec
         z_static = torch.full((A.n,), np.nan, dtype=torch.float64, device="cuda")
         z_ref = torch.zeros(A.n, dtype=torch.float64, device="cuda")
         torch.cuda.synchronize()
-        before = mem.snapshot()
+        before = (mem.snapshot(), afsai.pool_stats())
         afsai.afsai_apply_static(M, rd, z_static)
         torch.cuda.synchronize()
-        after = mem.snapshot()
+        after = (mem.snapshot(), afsai.pool_stats())
         if call == 1:
             assert after == before, (before, after)
         afsai.afsai_apply(M, rd, z_ref)
