@@ -89,8 +89,11 @@ def measured_traffic(kernel_key, units):
         return None, "no ncu record"
     if rec.get("source_digest") != source_digest(rec["sources"]):
         return None, "kernel changed since the ncu capture"
-    per_unit = rec["dram_bytes"] / rec["units"]
-    return per_unit * units, f"ncu {rec['capture']}: {rec['dram_bytes']:.4g} B over {rec['units']} rows, scaled"
+    # units = 1: the record is per launch, scaled to the full-size workload
+    # by its own factor (rows of the full problem / rows of the capture)
+    scale = rec.get("scale_to_full", 1.0) if units == 1 else units / rec["units"]
+    return rec["dram_bytes"] * scale, (f"ncu {rec['capture']}: {rec['dram_bytes']:.4g} B over {rec['units']} rows, "
+                                       f"scaled x{scale:.4g}")
 
 
 
@@ -286,6 +289,60 @@ def spmv_bytes(n, nnz, val_bytes=8, x_bytes=8, y_bytes=8):
     """Compulsory bytes of y = A x: values, columns, row pointers, x once,
     y once."""
     return nnz * (val_bytes + 4) + 4 * (n + 1) + n * x_bytes + n * y_bytes
+
+
+FP64_DFMA_PER_S = 152 * 2 * 2.07e9  # derived FP64 peak: SMs x DFMA/clk x max clock (no measured FP64 figure)
+
+
+def setup_roofline(key, flops, kern_ms, rp, steps, p, A, form):
+    """The set-up kernels against their roof: the FP64 ALU for the FP64
+    Cholesky (algorithmic flops), the measured HBM bandwidth for the FP32
+    Cholesky (method-touched bytes)."""
+    traffic, traffic_note = measured_traffic(key, A.n)
+    if FORMS[form]["chol_prec"] == 0:
+        r = {"kernel": key, "bound": "alu", "achieved": flops / (kern_ms * 1e-3) / 1e12,
+             "peak": 2 * FP64_DFMA_PER_S / 1e12, "unit": "TFLOP/s", "traffic": traffic, "traffic_note": traffic_note,
+             "kernel_ms": kern_ms, "algorithmic_flops": flops,
+             "peak_source": "FP64 ALU: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived from unit counts)"}
+    else:
+        touched = setup_touched_bytes(rp, steps, p["s"], A.nnz / A.n)
+        r = {"kernel": key, "bound": "hbm", "achieved": touched / (kern_ms * 1e-3) / 1e9, "peak": MEASURED_HBM_GBS,
+             "unit": "GB/s", "traffic": traffic, "traffic_note": traffic_note, "kernel_ms": kern_ms,
+             "algorithmic_bytes": touched, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    r["frac"] = r["achieved"] / r["peak"]
+    return r
+
+
+def pcg_kernel_table(A, nnz_G, form, kms):
+    """Roofline of each PCG kernel from its in-graph device time (ms):
+    algorithmic bytes (matrix entries and row pointers once, each vector
+    read or written once) and FP64 fmas; the binding roof is the larger of
+    bytes / measured HBM bandwidth and fmas / derived FP64 rate."""
+    n, nnzA = A.n, A.nnz
+    w = {0: 8, 1: 4, 2: 2}[FORMS[form]["g_prec"]]
+    f64g = FORMS[form]["g_prec"] == 0
+    rows = [
+        # key, kernel, bytes, FP64 fmas
+        ("pcg_A", "k_spmv_A_dot (q = A p, p.q)", 12 * nnzA + 4 * (n + 1) + 8 * n + 8 * n, nnzA + n),
+        ("pcg_xr", "k_update_xr (x, r update, r.r)", 48 * n, 3 * n),
+        ("pcg_G", "k_spmv_G (t = G r)", (4 + w) * nnz_G + 4 * (n + 1) + 8 * n + 8 * n, nnz_G if f64g else 0),
+        ("pcg_Gt", "k_spmv_Gt_dot (z = G^T t, r.z)", (4 + w) * nnz_G + 4 * (n + 1) + 3 * 8 * n,
+         (nnz_G if f64g else 0) + n),
+        ("pcg_p", "k_update_p (p = z + beta p)", 24 * n, n),
+    ]
+    out = []
+    for (key, name, by, dfma), ms in zip(rows, kms):
+        ms = float(ms)
+        if by / (MEASURED_HBM_GBS * 1e9) >= dfma / FP64_DFMA_PER_S:
+            ach = by / (ms * 1e-3) / 1e9 if ms > 0 else None
+            rec = {"bound": "hbm", "achieved": ach, "peak": MEASURED_HBM_GBS, "unit": "GB/s"}
+        else:
+            ach = 2 * dfma / (ms * 1e-3) / 1e12 if ms > 0 else None
+            rec = {"bound": "alu", "achieved": ach, "peak": 2 * FP64_DFMA_PER_S / 1e12, "unit": "TFLOP/s"}
+        rec.update({"key": key, "kernel": name, "ms": ms, "bytes": by, "dfma": dfma,
+                    "frac": (rec["achieved"] / rec["peak"]) if rec["achieved"] else None})
+        out.append(rec)
+    return out
 
 
 def make_workload(name, scale):
@@ -510,6 +567,52 @@ def run_batch(args, rank, world, local):
         torch.cuda.synchronize()
         extra["sequential_fp64"] = {"value": (time.perf_counter() - t0) / nsys, "unit": "s/solve",
                                     "desc": "afsai_setup + pcg_solve per system, FP64, one after another"}
+    # end to end from pinned host buffers: every system's A and b copied in,
+    # the batched solve, every x read back, inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+        host = [(pin(np.asarray(A.rowptr, np.int32)), pin(np.asarray(A.col, np.int32)),
+                 pin(np.asarray(A.val, np.float64)), pin(np.asarray(b, np.float64))) for A, b, _ in systems]
+        xh = [torch.zeros(A.n, dtype=torch.float64).pin_memory() for A, _, _ in systems]
+
+        def e2e_once():
+            Ads, bds, xds = [], [], []
+            for (A, _, _), (rp, ci, va, bh) in zip(systems, host):
+                Ads.append(afsai.DeviceCSR(A.n, rp.to(dev, non_blocking=True), ci.to(dev, non_blocking=True),
+                                           va.to(dev, non_blocking=True)))
+                bds.append(bh.to(dev, non_blocking=True))
+                xds.append(torch.zeros_like(bds[-1]))
+            afsai.afsai_batch_solve(Ads, prm_of(form), bds, xds, rtol=1e-8, maxit=20000, stream=stream)
+            for xd, xo in zip(xds, xh):
+                xo.copy_(xd, non_blocking=True)
+            torch.cuda.synchronize()
+
+        e2e_once()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_once()
+        te = (time.perf_counter() - t0) / args.steps
+        e2e = {"value": te / nsys, "unit": "s/solve",
+               "h2d_bytes_per_step": int(sum(4 * (A.n + 1) + 12 * A.nnz + 8 * A.n for A, _, _ in systems)),
+               "d2h_bytes_per_step": int(sum(8 * A.n for A, _, _ in systems))}
+    # the CPU oracle on a bounded sample of the batch: whole solves (set-up
+    # and PCG to 1e-8) of every 32nd system, all cores, scaled by rows
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        sample = systems[::32]
+        t0 = time.perf_counter()
+        for A, b, _ in sample:
+            Go = oracle.afsai_setup(A, kiter, s_, eps)
+            oracle.pcg(A, Go, b, rtol=1e-8, maxit=20000)
+        ts = time.perf_counter() - t0
+        rows_s = sum(A.n for A, _, _ in sample)
+        cpu = {"value": ts / rows_s * ntot / nsys, "unit": "s/solve", "cores": oracle.num_threads(), "kind": "oracle",
+               "cpu": _cpu_model(), "extrapolated": True,
+               "sample": f"whole FP64 oracle solves of {len(sample)} of the {nsys} systems (every 32nd, "
+                         f"{rows_s} rows, {ts:.1f} s), scaled by rows to the batch and divided by {nsys} systems"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "s/solve", "n_gpus": world, "steps": args.steps,
@@ -522,7 +625,7 @@ def run_batch(args, rank, world, local):
             "pcg_iters_median": float(np.median(iters)), "relres_true_max": worst,
             "converged": binfos[-1]["converged"], "graph_launches": binfos[-1]["graph_launches"],
             "setup_rows_per_s": ntot / (setup_ms * 1e-3), "gpu_launches": int(launches), "roofline": roof,
-            "forms": extra, "e2e": None, "cpu_baseline": None, "clocks": clk,
+            "forms": extra, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
         }
         print(json.dumps(line), flush=True)
 
@@ -582,13 +685,15 @@ def run_serve(args, rank, world, local):
     clocks.start()
     launches0 = afsai.kernel_launches()
 
-    def poisson_run(nreq):
+    def poisson_run(nreq, trace=None):
         outstanding, done = [], []
         t_next = time.perf_counter()
         start = t_next
         for _ in range(nreq):
             t_next += rng.exponential(1.0 / lam)
             m, b = make_request()
+            if trace is not None:
+                trace.append((t_next - start, m, b))
             while True:
                 now = time.perf_counter()
                 if now >= t_next:
@@ -608,7 +713,8 @@ def run_serve(args, rank, world, local):
         return done, time.perf_counter() - start
 
     poisson_run(args.warm_requests)
-    done, wall = poisson_run(args.requests)
+    trace = []
+    done, wall = poisson_run(args.requests, trace)
     launches = afsai.kernel_launches() - launches0
     clk = clocks.stop()
     st = S.stats()
@@ -619,26 +725,33 @@ def run_serve(args, rank, world, local):
     solves = sum(r[2]["nrhs"] for r in done)
     worst = max(r[2]["max_relres_true"] for r in done)
     conv = all(r[2]["converged"] == 1 for r in done)
-    # plain FP64 path, one request at a time (G cached per matrix), on a sample
-    nseq = min(100, args.requests)
+    # the plain FP64 path serving the SAME arrival trace one request at a
+    # time (G cached per matrix): each request's service time is measured
+    # (pcg_solve per right-hand side, b copied in and x read back), and it
+    # starts when it has arrived and the previous one has finished, so its
+    # latency includes its queueing
     Ad = [afsai.DeviceCSR.from_host(A) for A in pool]
     Ms = {}
-    seq = [make_request() for _ in range(nseq)]
-    for m in set(m for m, _ in seq):
+    for m in set(m for _, m, _ in trace):
         Ms[m] = afsai.afsai_setup(Ad[m], afsai.params(8, 2, 1e-3))
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    lat_seq = []
-    for m, b in seq:
+    lat_seq, svc = [], []
+    clock_free = 0.0
+    for arr, m, b in trace:
         t1 = time.perf_counter()
         for j in range(b.shape[0]):
             bd = torch.from_numpy(b[j]).cuda()
             x = torch.zeros_like(bd)
             afsai.pcg_solve(Ad[m], Ms[m], bd, x, rtol=1e-8, maxit=20000)
             x.cpu()
-        lat_seq.append((time.perf_counter() - t1) * 1e3)
-    seq_wall = time.perf_counter() - t0
-    seq_solves = sum(b.shape[0] for _, b in seq) / seq_wall
+        service = time.perf_counter() - t1
+        svc.append(service * 1e3)
+        start = max(arr, clock_free)
+        clock_free = start + service
+        lat_seq.append((clock_free - arr) * 1e3)
+    seq_solves = sum(b.shape[0] for _, _, b in trace) / (sum(svc) / 1e3)
+    for Mm in Ms.values():
+        Mm.close()
     if rank == 0:
         line = {
             "metric": METRIC + "; serve p50/p99 ms", "value": float(np.percentile(lat, 50)) / 1e3, "unit": "s/request",
@@ -656,8 +769,12 @@ def run_serve(args, rank, world, local):
             "all_converged": conv, "relres_true_max": worst, "server_steps": st["steps"],
             "peak_mem_gb": st["peak_mem_bytes"] / 2 ** 30, "gpu_launches": int(launches),
             "sequential_fp64": {"solves_per_s": seq_solves, "p50_ms": float(np.percentile(lat_seq, 50)),
-                                "p99_ms": float(np.percentile(lat_seq, 99)), "requests": nseq,
-                                "desc": "pcg_solve per right-hand side, one request after another, G cached"},
+                                "p99_ms": float(np.percentile(lat_seq, 99)),
+                                "service_p50_ms": float(np.percentile(svc, 50)),
+                                "service_p99_ms": float(np.percentile(svc, 99)), "requests": len(trace),
+                                "desc": "the same arrival trace served one request at a time by pcg_solve per "
+                                        "right-hand side (G cached): latency = queueing + measured service"},
+            "p99_vs_sequential": float(np.percentile(lat, 99)) / float(np.percentile(lat_seq, 99)),
             "roofline": None, "e2e": {"value": float(np.percentile(lat, 50)) / 1e3, "unit": "s/request",
                                       "h2d_bytes_per_step": None, "d2h_bytes_per_step": None},
             "cpu_baseline": None, "clocks": clk,
@@ -770,13 +887,14 @@ def main():
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    setup_ms, solve_ms, iters, kernel_ms = [], [], [], []
+    setup_ms, solve_ms, iters, kernel_ms, pcg_kernel_ms = [], [], [], [], []
     ev0.record(stream)
     last = None
     for _ in range(args.steps):
         M, sinfo, pinfo = one_solve(prm)
         setup_ms.append(sinfo["setup_ms"])
         kernel_ms.append(sinfo["kernel_ms"])
+        pcg_kernel_ms.append(pinfo.get("kernel_ms", [0.0] * 5))
         solve_ms.append(pinfo["solve_ms"])
         iters.append(pinfo["iters"])
         if last is not None:
@@ -792,30 +910,34 @@ def main():
     M, sinfo, pinfo = last
     value = job_value(ms_total, args.steps, world)
 
-    # dominant kernel: the set-up's pattern-search kernels, timed together
-    # with CUDA events around their launches (one set-up: the fused kernel,
-    # or the stepwise gather and solve kernels of every step)
+    # the set-up's pattern-search kernels, timed together with CUDA events
+    # around their launches (the gather and solve kernels of every step)
     kern_ms = float(np.mean(kernel_ms))
     rp, ci, va = M.export()
     psi, steps = M.rows()
     flops = setup_flops(rp, steps, p["s"], A.nnz / A.n)
-    kkey = f"setup/{args.workload}/{args.form}"
-    traffic, traffic_note = measured_traffic(kkey, A.n)
-    if FORMS[args.form]["chol_prec"] == 0:
-        fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12  # TFLOP/s: SMs x DFMA/clk x 2 x max clock
-        roof = {"kernel": kkey, "bound": "alu", "achieved": flops / (kern_ms * 1e-3) / 1e12, "peak": fp64_peak,
-                "unit": "TFLOP/s", "frac": None, "traffic": traffic, "traffic_note": traffic_note,
-                "kernel_ms": kern_ms, "algorithmic_flops": flops,
-                "peak_source": "FP64 ALU: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived from unit counts)"}
+    skey = f"setup/{args.workload}/{args.form}"
+    setup_roof = setup_roofline(skey, flops, kern_ms, rp, steps, p, A, args.form)
+    # each PCG kernel, timed with CUDA event nodes around the first iteration
+    # of the solve's graph (on the solve's stream), averaged over the timed
+    # solves, against its own roof (algorithmic bytes and FP64 fmas)
+    kms = np.mean(np.array(pcg_kernel_ms, dtype=np.float64), axis=0)
+    kernels = pcg_kernel_table(A, sinfo["nnz_G"], args.form, kms)
+    # the dominant kernel of the solve: the largest device time per solve
+    # among the PCG kernels (x iterations) and the set-up kernels together
+    n_it = int(np.median(iters))
+    top = max(kernels, key=lambda k: k["ms"])
+    if kern_ms >= top["ms"] * n_it:
+        roof = dict(setup_roof)
+        roof["share_of_solve"] = kern_ms / (value * 1e3)
     else:
-        # reduced-precision factorisation: the set-up's roof is the bytes it
-        # must touch, against the measured HBM copy bandwidth
-        touched = setup_touched_bytes(rp, steps, p["s"], A.nnz / A.n)
-        roof = {"kernel": kkey, "bound": "hbm", "achieved": touched / (kern_ms * 1e-3) / 1e9,
-                "peak": MEASURED_HBM_GBS, "unit": "GB/s", "frac": None, "traffic": traffic,
-                "traffic_note": traffic_note, "kernel_ms": kern_ms, "algorithmic_bytes": touched,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+        traffic, traffic_note = measured_traffic(f"{top['key']}/{args.workload}/{args.form}", 1)
+        roof = {"kernel": top["kernel"], "bound": top["bound"], "achieved": top["achieved"], "peak": top["peak"],
+                "unit": top["unit"], "frac": top["frac"], "traffic": traffic, "traffic_note": traffic_note,
+                "kernel_ms": top["ms"], "algorithmic_bytes": top["bytes"], "algorithmic_dfma": top["dfma"],
+                "launches_per_solve": n_it, "share_of_solve": top["ms"] * n_it / (value * 1e3),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if top["bound"] == "hbm"
+                else "FP64 ALU: 152 SMs x 2 DFMA/clk x 2.07 GHz (derived from unit counts)"}
 
     # preconditioner application z = G^T (G r) through the C ABI: algorithmic
     # bytes (G and G^T entries and row pointers, r gathered, t written and
@@ -903,7 +1025,9 @@ def main():
             "relres_true": pinfo["relres_true"], "nnz_G": sinfo["nnz_G"],
             "setup_rows_per_s": A.n / (float(np.median(setup_ms)) * 1e-3),
             "solve_gbs": pcg_iteration_bytes(A, sinfo, args.form) * n_it / (float(np.median(solve_ms)) * 1e-3) / 1e9,
-            "gpu_launches": int(launches), "roofline": roof, "forms": extra, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": int(launches), "roofline": roof, "setup_roofline": setup_roof,
+            "pcg_kernels": [{k: v for k, v in r.items() if k != "key"} for r in kernels],
+            "forms": extra, "e2e": e2e, "cpu_baseline": cpu,
             "clocks": clk,
             "apply": apply_rec,
             # SpMV engines the timed run used (AFSAI_SPMV_MODES="a,g,gt" pins them for a profile)

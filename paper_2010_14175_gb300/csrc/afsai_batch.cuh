@@ -36,8 +36,8 @@ struct BSys {
 
 // Per-system scalars (device).
 struct BScal {
-    double rz, alpha, beta, rr, bb, tol2, rtol, true_rr;
-    int32_t done;   // 0 running, 1 converged, 2 maxit reached
+    double rz, alpha, beta, rr, bb, tolr, rtol, true_rr;  // tolr = rtol ||b||
+    int32_t done;   // 0 running, 1 converged, 2 maxit reached, 3 true residual to check (within an iteration)
     int32_t iters;
     int32_t maxit;
     int32_t fresh;  // 1: not initialised yet (the start kernels act on fresh systems only)
@@ -65,7 +65,7 @@ struct BatchEngine {
     BChunk* d_chunks = nullptr;
     double* d_partials = nullptr;
     double* d_partials2 = nullptr;
-    int32_t* d_counts = nullptr;  // [0] active systems, [1] chunks
+    int32_t* d_counts = nullptr;  // [0] active systems, [1] chunks, [2] loop budget, [3] finished in a launch
     int32_t* h_counts = nullptr;  // pinned
     int32_t cap_sys = 0;
     int64_t cap_chunks = 0;
@@ -88,15 +88,43 @@ struct BatchEngine {
     afsai_status iteration(cudaStream_t st);
     afsai_status precond(int init, cudaStream_t st);
     afsai_status capture(int iters_per_graph, cudaStream_t st);
+    // The whole PCG loop as one graph: a device-side while loop (a
+    // conditional graph node) whose body runs iters_per_body iterations and
+    // then a kernel that continues the loop while systems are running and
+    // at most max_bodies bodies have run (the bound is kept on the device,
+    // so the loop always ends).
+    // With stop_on_retire the loop also ends after a body in which a system
+    // finished (counts[3] > 0), and with host_flag (device view of mapped
+    // pinned memory) once the host sets it (a request arrived).
+    afsai_status capture_loop(int iters_per_body, int32_t max_bodies, cudaStream_t st, bool stop_on_retire = false,
+                              const volatile int32_t* host_flag = nullptr);
+    int32_t loop_bodies = 0;
+    // Before a launch of the loop graph: the body budget, and the count of
+    // systems finished during the launch cleared.
+    afsai_status arm_loop(cudaStream_t st);
     afsai_status launch_graph(cudaStream_t st);
     afsai_status read_active(cudaStream_t st, int32_t* active);
     afsai_status finish(cudaStream_t st, int only_done = 0);  // true residuals (of finished systems only)
 };
 
-// Packs the systems into one block-diagonal CSR and runs the set-up on it.
-// On return G and G^T of *out are packed with system-local column indices;
-// row_off holds the first packed row of every system (nsys + 1 entries).
+// Systems set up together: packed block-diagonally into one CSR whose
+// set-up runs once over all its rows.
+struct SetupBucket {
+    std::vector<int32_t> members;   // system indices of the batch
+    std::vector<int64_t> row_off;   // first packed row of each member (members + 1 entries)
+    afsai_precond* M = nullptr;     // G and G^T of the bucket, system-local column indices
+    int32_t max_row = 0;            // longest row of A in the bucket
+    int lane_lpr = 0;               // solve-kernel lanes per row chosen by the autotuner (0: default)
+};
+
+// Groups the systems into buckets by the length of their rows of A (rows of
+// at most 8 entries take the lane-per-row set-up path, longer rows the
+// warp-per-row path), chooses each bucket's solve-kernel tile (rows per
+// warp) with the set-up autotuner, packs each bucket and runs its set-up.
+// Each system's G lives in exactly one bucket and equals the G of that
+// system alone.
 afsai_status batch_setup(int32_t nsys, const afsai_csr* A, const afsai_params* p, cudaStream_t st,
-                         afsai_precond** out, std::vector<int64_t>* row_off);
+                         std::vector<SetupBucket>* buckets);
+void free_buckets(std::vector<SetupBucket>* buckets);
 
 }  // namespace afsai

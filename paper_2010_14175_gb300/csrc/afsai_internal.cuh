@@ -152,12 +152,19 @@ int spmv_engine_of(int role, int32_t n, int64_t nnz, int vtype);
 // sliced = true also builds the sliced copies of G and G^T (the PCG and
 // apply engines of a single system); the batched and serving forms, which
 // run their own kernels on the CSR, pass false.
+// Lanes per row of the solve kernel of the small-stencil set-up path (0:
+// the default for the pattern size).  The batched form's autotuner sets it
+// per bucket of systems.
+struct SetupTuning {
+    int lane_lpr = 0;
+};
+
 afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_row_nnz, cudaStream_t st,
-                        afsai_precond* M, bool sliced);
+                        afsai_precond* M, bool sliced, const SetupTuning* tune = nullptr);
 
 // afsai_setup with the choice of sliced copies (api.cu).
 afsai_status setup_precond(const afsai_csr* A, const afsai_params* p, cudaStream_t st, bool sliced,
-                           afsai_precond** out);
+                           afsai_precond** out, const SetupTuning* tune = nullptr);
 
 // Sparse building blocks (sparse.cu).
 afsai_status exclusive_scan_i32(const int32_t* in, int32_t* out, int32_t n, cudaStream_t st, int64_t* total_host);

@@ -199,7 +199,7 @@ afsai_status check_params(const afsai_params* p) {
 }
 
 afsai_status setup_precond(const afsai_csr* A, const afsai_params* params, cudaStream_t st, bool sliced,
-                           afsai_precond** out) {
+                           afsai_precond** out, const SetupTuning* tune) {
     if (!out) return fail(AFSAI_EINVAL, "out is NULL");
     *out = nullptr;
     AFSAI_TRY(check_params(params));
@@ -209,7 +209,7 @@ afsai_status setup_precond(const afsai_csr* A, const afsai_params* params, cudaS
     if (!M) return fail(AFSAI_ENOMEM, "host allocation");
     cudaGetDevice(&M->device);
     M->params = *params;
-    const afsai_status s = setup_impl(A, params, maxrow, st, M, sliced);
+    const afsai_status s = setup_impl(A, params, maxrow, st, M, sliced, tune);
     if (s != AFSAI_OK) {
         const std::string msg = g_last_error;
         destroy_precond(M, st);

@@ -27,6 +27,9 @@
 #include <cstdlib>
 #include <string>
 #include <vector>
+#include <tuple>
+#include <mutex>
+#include <map>
 
 #include "afsai_batch.cuh"
 
@@ -123,11 +126,12 @@ __global__ void kb_init(const BSys* __restrict__ sys, BScal* sc, const BChunk* _
             for (int32_t k = 0; k < sy.nchunks; ++k) b2 += reinterpret_cast<volatile double*>(partials2)[sy.chunk0 + k];
             s->rr = tot;
             s->bb = b2;
-            s->tol2 = s->rtol * s->rtol * b2;
+            s->tolr = s->rtol * sqrt(b2);
             s->iters = 0;
-            if (tot <= s->tol2) {
+            if (sqrt(tot) <= s->tolr) {  // r = b - A x0 is the true residual here
                 s->done = 1;
                 atomicSub(s->active, 1);
+                atomicAdd(s->active + 3, 1);
             }
         }
         __syncthreads();
@@ -272,15 +276,67 @@ __global__ void kb_update_xr(const BSys* __restrict__ sys, BScal* sc, const BChu
         if (system_sum(tp, sy, c, partials, &s->ticket[3], &tot) && threadIdx.x == 0) {
             s->rr = tot;
             s->iters += 1;
-            if (tot <= s->tol2) {
-                s->done = 1;
-                atomicSub(s->active, 1);
+            if (sqrt(tot) <= s->tolr) {
+                s->done = 3;  // the true residual decides (kb_true_check)
             } else if (s->iters >= s->maxit) {
                 s->done = 2;
                 atomicSub(s->active, 1);
+                atomicAdd(s->active + 3, 1);
             }
         }
         __syncthreads();
+    }
+}
+
+// ---- the stopping rule's second half (Section 5.2, 8 orders of reduction):
+// a system whose recursive residual met rtol ||b|| ends only if its true
+// residual ||b - A x|| does too; otherwise its recurrence continues (the
+// rest of this iteration runs for it) ------------------------------------
+__global__ void kb_true_check(const BSys* __restrict__ sys, BScal* sc, const BChunk* __restrict__ chunks,
+                              const int32_t* nchunks, double* partials) {
+    __shared__ double sh[32];
+    for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
+        const BChunk ch = chunks[c];
+        BScal* s = &sc[ch.sys];
+        if (s->done != 3) continue;
+        const BSys& sy = sys[ch.sys];
+        const int32_t i = ch.row0 + threadIdx.x;
+        double part = 0.0;
+        if (i < ch.row1) {
+            const double d = sy.b[i] - row_f64(sy.Arp, sy.Acol, sy.Aval, sy.x, i);
+            part = d * d;
+        }
+        const double tp = chunk_sum(part, sh);
+        double tot;
+        if (system_sum(tp, sy, c, partials, &s->ticket[5], &tot) && threadIdx.x == 0) {
+            s->true_rr = tot;
+            if (sqrt(tot) <= s->tolr) {
+                s->done = 1;
+                atomicSub(s->active, 1);
+                atomicAdd(s->active + 3, 1);
+            } else if (s->iters >= s->maxit) {
+                s->done = 2;
+                atomicSub(s->active, 1);
+                atomicAdd(s->active + 3, 1);
+            } else {
+                s->done = 0;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---- loop condition of the one-graph PCG: continue while systems run and
+// the body budget lasts (counts[2], set by the host before the launch) -----
+__global__ void kb_loop_cond(int32_t* counts, cudaGraphConditionalHandle h, int stop_on_retire,
+                             const volatile int32_t* host_flag) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const int32_t left = counts[2] - 1;
+        counts[2] = left;
+        bool go = counts[0] > 0 && left > 0;
+        if (stop_on_retire && counts[3] > 0) go = false;
+        if (host_flag && *host_flag != 0) go = false;
+        cudaGraphSetConditional(h, go ? 1u : 0u);
     }
 }
 
@@ -515,8 +571,9 @@ afsai_status BatchEngine::iteration(cudaStream_t st) {
     const int gb = grid_blocks();
     kb_A_dot<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, d_counts + 1, d_partials);
     kb_update_xr<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, d_counts + 1, d_partials);
+    kb_true_check<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, d_counts + 1, d_partials);
     AFSAI_CUDA_TRY(cudaGetLastError());
-    count_launches(2);
+    count_launches(3);
     AFSAI_TRY(precond(0, st));
     kb_update_p<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, d_counts + 1);
     AFSAI_CUDA_TRY(cudaGetLastError());
@@ -549,6 +606,58 @@ afsai_status BatchEngine::capture(int iters_per_graph, cudaStream_t st) {
     return AFSAI_OK;
 }
 
+afsai_status BatchEngine::arm_loop(cudaStream_t st) {
+    h_counts[2] = loop_bodies;
+    h_counts[3] = 0;
+    AFSAI_CUDA_TRY(cudaMemcpyAsync(d_counts + 2, h_counts + 2, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    return AFSAI_OK;
+}
+
+afsai_status BatchEngine::capture_loop(int iters_per_body, int32_t max_bodies, cudaStream_t st, bool stop_on_retire,
+                                       const volatile int32_t* host_flag) {
+    if (exec) {
+        cudaGraphExecDestroy(exec);
+        exec = nullptr;
+    }
+    graph_iters = iters_per_body;
+    loop_bodies = std::max<int32_t>(max_bodies, 1);
+    cudaGraph_t graph = nullptr;
+    AFSAI_CUDA_TRY(cudaGraphCreate(&graph, 0));
+    struct GraphGuard {
+        cudaGraph_t g;
+        ~GraphGuard() {
+            if (g) cudaGraphDestroy(g);
+        }
+    } guard{graph};
+    cudaGraphConditionalHandle handle;
+    AFSAI_CUDA_TRY(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    AFSAI_CUDA_TRY(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    AFSAI_CUDA_TRY(cudaStreamBeginCaptureToGraph(st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const int64_t before = launches_so_far();
+    afsai_status cap = AFSAI_OK;
+    for (int k = 0; k < iters_per_body && cap == AFSAI_OK; ++k) cap = iteration(st);
+    if (cap == AFSAI_OK) {
+        kb_loop_cond<<<1, 32, 0, st>>>(d_counts, handle, stop_on_retire ? 1 : 0, host_flag);
+        count_launches(1);
+    }
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(st, &captured);
+    per_graph = launches_so_far() - before;  // kernels of one body
+    set_launches(before);
+    AFSAI_TRY(cap);
+    AFSAI_CUDA_TRY(ce);
+    AFSAI_CUDA_TRY(cudaGetLastError());
+    AFSAI_CUDA_TRY(cudaGraphInstantiate(&exec, graph, 0));
+    return AFSAI_OK;
+}
+
 afsai_status BatchEngine::launch_graph(cudaStream_t st) {
     AFSAI_CUDA_TRY(cudaGraphLaunch(exec, st));
     count_launches(per_graph);
@@ -570,39 +679,65 @@ afsai_status BatchEngine::finish(cudaStream_t st, int only_done) {
 }
 
 // ---------------------------------------------------------------------------
-// Packed set-up of many systems
+// Packed set-up of many systems, by buckets
 // ---------------------------------------------------------------------------
-afsai_status batch_setup(int32_t nsys, const afsai_csr* A, const afsai_params* p, cudaStream_t st,
-                         afsai_precond** out, std::vector<int64_t>* row_off_h) {
-    row_off_h->assign(nsys + 1, 0);
-    std::vector<PackSrc> src(nsys);
-    int64_t nnz_total = 0;
-    for (int32_t s = 0; s < nsys; ++s) {
-        if (!A[s].rowptr || !A[s].col || !A[s].val || A[s].n <= 0 || A[s].nnz < A[s].n)
-            return fail(AFSAI_EINVAL, "system " + std::to_string(s) + ": invalid CSR descriptor");
-        src[s] = PackSrc{A[s].n, A[s].nnz, nnz_total, A[s].rowptr, A[s].col, A[s].val};
-        (*row_off_h)[s + 1] = (*row_off_h)[s] + A[s].n;
-        nnz_total += A[s].nnz;
+namespace {
+
+// Longest row of each system's A (one block per system).
+__global__ void kb_max_row(int32_t nsys, const PackSrc* __restrict__ src, int32_t* __restrict__ out) {
+    __shared__ int32_t sh[32];
+    for (int32_t s = blockIdx.x; s < nsys; s += gridDim.x) {
+        const PackSrc p = src[s];
+        int32_t mx = 0;
+        for (int32_t i = threadIdx.x; i < p.n; i += blockDim.x) mx = max(mx, p.rowptr[i + 1] - p.rowptr[i]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            int32_t v = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(kFull, v, o));
+            if (threadIdx.x == 0) out[s] = v;
+        }
+        __syncthreads();
     }
-    const int64_t nrows = (*row_off_h)[nsys];
+}
+
+// Packs the members of a bucket into one block-diagonal CSR and runs the
+// set-up on it; G and G^T come back with system-local column indices.
+afsai_status setup_packed(const std::vector<PackSrc>& all, const std::vector<int32_t>& members,
+                          const afsai_params* p, const SetupTuning* tune, cudaStream_t st, afsai_precond** out,
+                          std::vector<int64_t>* row_off_h) {
+    const int32_t nm = static_cast<int32_t>(members.size());
+    row_off_h->assign(nm + 1, 0);
+    std::vector<PackSrc> src(nm);
+    int64_t nnz_total = 0;
+    for (int32_t k = 0; k < nm; ++k) {
+        src[k] = all[members[k]];
+        src[k].nnz_off = nnz_total;
+        (*row_off_h)[k + 1] = (*row_off_h)[k] + src[k].n;
+        nnz_total += src[k].nnz;
+    }
+    const int64_t nrows = (*row_off_h)[nm];
     if (nrows >= INT32_MAX || nnz_total >= INT32_MAX) return fail(AFSAI_ENOTSUP, "batch larger than 2^31 rows/entries");
     DevBuf<PackSrc> dsrc;
     DevBuf<int64_t> droff;
     DevBuf<int32_t> bad, prp, pcol;
     DevBuf<double> pval;
-    AFSAI_TRY(dsrc.alloc(nsys, st));
-    AFSAI_TRY(droff.alloc(nsys + 1, st));
+    AFSAI_TRY(dsrc.alloc(nm, st));
+    AFSAI_TRY(droff.alloc(nm + 1, st));
     AFSAI_TRY(bad.alloc(1, st));
     AFSAI_TRY(prp.alloc(nrows + 1, st));
     AFSAI_TRY(pcol.alloc(nnz_total, st));
     AFSAI_TRY(pval.alloc(nnz_total, st));
-    AFSAI_CUDA_TRY(cudaMemcpyAsync(dsrc.p, src.data(), sizeof(PackSrc) * nsys, cudaMemcpyHostToDevice, st));
-    AFSAI_CUDA_TRY(cudaMemcpyAsync(droff.p, row_off_h->data(), sizeof(int64_t) * (nsys + 1), cudaMemcpyHostToDevice, st));
+    AFSAI_CUDA_TRY(cudaMemcpyAsync(dsrc.p, src.data(), sizeof(PackSrc) * nm, cudaMemcpyHostToDevice, st));
+    AFSAI_CUDA_TRY(cudaMemcpyAsync(droff.p, row_off_h->data(), sizeof(int64_t) * (nm + 1), cudaMemcpyHostToDevice, st));
     AFSAI_CUDA_TRY(cudaMemsetAsync(bad.p, 0, sizeof(int32_t), st));
     const int32_t tot32 = static_cast<int32_t>(nnz_total);
     AFSAI_CUDA_TRY(cudaMemcpyAsync(prp.p + nrows, &tot32, sizeof(int32_t), cudaMemcpyHostToDevice, st));
     const int blocks = std::max(1, std::min(ceil_div(nrows * 32, 256), num_sms() * 16));
-    kb_pack<<<blocks, 256, 0, st>>>(nsys, dsrc.p, droff.p, nrows, prp.p, pcol.p, pval.p, bad.p);
+    kb_pack<<<blocks, 256, 0, st>>>(nm, dsrc.p, droff.p, nrows, prp.p, pcol.p, pval.p, bad.p);
     AFSAI_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     int32_t hbad = 0;
@@ -611,13 +746,157 @@ afsai_status batch_setup(int32_t nsys, const afsai_csr* A, const afsai_params* p
     if (hbad) return fail(AFSAI_EINVAL, "a system has malformed row pointers");
     afsai_csr packed{static_cast<int32_t>(nrows), nnz_total, prp.p, pcol.p, pval.p};
     afsai_precond* M = nullptr;
-    AFSAI_TRY(setup_precond(&packed, p, st, false, &M));
-    kb_localize<<<blocks, 256, 0, st>>>(nsys, droff.p, M->G.rowptr, nrows, M->G.col);
-    kb_localize<<<blocks, 256, 0, st>>>(nsys, droff.p, M->Gt.rowptr, nrows, M->Gt.col);
+    AFSAI_TRY(setup_precond(&packed, p, st, false, &M, tune));
+    kb_localize<<<blocks, 256, 0, st>>>(nm, droff.p, M->G.rowptr, nrows, M->G.col);
+    kb_localize<<<blocks, 256, 0, st>>>(nm, droff.p, M->Gt.rowptr, nrows, M->Gt.col);
     AFSAI_CUDA_TRY(cudaGetLastError());
     count_launches(2);
     AFSAI_CUDA_TRY(cudaStreamSynchronize(st));
     *out = M;
+    return AFSAI_OK;
+}
+
+// Set-up autotuner: the solve kernel's tile (lanes per row, hence rows per
+// warp) of the lane-per-row path, per bucket shape (pattern capacity,
+// Cholesky precision), timed once per process on a sample of the bucket
+// (members in order up to ~120k rows, each candidate twice, best time) and
+// cached.  AFSAI_BATCH_LPR pins the choice.
+struct TuneKey {
+    int dev;
+    int64_t mcap;
+    int chol;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(dev, mcap, chol) < std::tie(o.dev, o.mcap, o.chol);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune_cache;
+
+afsai_status tune_lane_lpr(const std::vector<PackSrc>& all, const std::vector<int32_t>& members,
+                           const afsai_params* p, cudaStream_t st, int* lpr_out) {
+    const int64_t mcap = 1 + static_cast<int64_t>(p->kiter) * p->s;
+    static const int pinned = [] {
+        const char* e = std::getenv("AFSAI_BATCH_LPR");
+        return e ? std::atoi(e) : 0;
+    }();
+    if (pinned > 0) {
+        *lpr_out = pinned;
+        return AFSAI_OK;
+    }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const TuneKey key{dev, mcap, p->chol_prec};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            *lpr_out = it->second;
+            return AFSAI_OK;
+        }
+    }
+    std::vector<int32_t> sample;
+    int64_t rows = 0;
+    for (int32_t m : members) {
+        sample.push_back(m);
+        rows += all[m].n;
+        if (rows >= 120000) break;
+    }
+    const int cands[2] = {mcap > 12 ? 4 : 2, mcap > 12 ? 8 : 4};
+    float best = 0.f;
+    int choice = cands[0];
+    cudaEvent_t e0, e1;
+    AFSAI_CUDA_TRY(cudaEventCreate(&e0));
+    AFSAI_CUDA_TRY(cudaEventCreate(&e1));
+    afsai_status result = AFSAI_OK;
+    for (int c = 0; c < 2 && result == AFSAI_OK; ++c) {
+        SetupTuning t;
+        t.lane_lpr = cands[c];
+        for (int rep = 0; rep < 2 && result == AFSAI_OK; ++rep) {
+            afsai_precond* M = nullptr;
+            std::vector<int64_t> off;
+            cudaEventRecord(e0, st);
+            result = setup_packed(all, sample, p, &t, st, &M, &off);
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (M) afsai_destroy(M);
+            if (result == AFSAI_OK && (best == 0.f || ms < best)) {
+                best = ms;
+                choice = cands[c];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    AFSAI_TRY(result);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = choice;
+    *lpr_out = choice;
+    return AFSAI_OK;
+}
+
+}  // namespace
+
+void free_buckets(std::vector<SetupBucket>* buckets) {
+    for (auto& b : *buckets) {
+        if (b.M) afsai_destroy(b.M);
+        b.M = nullptr;
+    }
+    buckets->clear();
+}
+
+afsai_status batch_setup(int32_t nsys, const afsai_csr* A, const afsai_params* p, cudaStream_t st,
+                         std::vector<SetupBucket>* buckets) {
+    buckets->clear();
+    std::vector<PackSrc> all(nsys);
+    for (int32_t s = 0; s < nsys; ++s) {
+        if (!A[s].rowptr || !A[s].col || !A[s].val || A[s].n <= 0 || A[s].nnz < A[s].n)
+            return fail(AFSAI_EINVAL, "system " + std::to_string(s) + ": invalid CSR descriptor");
+        all[s] = PackSrc{A[s].n, A[s].nnz, 0, A[s].rowptr, A[s].col, A[s].val};
+    }
+    // longest row of every system
+    std::vector<int32_t> maxrow(nsys, 0);
+    {
+        DevBuf<PackSrc> dsrc;
+        DevBuf<int32_t> dmax;
+        AFSAI_TRY(dsrc.alloc(nsys, st));
+        AFSAI_TRY(dmax.alloc(nsys, st));
+        AFSAI_CUDA_TRY(cudaMemcpyAsync(dsrc.p, all.data(), sizeof(PackSrc) * nsys, cudaMemcpyHostToDevice, st));
+        kb_max_row<<<std::max(1, std::min(nsys, num_sms() * 8)), 256, 0, st>>>(nsys, dsrc.p, dmax.p);
+        AFSAI_CUDA_TRY(cudaGetLastError());
+        count_launches(1);
+        AFSAI_CUDA_TRY(cudaMemcpyAsync(maxrow.data(), dmax.p, sizeof(int32_t) * nsys, cudaMemcpyDeviceToHost, st));
+        AFSAI_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    // buckets by the length of the rows of A: at most kBucketShortRow
+    // entries (the lane-per-row set-up path), and longer
+    constexpr int32_t kBucketShortRow = 8;
+    std::vector<SetupBucket> out(2);
+    for (int32_t s = 0; s < nsys; ++s) {
+        SetupBucket& b = out[maxrow[s] <= kBucketShortRow ? 0 : 1];
+        b.members.push_back(s);
+        b.max_row = std::max(b.max_row, maxrow[s]);
+    }
+    const int64_t mcap = 1 + static_cast<int64_t>(p->kiter) * p->s;
+    for (auto& b : out) {
+        if (b.members.empty()) continue;
+        SetupTuning t;
+        if (b.max_row <= kBucketShortRow && mcap <= 20 && p->s <= 4 && p->kiter > 0) {
+            const afsai_status ts = tune_lane_lpr(all, b.members, p, st, &b.lane_lpr);
+            if (ts != AFSAI_OK) {
+                free_buckets(&out);
+                return ts;
+            }
+            t.lane_lpr = b.lane_lpr;
+        }
+        const afsai_status ss = setup_packed(all, b.members, p, &t, st, &b.M, &b.row_off);
+        if (ss != AFSAI_OK) {
+            free_buckets(&out);
+            return ss;
+        }
+        buckets->push_back(std::move(b));
+    }
     return AFSAI_OK;
 }
 
@@ -638,17 +917,34 @@ afsai_status batch_solve_impl(int32_t nsys, const afsai_csr* A, const afsai_para
     AFSAI_CUDA_TRY(cudaEventCreate(&e1));
     AFSAI_CUDA_TRY(cudaEventCreate(&e2));
     AFSAI_CUDA_TRY(cudaEventRecord(e0, st));
-    afsai_precond* M = nullptr;
-    std::vector<int64_t> row_off;
-    AFSAI_TRY(batch_setup(nsys, A, params, st, &M, &row_off));
+    std::vector<SetupBucket> buckets;
+    AFSAI_TRY(batch_setup(nsys, A, params, st, &buckets));
     AFSAI_CUDA_TRY(cudaEventRecord(e1, st));
+    // vectors: systems back to back in batch order
+    std::vector<int64_t> row_off(nsys + 1, 0);
+    for (int32_t k = 0; k < nsys; ++k) row_off[k + 1] = row_off[k] + A[k].n;
     const int64_t ntot = row_off[nsys];
+    int64_t nnz_G = 0;
+    for (const auto& bk : buckets) nnz_G += bk.M->info.nnz_G;
     DevBuf<double> vec;
     afsai_status s = vec.alloc(static_cast<size_t>(ntot) * 5, st);
     BatchEngine E;
     if (s == AFSAI_OK) {
         std::vector<BSys> sys(nsys);
         std::vector<BScal> sc(nsys);
+        for (const auto& bk : buckets) {
+            for (size_t m = 0; m < bk.members.size(); ++m) {
+                const int32_t k = bk.members[m];
+                const int64_t go = bk.row_off[m];
+                BSys& y = sys[k];
+                y.Grp = bk.M->G.rowptr + go;
+                y.Gcol = bk.M->G.col;
+                y.Gval = bk.M->G.val;
+                y.Trp = bk.M->Gt.rowptr + go;
+                y.Tcol = bk.M->Gt.col;
+                y.Tval = bk.M->Gt.val;
+            }
+        }
         for (int32_t k = 0; k < nsys; ++k) {
             BSys& y = sys[k];
             const int64_t o = row_off[k];
@@ -656,12 +952,6 @@ afsai_status batch_solve_impl(int32_t nsys, const afsai_csr* A, const afsai_para
             y.Arp = A[k].rowptr;
             y.Acol = A[k].col;
             y.Aval = A[k].val;
-            y.Grp = M->G.rowptr + o;
-            y.Gcol = M->G.col;
-            y.Gval = M->G.val;
-            y.Trp = M->Gt.rowptr + o;
-            y.Tcol = M->Gt.col;
-            y.Tval = M->Gt.val;
             y.b = b[k];
             y.x = x[k];
             y.r = vec.p + o;
@@ -674,19 +964,24 @@ afsai_status batch_solve_impl(int32_t nsys, const afsai_csr* A, const afsai_para
             c.rtol = rtol;
             c.maxit = maxit;
         }
-        E.vtype = M->G.vtype;
+        E.vtype = buckets.front().M->G.vtype;
         s = E.upload(sys, sc, st);
         if (s == AFSAI_OK) s = E.start(st);
-        const int K = 8;
-        if (s == AFSAI_OK) s = E.capture(K, st);
+        // the whole iteration loop is one graph launch: a device-side while
+        // loop over bodies of K iterations, bounded by maxit
+        const int K = 4;
+        const int64_t max_bodies = maxit > 0 ? (static_cast<int64_t>(maxit) + K - 1) / K + 1 : 0;
+        if (s == AFSAI_OK) s = E.capture_loop(K, static_cast<int32_t>(std::min<int64_t>(max_bodies, INT32_MAX)), st);
         int32_t active = nsys;
         int64_t launches = 0;
-        const int64_t max_launches = maxit > 0 ? (static_cast<int64_t>(maxit) + K - 1) / K + 1 : 0;
         if (s == AFSAI_OK) s = E.read_active(st, &active);
-        while (s == AFSAI_OK && active > 0 && launches < max_launches) {
-            s = E.launch_graph(st);
+        if (s == AFSAI_OK && active > 0 && max_bodies > 0) {
+            s = E.arm_loop(st);
+            if (s == AFSAI_OK) s = E.launch_graph(st);
             ++launches;
             if (s == AFSAI_OK) s = E.read_active(st, &active);
+            // launch_graph counted one body; the loop ran loop_bodies - left
+            if (s == AFSAI_OK) count_launches((E.loop_bodies - E.h_counts[2] - 1) * E.per_graph);
         }
         if (s == AFSAI_OK) s = E.finish(st);
         if (s == AFSAI_OK && cudaEventRecord(e2, st) != cudaSuccess) s = fail(AFSAI_ECUDA, "cudaEventRecord");
@@ -717,7 +1012,7 @@ afsai_status batch_solve_impl(int32_t nsys, const afsai_csr* A, const afsai_para
             if (binfo) {
                 binfo->nsys = nsys;
                 binfo->total_rows = ntot;
-                binfo->nnz_G = M->info.nnz_G;
+                binfo->nnz_G = nnz_G;
                 binfo->setup_ms = ms_setup;
                 binfo->solve_ms = ms_solve;
                 binfo->graph_launches = static_cast<int32_t>(launches);
@@ -730,7 +1025,7 @@ afsai_status batch_solve_impl(int32_t nsys, const afsai_csr* A, const afsai_para
     E.release(st);
     vec.release();
     cudaStreamSynchronize(st);
-    afsai_destroy(M);
+    free_buckets(&buckets);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaEventDestroy(e2);

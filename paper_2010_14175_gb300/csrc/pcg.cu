@@ -358,6 +358,7 @@ bool with_mode(int mode, F f) {
         case tiled::kModeSlicedPipeIlv: f(std::integral_constant<int, tiled::kModeSlicedPipeIlv>{}); return true;
         case tiled::kModeSlicedStaged8: f(std::integral_constant<int, tiled::kModeSlicedStaged8>{}); return true;
         case tiled::kModeSlicedStaged16: f(std::integral_constant<int, tiled::kModeSlicedStaged16>{}); return true;
+        case tiled::kModeBalanced: f(std::integral_constant<int, tiled::kModeBalanced>{}); return true;
         default: return false;
     }
 }

@@ -6,12 +6,18 @@
 // right-hand sides; each becomes one system of the batched engine
 // (batch.cu) in a slot with its own vectors.  A server thread runs the step
 // loop:
-//   admit   while the queue head fits (free slots for its right-hand sides,
-//           device-memory budget for its vectors and, if not built yet, its
-//           preconditioner) take it: set-up if needed, allocate vectors,
-//           copy b, initialise only the new systems;
-//   step    one graph launch = K PCG iterations of every running system,
-//           whatever its size and however long it has been running;
+//   admit   queued requests in arrival order while they fit (free slots for
+//           their right-hand sides, device-memory budget for their vectors):
+//           allocate vectors, copy b, initialise only the new systems.  A
+//           request whose matrix has no preconditioner yet hands its
+//           set-up to the set-up thread (its own stream, so the set-up
+//           overlaps the running systems on the GPU) and waits for it;
+//           the requests behind it may be admitted meanwhile;
+//   step    one graph launch: a device-side loop of bodies of K PCG
+//           iterations of every running system, which ends after the body
+//           in which a system finished, when a new request arrives (the
+//           submitting thread raises a flag in mapped host memory that the
+//           loop reads) or after a bounded number of bodies;
 //   retire  systems that converged (or hit maxit) get their true residual,
 //           x goes back to the request's host buffer, the slot and its
 //           memory are freed and the next requests can enter.
@@ -51,6 +57,9 @@ struct ServeMatrix {
     afsai_precond* M = nullptr;  // built at the first request
     int64_t g_bytes = 0;
     int32_t running = 0;         // right-hand sides of this matrix on the GPU
+    bool building = false;       // set-up queued or running on the set-up thread
+    double setup_ms = 0.0;       // duration of its last set-up
+    std::string setup_error;     // message of a failed set-up
     Clock::time_point last_use;
 };
 
@@ -66,6 +75,7 @@ struct ServeRequest {
     std::vector<pcg_info> info;
     Clock::time_point t_submit, t_admit, t_done;
     double setup_ms = 0.0;
+    bool triggered_setup = false;  // its arrival started its matrix's set-up
     std::string error;
 };
 
@@ -86,12 +96,19 @@ struct ServerImpl {
     int64_t budget = 0;
     int32_t max_slots = 0;
     int iters_per_step = 4;
+    int32_t max_bodies = 16;      // bodies of K iterations per step at most
     cudaStream_t st = nullptr;
+    cudaStream_t setup_st = nullptr;
     BatchEngine E;
     std::mutex mu;
     std::condition_variable cv;
+    std::condition_variable setup_cv;
     bool stop = false;
     std::thread th;
+    std::thread setup_th;
+    std::deque<int32_t> setup_queue;
+    int32_t* arrival_flag = nullptr;  // mapped pinned host memory, raised by serve_submit
+    int32_t* arrival_flag_dev = nullptr;
     std::vector<std::unique_ptr<ServeMatrix>> mats;
     std::map<int64_t, ServeRequest> reqs;
     std::deque<int64_t> queue;
@@ -116,18 +133,71 @@ struct ServerImpl {
         sys.assign(max_slots, BSys{});
         std::vector<char> running(max_slots, 0);
         AFSAI_TRY(E.set_tables(sys, running, 0, st));
-        AFSAI_TRY(E.capture(iters_per_step, st));
+        AFSAI_CUDA_TRY(cudaHostAlloc(reinterpret_cast<void**>(&arrival_flag), sizeof(int32_t), cudaHostAllocMapped));
+        *arrival_flag = 0;
+        AFSAI_CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&arrival_flag_dev), arrival_flag, 0));
+        AFSAI_TRY(E.capture_loop(iters_per_step, max_bodies, st, true, arrival_flag_dev));
         return AFSAI_OK;
     }
 
+    // The set-up thread: builds the preconditioners of matrices at their
+    // first request on its own stream.
+    void setup_loop() {
+        cudaSetDevice(device);
+        std::unique_lock<std::mutex> lock(mu);
+        while (!stop) {
+            if (setup_queue.empty()) {
+                setup_cv.wait_for(lock, std::chrono::milliseconds(5));
+                continue;
+            }
+            const int32_t id = setup_queue.front();
+            setup_queue.pop_front();
+            ServeMatrix& m = *mats[id];
+            afsai_csr A{m.n, m.nnz, m.rowptr, m.col, m.val};
+            const afsai_params prm = params;
+            lock.unlock();
+            afsai_precond* M = nullptr;
+            const auto t0 = Clock::now();
+            const afsai_status s = setup_precond(&A, &prm, setup_st, false, &M);
+            const double ms = ms_between(t0, Clock::now());
+            const std::string msg = s == AFSAI_OK ? std::string() : std::string(afsai_last_error());
+            lock.lock();
+            m.building = false;
+            if (s == AFSAI_OK) {
+                m.M = M;
+                m.setup_ms = ms;
+            } else {
+                // the requests waiting for this matrix fail; its reserved memory is returned
+                mem_used -= m.g_bytes;
+                m.g_bytes = 0;
+                m.setup_error = msg;
+                for (auto it = queue.begin(); it != queue.end();) {
+                    ServeRequest& R = reqs[*it];
+                    if (R.matrix == id) {
+                        R.state = Q_FAIL;
+                        R.error = "set-up failed: " + msg;
+                        R.t_done = Clock::now();
+                        it = queue.erase(it);
+                    } else {
+                        ++it;
+                    }
+                }
+            }
+            cv.notify_all();
+        }
+    }
+
     // Frees preconditioners of idle matrices, oldest use first, until
-    // `need` bytes fit the budget.  Caller holds the lock.
-    void evict_for(int64_t need) {
+    // `need` bytes fit the budget; `keep` (the matrix being admitted) is
+    // never a victim.  Caller holds the lock.
+    void evict_for(int64_t need, const ServeMatrix* keep) {
         while (mem_used + need > budget) {
             ServeMatrix* victim = nullptr;
             for (auto& m : mats)
-                if (m->M && m->running == 0 && (!victim || m->last_use < victim->last_use)) victim = m.get();
+                if (m.get() != keep && m->M && m->running == 0 && (!victim || m->last_use < victim->last_use))
+                    victim = m.get();
             if (!victim) return;
+            cudaStreamSynchronize(st);  // no step in flight reads it any more
             afsai_destroy(victim->M);
             victim->M = nullptr;
             mem_used -= victim->g_bytes;
@@ -138,33 +208,36 @@ struct ServerImpl {
     // Admission (caller holds the lock).  Returns true if tables changed.
     bool admit(afsai_status* err) {
         bool changed = false;
-        while (!queue.empty()) {
-            const int64_t t = queue.front();
+        for (auto it = queue.begin(); it != queue.end();) {
+            const int64_t t = *it;
             ServeRequest& R = reqs[t];
             ServeMatrix& m = *mats[R.matrix];
+            if (!m.M) {
+                // the preconditioner is built on the set-up thread; the
+                // request keeps its place and the ones behind it may go first
+                if (!m.building) {
+                    R.triggered_setup = true;
+                    const int64_t need_g = g_estimate(m);
+                    if (mem_used + need_g > budget) evict_for(need_g, &m);
+                    if (mem_used + need_g > budget) break;
+                    m.building = true;
+                    m.g_bytes = need_g;
+                    mem_used += need_g;
+                    setup_queue.push_back(R.matrix);
+                    setup_cv.notify_all();
+                }
+                ++it;
+                continue;
+            }
             int32_t free_slots = 0;
             for (const Slot& s : slots) free_slots += s.used ? 0 : 1;
             if (free_slots < R.nrhs) break;
-            const int64_t need = vec_bytes(m.n) * R.nrhs + (m.M ? 0 : g_estimate(m));
-            if (mem_used + need > budget) evict_for(need);
+            const int64_t need = vec_bytes(m.n) * R.nrhs;
+            if (mem_used + need > budget) evict_for(need, &m);
             if (mem_used + need > budget) break;
-            queue.pop_front();
+            it = queue.erase(it);
             R.t_admit = Clock::now();
-            if (!m.M) {
-                const auto t0 = Clock::now();
-                afsai_csr A{m.n, m.nnz, m.rowptr, m.col, m.val};
-                const afsai_status s = setup_precond(&A, &params, st, false, &m.M);
-                if (s != AFSAI_OK) {
-                    R.state = Q_FAIL;
-                    R.error = afsai_last_error();
-                    R.t_done = Clock::now();
-                    cv.notify_all();
-                    continue;
-                }
-                m.g_bytes = g_estimate(m);
-                mem_used += m.g_bytes;
-                R.setup_ms = ms_between(t0, Clock::now());
-            }
+            if (R.triggered_setup) R.setup_ms = m.setup_ms;
             m.last_use = Clock::now();
             R.state = Q_RUN;
             R.remaining = R.nrhs;
@@ -292,7 +365,10 @@ struct ServerImpl {
                 continue;
             }
             if (err == AFSAI_OK) {
-                err = E.launch_graph(st);
+                // requests queued from here on raise the flag again and end this step
+                *reinterpret_cast<volatile int32_t*>(arrival_flag) = 0;
+                err = E.arm_loop(st);
+                if (err == AFSAI_OK) err = E.launch_graph(st);
                 stats.steps += 1;
             }
             // the lock is released while the GPU works, so callers can submit
@@ -352,14 +428,22 @@ afsai_status serve_create(size_t mem_budget_bytes, int32_t max_slots, const afsa
         delete S;
         return fail(AFSAI_ECUDA, "cudaStreamCreate");
     }
+    if (cudaStreamCreateWithFlags(&I.setup_st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamDestroy(I.st);
+        delete S;
+        return fail(AFSAI_ECUDA, "cudaStreamCreate");
+    }
     const afsai_status s = I.init_engine();
     if (s != AFSAI_OK) {
         I.E.release(I.st);
+        if (I.arrival_flag) cudaFreeHost(I.arrival_flag);
         cudaStreamDestroy(I.st);
+        cudaStreamDestroy(I.setup_st);
         delete S;
         return s;
     }
     I.th = std::thread([&I] { I.loop(); });
+    I.setup_th = std::thread([&I] { I.setup_loop(); });
     *out = S;
     return AFSAI_OK;
 }
@@ -415,6 +499,7 @@ afsai_status serve_submit(afsai_server* S, int32_t matrix_id, const double* b, i
     R.t_submit = Clock::now();
     I.queue.push_back(t);
     I.stats.requests_submitted += 1;
+    if (I.arrival_flag) *reinterpret_cast<volatile int32_t*>(I.arrival_flag) = 1;  // ends the running step
     I.cv.notify_all();
     *ticket = t;
     return AFSAI_OK;
@@ -474,8 +559,11 @@ void serve_destroy(afsai_server* S) {
         I.stop = true;
     }
     I.cv.notify_all();
+    I.setup_cv.notify_all();
     if (I.th.joinable()) I.th.join();
+    if (I.setup_th.joinable()) I.setup_th.join();
     cudaSetDevice(I.device);
+    cudaStreamSynchronize(I.setup_st);
     cudaStreamSynchronize(I.st);
     for (auto& s : I.slots)
         if (s.vec) cudaFreeAsync(s.vec, I.st);
@@ -487,7 +575,9 @@ void serve_destroy(afsai_server* S) {
     }
     I.E.release(I.st);
     cudaStreamSynchronize(I.st);
+    if (I.arrival_flag) cudaFreeHost(I.arrival_flag);
     cudaStreamDestroy(I.st);
+    cudaStreamDestroy(I.setup_st);
     delete S;
 }
 

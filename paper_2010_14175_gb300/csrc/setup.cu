@@ -1127,13 +1127,34 @@ __global__ void __launch_bounds__(256) step_gather(StepArgs a) {
 constexpr int kLaneHT = 64;
 constexpr int kLaneRowMax = 8;
 
-__device__ __forceinline__ bool occ_test(uint64_t occ, uint32_t h) { return (occ >> h) & 1ull; }
+// Occupancy of a lane's table: one bit per slot, in registers.
+template <int HT>
+struct Occ {
+    static constexpr int W = (HT + 63) / 64;
+    uint64_t w[W];
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int k = 0; k < W; ++k) w[k] = 0ull;
+    }
+    static_assert(W <= 2, "at most 128 slots");
+    // selects instead of a dynamic index keep the words in registers
+    __device__ __forceinline__ bool test(uint32_t h) const {
+        const uint64_t x = (W == 2 && (h & 64u)) ? w[W - 1] : w[0];
+        return (x >> (h & 63u)) & 1ull;
+    }
+    __device__ __forceinline__ void set(uint32_t h) {
+        if (W == 2 && (h & 64u))
+            w[W - 1] |= 1ull << (h & 63u);
+        else
+            w[0] |= 1ull << (h & 63u);
+    }
+};
 
 template <int MC, int HT>
 __global__ void __launch_bounds__(128) step_gather_lane(StepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int LOG2 = HT == 32 ? 5 : 6;
-    static_assert((1 << LOG2) == HT && HT <= 64, "table size");
+    constexpr int LOG2 = HT == 32 ? 5 : (HT == 64 ? 6 : 7);
+    static_assert((1 << LOG2) == HT && HT <= 128, "table size");
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int nwb = blockDim.x >> 5;
@@ -1153,7 +1174,8 @@ __global__ void __launch_bounds__(128) step_gather_lane(StepArgs a) {
         for (int t = 0; t < m; ++t) TP(t) = a.P[ii * a.mc + t];
         // ---- Kaporin gradient over j < i (Eq. "grapsi"); row t + 1 of A
         // is loaded while row t is accumulated ----
-        uint64_t occ = 0ull;
+        Occ<HT> occ;
+        occ.clear();
         int nk = 0;
         int32_t c0[kLaneRowMax], c1[kLaneRowMax];
         double v0[kLaneRowMax], v1[kLaneRowMax];
@@ -1179,8 +1201,8 @@ __global__ void __launch_bounds__(128) step_gather_lane(StepArgs a) {
                 if (j < i) {
                     uint32_t h = slot_of(j, LOG2);
                     for (int probe = 0; probe < HT; ++probe) {
-                        if (!occ_test(occ, h)) {
-                            occ |= 1ull << h;
+                        if (!occ.test(h)) {
+                            occ.set(h);
                             TK(h) = j;
                             TV(h) = 0.0;
                             ++nk;
@@ -1208,7 +1230,7 @@ __global__ void __launch_bounds__(128) step_gather_lane(StepArgs a) {
         for (int t = 0; t < m - 1; ++t) {
             const int32_t pj = TP(t);
             uint32_t h = slot_of(pj, LOG2);
-            for (int probe = 0; probe < HT && occ_test(occ, h); ++probe) {
+            for (int probe = 0; probe < HT && occ.test(h); ++probe) {
                 if (TK(h) == pj) {
                     TV(h) = 0.0;
                     break;
@@ -1219,35 +1241,39 @@ __global__ void __launch_bounds__(128) step_gather_lane(StepArgs a) {
         // locality bound (Section 4): candidates outside the allowed stripes
         const StripeBound bd = stripe_bound(a.reach, a.reach_words, a.stripe_magic, a.stripe_shift, i);
         if (bd.row != nullptr) {
-            for (uint64_t mm = occ; mm; mm &= mm - 1) {
-                const uint32_t h = static_cast<uint32_t>(__ffsll(static_cast<long long>(mm)) - 1);
-                if (!bd.allows(TK(h))) TV(h) = 0.0;
-            }
+#pragma unroll
+            for (int wd = 0; wd < Occ<HT>::W; ++wd)
+                for (uint64_t mm = occ.w[wd]; mm; mm &= mm - 1) {
+                    const uint32_t h = 64u * wd + static_cast<uint32_t>(__ffsll(static_cast<long long>(mm)) - 1);
+                    if (!bd.allows(TK(h))) TV(h) = 0.0;
+                }
         }
         // ---- the s (<= 4) largest |gradient|, ties to the smaller column ----
         unsigned long long kb[4] = {0ull, 0ull, 0ull, 0ull};
         int32_t kj[4] = {INT_MAX, INT_MAX, INT_MAX, INT_MAX};
-        for (uint64_t mm = occ; mm; mm &= mm - 1) {
-            const uint32_t h = static_cast<uint32_t>(__ffsll(static_cast<long long>(mm)) - 1);
-            const unsigned long long ab =
-                static_cast<unsigned long long>(__double_as_longlong(TV(h))) & 0x7fffffffffffffffull;
-            if (ab == 0ull || ab > 0x7ff0000000000000ull) continue;  // zero or NaN
-            const int32_t j = TK(h);
-            if (!cand_better(ab, j, kb[3], kj[3])) continue;
-            kb[3] = ab;
-            kj[3] = j;
 #pragma unroll
-            for (int q = 3; q > 0; --q) {
-                if (cand_better(kb[q], kj[q], kb[q - 1], kj[q - 1])) {
-                    const unsigned long long tb = kb[q];
-                    kb[q] = kb[q - 1];
-                    kb[q - 1] = tb;
-                    const int32_t tj = kj[q];
-                    kj[q] = kj[q - 1];
-                    kj[q - 1] = tj;
+        for (int wd = 0; wd < Occ<HT>::W; ++wd)
+            for (uint64_t mm = occ.w[wd]; mm; mm &= mm - 1) {
+                const uint32_t h = 64u * wd + static_cast<uint32_t>(__ffsll(static_cast<long long>(mm)) - 1);
+                const unsigned long long ab =
+                    static_cast<unsigned long long>(__double_as_longlong(TV(h))) & 0x7fffffffffffffffull;
+                if (ab == 0ull || ab > 0x7ff0000000000000ull) continue;  // zero or NaN
+                const int32_t j = TK(h);
+                if (!cand_better(ab, j, kb[3], kj[3])) continue;
+                kb[3] = ab;
+                kj[3] = j;
+#pragma unroll
+                for (int q = 3; q > 0; --q) {
+                    if (cand_better(kb[q], kj[q], kb[q - 1], kj[q - 1])) {
+                        const unsigned long long tb = kb[q];
+                        kb[q] = kb[q - 1];
+                        kb[q - 1] = tb;
+                        const int32_t tj = kj[q];
+                        kj[q] = kj[q - 1];
+                        kj[q - 1] = tj;
+                    }
                 }
             }
-        }
         int npick = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q)
@@ -1979,7 +2005,7 @@ bool lane_gather_applies(int64_t mcap, int32_t s, int32_t max_row_nnz) {
         const char* e = std::getenv("AFSAI_GATHER_LANE");
         return !e || std::atoi(e) != 0;
     }();
-    return on && mcap <= 12 && s <= 4 && max_row_nnz <= kLaneRowMax;
+    return on && mcap <= 20 && s <= 4 && max_row_nnz <= kLaneRowMax;
 }
 
 afsai_status run_stepwise(const SetupArgs& o, int64_t mcap, int ht, int32_t kiter, bool chol32, cudaStream_t st,
@@ -2134,7 +2160,7 @@ int lanes_per_row(int mcap_t, bool chol32) {
 }  // namespace
 
 afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_row_nnz, cudaStream_t st,
-                        afsai_precond* M, bool sliced) {
+                        afsai_precond* M, bool sliced, const SetupTuning* tune) {
     const int32_t n = A->n;
     const int64_t mcap = 1 + static_cast<int64_t>(p->kiter) * p->s;
     if (mcap > 128) return fail(AFSAI_ENOTSUP, "1 + kiter*s must be <= 128");
@@ -2229,7 +2255,20 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
             const char* e = std::getenv("AFSAI_SOLVE_SQRT");
             return e && std::atoi(e) == 1;
         }();
-        if (chol32)
+        // patterns of 13 to 20 entries (kiter 8, s 2 in the uneven batch):
+        // up to ~60 distinct candidates, 128-slot tables, 4 lanes per row
+        const int lpr = tune ? tune->lane_lpr : 0;
+        if (mcap > 12) {
+            if (lpr == 8)
+                AFSAI_TRY(chol32 ? (run_stepwise_lane<20, 8, true, 128>(a, p->kiter, st))
+                                 : (run_stepwise_lane<20, 8, false, 128>(a, p->kiter, st)));
+            else
+                AFSAI_TRY(chol32 ? (run_stepwise_lane<20, 4, true, 128>(a, p->kiter, st))
+                                 : (run_stepwise_lane<20, 4, false, 128>(a, p->kiter, st)));
+        } else if (lpr == 4) {
+            AFSAI_TRY(chol32 ? (run_stepwise_lane<12, 4, true, 64>(a, p->kiter, st))
+                             : (run_stepwise_lane<12, 4, false, 64>(a, p->kiter, st)));
+        } else if (chol32)
             AFSAI_TRY(lane_ht == 32 ? (run_stepwise_lane<12, 2, true, 32>(a, p->kiter, st))
                                     : (run_stepwise_lane<12, 2, true, 64>(a, p->kiter, st)));
         else if (sqrt_int)

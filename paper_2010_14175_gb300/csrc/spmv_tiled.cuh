@@ -561,6 +561,110 @@ __device__ bool spmv_sliced_staged(const SellView& S, const XT* __restrict__ x, 
     return __syncthreads_and(ok_warp) != 0;
 }
 
+// Balanced rows: a warp takes 32 consecutive rows and splits their
+// entries evenly over its lanes (each lane a contiguous run of
+// ceil(T / 32) entries, T the rows' entry count), so every FP64 fma
+// instruction of the warp is full whatever the row lengths (G^T: from 1 to
+// ~40 entries per row, where one lane per row leaves about half the lanes
+// idle).  A row inside one run is the sequential sum of its entries; a row
+// cut by run boundaries is summed from its pieces in lane order by the lane
+// that holds its last entry.  Shared memory per warp: kBalancedWarpBytes.
+constexpr int kModeBalanced = 301;
+
+template <typename ACC>
+struct BalancedWarp {
+    int32_t rp[33];   // row pointers of the warp's rows (rp[nr] = end)
+    int32_t prow[32]; // row continued past the end of each lane's run (-1: none)
+    ACC part[32];     // that row's partial sum over the lane's run
+};
+
+template <typename VT, typename XT, typename ACC, class Epi>
+__device__ __forceinline__ void spmv_balanced(int32_t n, const int32_t* __restrict__ rowptr,
+                                              const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                              const XT* __restrict__ x, Epi& epi) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    BalancedWarp<ACC>& W = reinterpret_cast<BalancedWarp<ACC>*>(smem)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t r0 = w0 * 32; r0 < n; r0 += nw * 32) {
+        const int nr = static_cast<int>(n - r0 < 32 ? n - r0 : 32);
+        const int32_t e_all = __ldg(&rowptr[r0 + nr]);
+        W.rp[lane] = lane < nr ? __ldg(&rowptr[r0 + lane]) : e_all;
+        if (lane == 0) W.rp[32] = e_all;
+        W.prow[lane] = -1;
+        __syncwarp();
+        const int32_t E0 = W.rp[0];
+        const int32_t T = e_all - E0;
+        const int32_t C = (T + 31) >> 5;
+        const int32_t s = E0 + lane * C;
+        const int32_t e_end = s + C < e_all ? s + C : e_all;
+        ACC head = ACC(0);
+        int head_row = -1;
+        if (T == 0) {
+            if (lane < nr) epi.row(r0 + lane, ACC(0));
+        } else if (s < e_end) {
+            // first row of the run: row 0 for lane 0 (empty leading rows
+            // included), else the last row starting at or before s
+            int k = 0;
+            if (lane > 0) {
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (k + step < nr && W.rp[k + step] <= s) k += step;
+            }
+            ACC acc = ACC(0);
+            auto close_row = [&]() {
+                if (W.rp[k] >= s) {
+                    epi.row(r0 + k, acc);  // the whole row lies in this run
+                } else {
+                    head = acc;            // the row began in an earlier run
+                    head_row = k;
+                }
+                ++k;
+                acc = ACC(0);
+            };
+            int32_t e = s;
+            for (; e + 4 <= e_end; e += 4) {
+                int32_t c4[4];
+                VT v4[4];
+                XT x4[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    c4[u] = __ldg(&col[e + u]);
+                    v4[u] = __ldg(&val[e + u]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) x4[u] = __ldg(&x[c4[u]]);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    while (W.rp[k + 1] <= e + u) close_row();
+                    acc = Mul<ACC>::fma_(v4[u], x4[u], acc);
+                }
+            }
+            for (; e < e_end; ++e) {
+                while (W.rp[k + 1] <= e) close_row();
+                acc = Mul<ACC>::fma_(__ldg(&val[e]), __ldg(&x[__ldg(&col[e])]), acc);
+            }
+            // rows that end with this run (and empty rows right after it)
+            while (k < nr && W.rp[k + 1] <= e_end) close_row();
+            if (k < nr) {
+                W.part[lane] = acc;
+                W.prow[lane] = k;
+            }
+        }
+        __syncwarp();
+        if (head_row >= 0) {
+            // pieces of the row from the lane of its first entry onwards
+            const int L0 = (W.rp[head_row] - E0) / C;
+            ACC sum = W.part[L0];
+            for (int L = L0 + 1; L < lane; ++L) sum += W.part[L];
+            sum += head;
+            epi.row(r0 + head_row, sum);
+        }
+        __syncwarp();
+    }
+}
+
 constexpr int kModeSliced = 200;
 constexpr int kModeSlicedPipe = 201;
 constexpr int kModeSlicedPipe8 = 202;
@@ -597,6 +701,9 @@ __device__ __forceinline__ bool spmv_rows(int32_t n, int64_t nnz, const int32_t*
         return spmv_sliced_staged<8, 3, VT, XT, ACC>(sv, x, errflag, epi, wait);
     } else if constexpr (MODE == kModeSlicedStaged16) {
         return spmv_sliced_staged<16, 2, VT, XT, ACC>(sv, x, errflag, epi, wait);
+    } else if constexpr (MODE == kModeBalanced) {
+        spmv_balanced<VT, XT, ACC>(n, rowptr, col, val, x, epi);
+        return true;
     } else if constexpr (MODE > 100) {
         return spmv_tiles<MODE - 100, VT, XT, ACC>(n, nnz, rowptr, col, val, x, cap, errflag, epi, wait);
     } else if constexpr (MODE == 3 || MODE == 6) {

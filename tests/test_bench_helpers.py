@@ -92,3 +92,21 @@ def test_measured_traffic_follows_the_source_digest(tmp_path, monkeypatch):
     f.write_text(json.dumps(rec))
     assert bench.measured_traffic("k", 25) == (None, "kernel changed since the ncu capture")
     assert bench.measured_traffic("absent", 25) == (None, "no ncu record")
+
+
+def test_pcg_kernel_table_bounds():
+    class A:
+        n, nnz = 1000, 7000
+
+    # FP64 G: the G SpMV moves 12 B per entry for one FP64 fma; at the
+    # measured bandwidth and the derived FP64 rate the bytes bind
+    t = bench.pcg_kernel_table(A, 10000, "fp64", [0.1, 0.02, 0.1, 0.1, 0.02])
+    g = [k for k in t if k["key"] == "pcg_G"][0]
+    assert g["bytes"] == 12 * 10000 + 4 * 1001 + 16 * 1000 and g["dfma"] == 10000
+    assert g["bound"] == "hbm"
+    assert g["achieved"] == pytest.approx(g["bytes"] / 1e-4 / 1e9)
+    assert g["frac"] == pytest.approx(g["achieved"] / bench.MEASURED_HBM_GBS)
+    # FP32 G: 8 B per entry, no FP64 fma in the product
+    t32 = bench.pcg_kernel_table(A, 10000, "mixed", [0.1] * 5)
+    g32 = [k for k in t32 if k["key"] == "pcg_G"][0]
+    assert g32["bytes"] == 8 * 10000 + 4 * 1001 + 16 * 1000 and g32["dfma"] == 0

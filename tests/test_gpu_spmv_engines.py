@@ -20,7 +20,7 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-ENGINES = [1, 2, 3, 4, 6, 8, 101, 102, 200, 201, 202, 203, 210, 211]
+ENGINES = [1, 2, 3, 4, 6, 8, 101, 102, 200, 201, 202, 203, 210, 211, 301]
 
 _SCRIPT = r'''
 import sys
@@ -75,12 +75,12 @@ for name, A, kiter, s in cases:
     x = torch.zeros_like(bd)
     info = afsai.pcg_solve(Ad, M, bd, x, rtol=1e-8, maxit=20000)
     assert info["converged"] == 1 and abs(info["iters"] - it_o) <= 1, (name, info["iters"], it_o)
-    assert info["relres_true"] <= 1.05e-8, (name, info["relres_true"])
+    assert info["relres_true"] <= 1e-8, (name, info["relres_true"])
     nnz_g = int(ref.rowptr[-1])
     got = (afsai.spmv_engine(0, A.n, A.nnz), afsai.spmv_engine(1, A.n, nnz_g), afsai.spmv_engine(2, A.n, nnz_g))
     if name == "arrow":
-        assert got[0] < 200, (name, got)  # no sliced copy of A: a CSR engine serves
-    elif mode in (1, 2, 3, 4, 6, 8, 200, 201, 202, 203, 210, 211):
+        assert got[0] < 200 or got[0] == 301, (name, got)  # no sliced copy of A: a CSR engine serves
+    elif mode in (1, 2, 3, 4, 6, 8, 200, 201, 202, 203, 210, 211, 301):
         assert got == (mode, mode, mode), (name, got)
 print("ok")
 '''
