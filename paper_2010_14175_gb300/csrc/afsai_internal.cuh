@@ -200,6 +200,24 @@ inline int ceil_div(int64_t a, int64_t b) { return static_cast<int>((a + b - 1) 
 
 int num_sms();
 
+// Blocks of `kern` (threads, dynamic shared memory) resident on the GPU at
+// once, capped at `blocks`.  The SpMV engines loop grid-stride, so a grid
+// trimmed to this count does the same work; the engine plans count shared
+// memory and threads, not the registers of the kernel that finally runs.
+// A fused kernel a few registers above the plain product would run its
+// last blocks as a second wave (rows of 7 entries: 7 blocks of 256
+// threads per SM at 32 registers, 6 at 34, so every seventh block waits
+// for the others and the product takes twice as long).
+template <typename K>
+int resident_grid(K kern, int blocks, int threads, size_t smem) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess || per_sm <= 0) {
+        cudaGetLastError();
+        return blocks;
+    }
+    return per_sm * num_sms() < blocks ? per_sm * num_sms() : blocks;
+}
+
 // Kernel launch accounting (reported by afsai_kernel_launches()).
 void count_launches(int64_t k);
 int64_t launches_so_far();

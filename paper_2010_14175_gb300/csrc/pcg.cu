@@ -335,9 +335,12 @@ int vec_blocks(int64_t n) {
     return static_cast<int>(std::max<int64_t>(1, std::min(need, cap)));
 }
 
+// Shared-memory limit of a product kernel, and its grid trimmed to one
+// resident wave of that kernel.
 template <typename K>
-void set_smem_attr(K kern, size_t smem) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+void fit(K kern, SpmvMode& m) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    m.blocks = resident_grid(kern, m.blocks, m.threads, m.smem);
 }
 
 // Calls f(std::integral_constant<int, MODE>) for the engine mode.
@@ -352,6 +355,7 @@ bool with_mode(int mode, F f) {
         case 6: f(std::integral_constant<int, 6>{}); return true;
         case 101: f(std::integral_constant<int, 101>{}); return true;
         case 102: f(std::integral_constant<int, 102>{}); return true;
+        case 103: f(std::integral_constant<int, 103>{}); return true;
         case tiled::kModeSliced: f(std::integral_constant<int, tiled::kModeSliced>{}); return true;
         case tiled::kModeSlicedPipe: f(std::integral_constant<int, tiled::kModeSlicedPipe>{}); return true;
         case tiled::kModeSlicedPipe8: f(std::integral_constant<int, tiled::kModeSlicedPipe8>{}); return true;
@@ -398,24 +402,28 @@ struct Launcher {
             AFSAI_TRY(spmv_mode_for(ROLE_G, M->G, st, &mg));
             AFSAI_TRY(spmv_mode_for(ROLE_GT, M->Gt, st, &mt));
         }
-        with_mode(ma.mode, [&](auto Mc) { set_smem_attr(k_spmv_A_dot<decltype(Mc)::value>, 200u * 1024u); });
+        with_mode(ma.mode, [&](auto Mc) { fit(k_spmv_A_dot<decltype(Mc)::value>, ma); });
         if (M) {
             const int vt = M->G.vtype;
+            const bool a64 = acc64();
             with_mode(mg.mode, [&](auto Mc) {
                 constexpr int MD = decltype(Mc)::value;
-                if (vt == VAL_F64) set_smem_attr(k_spmv_G<MD, double, double>, 200u * 1024u);
-                if (vt == VAL_F32) set_smem_attr(k_spmv_G<MD, float, float>, 200u * 1024u);
-                if (vt == VAL_BF16) set_smem_attr(k_spmv_G<MD, __nv_bfloat16, float>, 200u * 1024u);
-                if (vt == VAL_F32) set_smem_attr(k_spmv_G<MD, float, double>, 200u * 1024u);
-                if (vt == VAL_BF16) set_smem_attr(k_spmv_G<MD, __nv_bfloat16, double>, 200u * 1024u);
+                if (vt == VAL_F64)
+                    fit(k_spmv_G<MD, double, double>, mg);
+                else if (vt == VAL_F32)
+                    a64 ? fit(k_spmv_G<MD, float, double>, mg) : fit(k_spmv_G<MD, float, float>, mg);
+                else
+                    a64 ? fit(k_spmv_G<MD, __nv_bfloat16, double>, mg) : fit(k_spmv_G<MD, __nv_bfloat16, float>, mg);
             });
             with_mode(mt.mode, [&](auto Mc) {
                 constexpr int MD = decltype(Mc)::value;
-                if (vt == VAL_F64) set_smem_attr(k_spmv_Gt_dot<MD, double, double>, 200u * 1024u);
-                if (vt == VAL_F32) set_smem_attr(k_spmv_Gt_dot<MD, float, float>, 200u * 1024u);
-                if (vt == VAL_BF16) set_smem_attr(k_spmv_Gt_dot<MD, __nv_bfloat16, float>, 200u * 1024u);
-                if (vt == VAL_F32) set_smem_attr(k_spmv_Gt_dot<MD, float, double>, 200u * 1024u);
-                if (vt == VAL_BF16) set_smem_attr(k_spmv_Gt_dot<MD, __nv_bfloat16, double>, 200u * 1024u);
+                if (vt == VAL_F64)
+                    fit(k_spmv_Gt_dot<MD, double, double>, mt);
+                else if (vt == VAL_F32)
+                    a64 ? fit(k_spmv_Gt_dot<MD, float, double>, mt) : fit(k_spmv_Gt_dot<MD, float, float>, mt);
+                else
+                    a64 ? fit(k_spmv_Gt_dot<MD, __nv_bfloat16, double>, mt)
+                        : fit(k_spmv_Gt_dot<MD, __nv_bfloat16, float>, mt);
             });
         }
         return AFSAI_OK;

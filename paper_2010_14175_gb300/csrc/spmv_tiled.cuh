@@ -175,8 +175,114 @@ __device__ __forceinline__ void tile_rows(int64_t r0, int64_t r1, const int32_t*
     if (part == 0 && i < r1) epi.row(i, acc);
 }
 
+// Balanced variant of the tile's row loop (engine 103): the tile's entries
+// are split evenly over the block's threads (each a contiguous run of
+// C = ceil(T / threads) entries, T the tile's entry count), so every FP64
+// fma instruction of the products is full whatever the row lengths (G^T
+// rows: 1 to ~40 entries; one thread per row leaves about half of each
+// warp idle in the FP64 pipe, the binding unit).  A run's thread only
+// records sums in shared memory (no FP64 work in its divergent row-end
+// branches): res[j] for a row j that lies inside its run, head[t] for the
+// piece of a row begun in an earlier run, part[t] for the piece of a row
+// that continues past the run.  Then thread j finishes row j with every
+// lane active: res[j], or part over the runs the row starts in and
+// crosses, then head of the run it ends in; the epilogue (store, fused
+// dot product) runs once per row in row order.  Work area in shared
+// memory after the stage: kBalancedTileBytes.
+template <typename ACC>
+struct BalancedTile {
+    int32_t rp[257];  // row pointers of the tile's rows (blockDim.x <= 256)
+    ACC res[256];     // sums of rows inside one run
+    ACC part[256];    // each run's piece of the row continuing past its end
+    ACC head[256];    // each run's piece of a row begun in an earlier run
+};
+constexpr size_t kBalancedTileBytes = sizeof(BalancedTile<double>);
+
+template <typename VT, typename XT, typename ACC, class Epi>
+__device__ __forceinline__ void tile_rows_balanced(int64_t r0, int64_t r1, const int32_t* __restrict__ rowptr,
+                                                   const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                                   const XT* __restrict__ x, const int32_t* scol, const VT* sval,
+                                                   int64_t c_lo, int64_t v_lo, bool staged, BalancedTile<ACC>& B,
+                                                   Epi& epi) {
+    const int t = threadIdx.x, nt = blockDim.x;
+    const int nr = static_cast<int>(r1 - r0);
+    for (int k = t; k <= nr; k += nt) B.rp[k] = rowptr[r0 + k];
+    __syncthreads();
+    const int32_t e0 = B.rp[0], e1 = B.rp[nr];
+    const int32_t T = e1 - e0;
+    const int32_t* __restrict__ cs = staged ? scol - c_lo : col;
+    const VT* __restrict__ vs = staged ? sval - v_lo : val;
+    const int32_t C = T > 0 ? (T + nt - 1) / nt : 1;
+    const int32_t s = e0 + t * C;
+    const int32_t e_end = s + C < e1 ? s + C : e1;
+    if (s < e_end) {
+        // the row holding entry s: the last row starting at or before s
+        int k = 0, hi = nr - 1;
+        while (k < hi) {
+            const int mid = (k + hi + 1) >> 1;
+            if (B.rp[mid] <= s)
+                k = mid;
+            else
+                hi = mid - 1;
+        }
+        ACC acc = ACC(0);
+        auto close_row = [&]() {
+            if (B.rp[k] >= s)
+                B.res[k] = acc;  // the whole row lies in this run
+            else
+                B.head[t] = acc;  // the row began in an earlier run
+            ++k;
+            acc = ACC(0);
+        };
+        int32_t e = s;
+        for (; e + 4 <= e_end; e += 4) {
+            int32_t c4[4];
+            VT v4[4];
+            XT x4[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                c4[u] = cs[e + u];
+                v4[u] = vs[e + u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x4[u] = __ldg(&x[c4[u]]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                while (B.rp[k + 1] <= e + u) close_row();
+                acc = Mul<ACC>::fma_(v4[u], x4[u], acc);
+            }
+        }
+        for (; e < e_end; ++e) {
+            while (B.rp[k + 1] <= e) close_row();
+            acc = Mul<ACC>::fma_(vs[e], __ldg(&x[cs[e]]), acc);
+        }
+        // the row of the last entry: it ends with the run or continues
+        if (B.rp[k + 1] <= e_end)
+            close_row();
+        else
+            B.part[t] = acc;
+    }
+    __syncthreads();
+    if (t < nr) {
+        const int32_t b = B.rp[t] - e0, e = B.rp[t + 1] - e0;
+        ACC sum = ACC(0);
+        if (e > b) {
+            const int L0 = b / C, L1 = (e - 1) / C;
+            if (L0 == L1) {
+                sum = B.res[t];
+            } else {
+                sum = B.part[L0];
+                for (int L = L0 + 1; L < L1; ++L) sum += B.part[L];
+                sum += B.head[L1];
+            }
+        }
+        epi.row(r0 + t, sum);
+    }
+}
+
 // The tile loop.  Returns false if a bounded wait expired (error flag set).
-template <int TPR, typename VT, typename XT, typename ACC, class Epi>
+// BAL: the balanced row loop (tile_rows_balanced; TPR must be 1).
+template <int TPR, typename VT, typename XT, typename ACC, class Epi, bool BAL = false>
 __device__ bool spmv_tiles(int32_t n, int64_t nnz, const int32_t* __restrict__ rowptr,
                            const int32_t* __restrict__ col, const VT* __restrict__ val, const XT* __restrict__ x,
                            int cap, int32_t* errflag, Epi& epi, long long wait) {
@@ -184,6 +290,7 @@ __device__ bool spmv_tiles(int32_t n, int64_t nnz, const int32_t* __restrict__ r
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     int32_t* scol = reinterpret_cast<int32_t*>(smem + 128);
     VT* sval = reinterpret_cast<VT*>(smem + 128 + stage_col_bytes<VT>(cap));
+    BalancedTile<ACC>& B = *reinterpret_cast<BalancedTile<ACC>*>(smem + stage_bytes<VT>(cap));
     const int rows_per_tile = blockDim.x / TPR;
     const int64_t ntiles = (static_cast<int64_t>(n) + rows_per_tile - 1) / rows_per_tile;
     constexpr int VPER = 16 / sizeof(VT);  // values per 16 bytes
@@ -229,9 +336,15 @@ __device__ bool spmv_tiles(int32_t n, int64_t nnz, const int32_t* __restrict__ r
                 return false;
             }
             phase ^= 1u;
-            tile_rows<TPR, VT, XT, ACC>(r0, r1, rowptr, col, val, x, scol, sval, c_lo, v_lo, true, epi);
+            if constexpr (BAL)
+                tile_rows_balanced<VT, XT, ACC>(r0, r1, rowptr, col, val, x, scol, sval, c_lo, v_lo, true, B, epi);
+            else
+                tile_rows<TPR, VT, XT, ACC>(r0, r1, rowptr, col, val, x, scol, sval, c_lo, v_lo, true, epi);
         } else {
-            tile_rows<TPR, VT, XT, ACC>(r0, r1, rowptr, col, val, x, scol, sval, c_lo, v_lo, false, epi);
+            if constexpr (BAL)
+                tile_rows_balanced<VT, XT, ACC>(r0, r1, rowptr, col, val, x, scol, sval, c_lo, v_lo, false, B, epi);
+            else
+                tile_rows<TPR, VT, XT, ACC>(r0, r1, rowptr, col, val, x, scol, sval, c_lo, v_lo, false, epi);
         }
         __syncthreads();  // the stage is reused by the next tile
     }
@@ -675,7 +788,8 @@ constexpr int kStagedWarps = 4;           // warps per block of the staged engin
 
 // SpMV row engine.  MODE 1, 2, 4, 8: strided with MODE lanes per row;
 // MODE 3, 6: grouped with MODE lanes per row; MODE 101, 102: TMA-staged
-// tiles with MODE - 100 threads per row; MODE 200 - 203: the sliced copy,
+// tiles with MODE - 100 threads per row; MODE 103: TMA-staged tiles with the
+// balanced row loop (tile_rows_balanced); MODE 200 - 203: the sliced copy,
 // one lane per row (201, 202 software-pipelined by 4 and 8 entries, 203 as
 // 201 with the windows interleaved);
 // MODE 210, 211: the sliced copy staged through shared memory by bulk
@@ -704,6 +818,8 @@ __device__ __forceinline__ bool spmv_rows(int32_t n, int64_t nnz, const int32_t*
     } else if constexpr (MODE == kModeBalanced) {
         spmv_balanced<VT, XT, ACC>(n, rowptr, col, val, x, epi);
         return true;
+    } else if constexpr (MODE == 103) {
+        return spmv_tiles<1, VT, XT, ACC, Epi, true>(n, nnz, rowptr, col, val, x, cap, errflag, epi, wait);
     } else if constexpr (MODE > 100) {
         return spmv_tiles<MODE - 100, VT, XT, ACC>(n, nnz, rowptr, col, val, x, cap, errflag, epi, wait);
     } else if constexpr (MODE == 3 || MODE == 6) {
@@ -756,6 +872,6 @@ struct TiledPlan {
 
 // Plans a tiled SpMV for a CSR with the given shape and value size.
 TiledPlan plan_tiled(int32_t n, int64_t nnz, int32_t max_row, size_t val_size, const void* col, const void* val,
-                     int tpr = 0);
+                     int tpr = 0, size_t extra_smem = 0);
 
 }  // namespace afsai

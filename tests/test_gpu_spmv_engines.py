@@ -20,7 +20,7 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-ENGINES = [1, 2, 3, 4, 6, 8, 101, 102, 200, 201, 202, 203, 210, 211, 301]
+ENGINES = [1, 2, 3, 4, 6, 8, 101, 102, 103, 200, 201, 202, 203, 210, 211, 301]
 
 _SCRIPT = r'''
 import sys
@@ -80,7 +80,7 @@ for name, A, kiter, s in cases:
     got = (afsai.spmv_engine(0, A.n, A.nnz), afsai.spmv_engine(1, A.n, nnz_g), afsai.spmv_engine(2, A.n, nnz_g))
     if name == "arrow":
         assert got[0] < 200 or got[0] == 301, (name, got)  # no sliced copy of A: a CSR engine serves
-    elif mode in (1, 2, 3, 4, 6, 8, 200, 201, 202, 203, 210, 211, 301):
+    elif mode in (1, 2, 3, 4, 6, 8, 103, 200, 201, 202, 203, 210, 211, 301):
         assert got == (mode, mode, mode), (name, got)
 print("ok")
 '''
