@@ -395,12 +395,88 @@ struct Launcher {
         if (marks) cudaEventRecordWithFlags(marks[k], st, cudaEventRecordExternal);
     }
 
-    // engine choice and shared-memory limits, before any stream capture
+    // fused product kernels launched with engine m0 for the engine timing
+    // (on scratch scalars ts; y = C x; x_float: t is FP32)
+    afsai_status tune_A(const SpmvMode& m0, const void* x, void* y, cudaStream_t s2, Scalars* ts) {
+        SpmvMode m = m0;
+        const auto* v = static_cast<const double*>(A->val);
+        if (!with_mode(m.mode, [&](auto Mc) {
+                constexpr int MD = decltype(Mc)::value;
+                fit(k_spmv_A_dot<MD>, m);
+                k_spmv_A_dot<MD><<<m.blocks, m.threads, m.smem, s2>>>(
+                    A->n, A->nnz, A->rowptr, A->col, v, static_cast<const double*>(x), static_cast<double*>(y), ts,
+                    partials, m.cap, tiled::sell_view(A->sell), tiled::kWaitCycles);
+            }))
+            return fail(AFSAI_EINVAL, "unknown SpMV mode");
+        AFSAI_CUDA_TRY(cudaGetLastError());
+        return AFSAI_OK;
+    }
+    template <typename VT, typename ACC>
+    afsai_status tune_G(const SpmvMode& m0, const void* x, void* y, cudaStream_t s2, Scalars* ts) {
+        SpmvMode m = m0;
+        const CsrDev& G = M->G;
+        if (!with_mode(m.mode, [&](auto Mc) {
+                constexpr int MD = decltype(Mc)::value;
+                fit(k_spmv_G<MD, VT, ACC>, m);
+                k_spmv_G<MD, VT, ACC><<<m.blocks, m.threads, m.smem, s2>>>(
+                    G.n, G.nnz, G.rowptr, G.col, static_cast<const VT*>(G.val), static_cast<const double*>(x),
+                    static_cast<ACC*>(y), ts, m.cap, 1, tiled::sell_view(G.sell), tiled::kWaitCycles);
+            }))
+            return fail(AFSAI_EINVAL, "unknown SpMV mode");
+        AFSAI_CUDA_TRY(cudaGetLastError());
+        return AFSAI_OK;
+    }
+    template <typename VT, typename ACC>
+    afsai_status tune_Gt(const SpmvMode& m0, const void* x, void* y, cudaStream_t s2, Scalars* ts) {
+        SpmvMode m = m0;
+        const CsrDev& Gt = M->Gt;
+        if (!with_mode(m.mode, [&](auto Mc) {
+                constexpr int MD = decltype(Mc)::value;
+                fit(k_spmv_Gt_dot<MD, VT, ACC>, m);
+                k_spmv_Gt_dot<MD, VT, ACC><<<m.blocks, m.threads, m.smem, s2>>>(
+                    Gt.n, Gt.nnz, Gt.rowptr, Gt.col, static_cast<const VT*>(Gt.val), static_cast<const ACC*>(x), r,
+                    static_cast<double*>(y), ts, partials, m.cap, 1, tiled::sell_view(Gt.sell), tiled::kWaitCycles);
+            }))
+            return fail(AFSAI_EINVAL, "unknown SpMV mode");
+        AFSAI_CUDA_TRY(cudaGetLastError());
+        return AFSAI_OK;
+    }
+    template <typename VT, typename ACC>
+    afsai_status plan_G(Scalars* ts) {
+        RoleLaunch lg, lt;
+        lg.launch = [&](const SpmvMode& m, const void* x, void* y, cudaStream_t s2) {
+            return tune_G<VT, ACC>(m, x, y, s2, ts);
+        };
+        lt.x_float = sizeof(ACC) == sizeof(float);
+        lt.launch = [&](const SpmvMode& m, const void* x, void* y, cudaStream_t s2) {
+            return tune_Gt<VT, ACC>(m, x, y, s2, ts);
+        };
+        AFSAI_TRY(spmv_mode_for(ROLE_G, M->G, st, &mg, true, &lg));
+        return spmv_mode_for(ROLE_GT, M->Gt, st, &mt, true, &lt);
+    }
+
+    // engine choice (timed on the fused kernels of the solve) and
+    // shared-memory limits, before any stream capture
     afsai_status plan() {
-        AFSAI_TRY(spmv_mode_for(ROLE_A, *A, st, &ma));
+        DevBuf<Scalars> ts;
+        AFSAI_TRY(ts.alloc(1, st));
+        AFSAI_CUDA_TRY(cudaMemsetAsync(ts.p, 0, sizeof(Scalars), st));
+        // r (set by the solve's first kernel) serves the timed dot products
+        fill_tune_vector(r, n, false, st);
+        RoleLaunch la;
+        la.launch = [&](const SpmvMode& m, const void* x, void* y, cudaStream_t s2) {
+            return tune_A(m, x, y, s2, ts.p);
+        };
+        AFSAI_TRY(spmv_mode_for(ROLE_A, *A, st, &ma, true, &la));
         if (M) {
-            AFSAI_TRY(spmv_mode_for(ROLE_G, M->G, st, &mg));
-            AFSAI_TRY(spmv_mode_for(ROLE_GT, M->Gt, st, &mt));
+            const int vt = M->G.vtype;
+            if (vt == VAL_F64)
+                AFSAI_TRY((plan_G<double, double>(ts.p)));
+            else if (vt == VAL_F32)
+                AFSAI_TRY((acc64() ? plan_G<float, double>(ts.p) : plan_G<float, float>(ts.p)));
+            else
+                AFSAI_TRY((acc64() ? plan_G<__nv_bfloat16, double>(ts.p)
+                                   : plan_G<__nv_bfloat16, float>(ts.p)));
         }
         with_mode(ma.mode, [&](auto Mc) { fit(k_spmv_A_dot<decltype(Mc)::value>, ma); });
         if (M) {

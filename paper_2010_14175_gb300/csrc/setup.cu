@@ -900,7 +900,53 @@ struct StepArgs {
     int32_t reach_words;
     int32_t stripe_shift;
     uint64_t stripe_magic;
+    // rows still active after the previous step: list[0 .. *count) (null
+    // before the first step)
+    const int32_t* list;
+    const int32_t* count;
 };
+
+// The rows a step's kernels visit: the active list once at most 3/4 of the
+// rows remain, else every row (skipping the finished ones).  The list adds
+// a dependent load to each row's chain of loads and gives up the row
+// order; on the 7-point diffusion problem (78-100% of the rows active at
+// every step) visiting every row measured faster.
+struct StepRows {
+    const int32_t* list;
+    int64_t count;
+    __device__ __forceinline__ int64_t row(int64_t q) const { return list ? list[q] : q; }
+};
+__device__ __forceinline__ StepRows step_rows(const StepArgs& a) {
+    if (a.list) {
+        const int64_t c = *a.count;
+        if (4 * c <= 3 * static_cast<int64_t>(a.n)) return StepRows{a.list, c};
+    }
+    return StepRows{nullptr, a.n};
+}
+
+// The rows of `in` (every row when `in` is null) that are still active
+// after a step's solve, appended to `out` (*out_count zeroed before).  Each
+// warp keeps the order of its 32 entries; warps append in any order, which
+// changes no result (rows are independent) and keeps runs of neighbouring
+// rows together for the gathers from A.
+__global__ void step_compact(int32_t n, const int32_t* __restrict__ in, const int32_t* __restrict__ in_count,
+                             const int32_t* __restrict__ st, int32_t* __restrict__ out, int32_t* out_count) {
+    const int64_t cnt = in ? *in_count : n;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t w = w0; w * 32 < cnt; w += nw) {
+        const int64_t q = w * 32 + lane;
+        const int32_t i = q < cnt ? (in ? in[q] : static_cast<int32_t>(q)) : -1;
+        const bool keep = i >= 0 && st[i] == kStActive;
+        const unsigned mask = __ballot_sync(0xffffffffu, keep);
+        if (mask == 0u) continue;
+        int32_t base = 0;
+        if (lane == 0) base = atomicAdd(out_count, __popc(mask));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (keep) out[base + __popc(mask & ((1u << lane) - 1u))] = i;
+    }
+}
 
 __global__ void step_init(StepArgs a) {
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < a.n;
@@ -967,7 +1013,9 @@ __global__ void __launch_bounds__(256) step_gather(StepArgs a) {
     static_assert((1 << log2) == HT, "table size");
     const int64_t gw = static_cast<int64_t>(blockIdx.x) * (blockDim.x / GL) + group;
     const int64_t nw = static_cast<int64_t>(gridDim.x) * (blockDim.x / GL);
-    for (int64_t ii = gw; ii < a.n; ii += nw) {
+    const StepRows rows = step_rows(a);
+    for (int64_t q = gw; q < rows.count; q += nw) {
+        const int64_t ii = rows.row(q);
         if (a.st[ii] != kStActive) continue;
         const int32_t i = static_cast<int32_t>(ii);
         int m = a.m[i];
@@ -1164,11 +1212,13 @@ __global__ void __launch_bounds__(128) step_gather_lane(StepArgs a) {
 #define TV(h) sv[(h) * 32 + lane]
 #define TK(h) sk[(h) * 32 + lane]
 #define TP(t) sk[(HT + (t)) * 32 + lane]
-    const int64_t ngroups = (static_cast<int64_t>(a.n) + 31) / 32;
+    const StepRows rows = step_rows(a);
+    const int64_t ngroups = (rows.count + 31) / 32;
     for (int64_t grp = static_cast<int64_t>(blockIdx.x) * nwb + warp; grp < ngroups;
          grp += static_cast<int64_t>(gridDim.x) * nwb) {
-        const int64_t ii = grp * 32 + lane;
-        if (ii >= a.n || a.st[ii] != kStActive) continue;
+        if (grp * 32 + lane >= rows.count) continue;
+        const int64_t ii = rows.row(grp * 32 + lane);
+        if (a.st[ii] != kStActive) continue;
         const int32_t i = static_cast<int32_t>(ii);
         const int m = a.m[ii];
         for (int t = 0; t < m; ++t) TP(t) = a.P[ii * a.mc + t];
@@ -1365,11 +1415,13 @@ __global__ void __launch_bounds__(64) step_solve(StepArgs a) {
 #define MS(e) Ms[(e) * 32 + lane]
 #define GS(e) gs[(e) * 32 + lane]
 #define VS(e) vs[(e) * 32 + lane]
-    const int64_t ngroups = (static_cast<int64_t>(a.n) + 31) / 32;
+    const StepRows rows = step_rows(a);
+    const int64_t ngroups = (rows.count + 31) / 32;
     for (int64_t grp = static_cast<int64_t>(blockIdx.x) * nwb + warp; grp < ngroups;
          grp += static_cast<int64_t>(gridDim.x) * nwb) {
-        const int64_t ii = grp * 32 + lane;
-        if (ii >= a.n || a.st[ii] != kStSolve) continue;
+        if (grp * 32 + lane >= rows.count) continue;
+        const int64_t ii = rows.row(grp * 32 + lane);
+        if (a.st[ii] != kStSolve) continue;
         const int m = a.m[ii];
         const int tm = tri(m);
         for (int t = 0; t < tm; ++t) MS(t) = a.M[ii * a.tmc + t];
@@ -1465,8 +1517,9 @@ __global__ void __launch_bounds__(128) step_solve_wide(StepArgs a) {
     double* g = M + TMC;           // this row's solution
     uint64_t* V = reinterpret_cast<uint64_t*>(g + MC);  // prepared pivot reciprocals
     const int64_t nrw = static_cast<int64_t>(gridDim.x) * nwb * RPW;
-    for (int64_t r0 = (static_cast<int64_t>(blockIdx.x) * nwb + warp) * RPW; r0 < a.n; r0 += nrw) {
-        const int64_t ii = r0 + grp;
+    const StepRows rows = step_rows(a);
+    for (int64_t r0 = (static_cast<int64_t>(blockIdx.x) * nwb + warp) * RPW; r0 < rows.count; r0 += nrw) {
+        const int64_t ii = r0 + grp < rows.count ? rows.row(r0 + grp) : a.n;
         const bool row = ii < a.n && a.st[ii] == kStSolve;
         const int m = row ? a.m[ii] : 0;
         if constexpr (GATHER) {
@@ -1481,9 +1534,10 @@ __global__ void __launch_bounds__(128) step_solve_wide(StepArgs a) {
             // load the warp's triangles, one row at a time with all lanes
             for (int q = 0; q < RPW; ++q) {
                 const int mq = __shfl_sync(0xffffffffu, m, q * LPR);
+                const int64_t iq = __shfl_sync(0xffffffffu, ii, q * LPR);
                 const int tq = tri(mq);
                 double* Mq = wbase + q * RS;
-                for (int t = lane; t < tq; t += 32) Mq[t] = a.M[(r0 + q) * a.tmc + t];
+                for (int t = lane; t < tq; t += 32) Mq[t] = a.M[iq * a.tmc + t];
             }
         }
         int mmax = m;
@@ -1591,8 +1645,9 @@ __global__ void __launch_bounds__(128) step_solve_wide32(StepArgs a) {
     float* L = reinterpret_cast<float*>(reinterpret_cast<double*>(wbase + grp * kRowBytes) + RSD);
     float* x = L + TMC;
     const int64_t nrw = static_cast<int64_t>(gridDim.x) * nwb * RPW;
-    for (int64_t r0 = (static_cast<int64_t>(blockIdx.x) * nwb + warp) * RPW; r0 < a.n; r0 += nrw) {
-        const int64_t ii = r0 + grp;
+    const StepRows rows = step_rows(a);
+    for (int64_t r0 = (static_cast<int64_t>(blockIdx.x) * nwb + warp) * RPW; r0 < rows.count; r0 += nrw) {
+        const int64_t ii = r0 + grp < rows.count ? rows.row(r0 + grp) : a.n;
         const bool row = ii < a.n && a.st[ii] == kStSolve;
         const int m = row ? a.m[ii] : 0;
         if constexpr (GATHER) {
@@ -1613,11 +1668,12 @@ __global__ void __launch_bounds__(128) step_solve_wide32(StepArgs a) {
         } else {
             for (int q = 0; q < RPW; ++q) {
                 const int mq = __shfl_sync(0xffffffffu, m, q * LPR);
+                const int64_t iq = __shfl_sync(0xffffffffu, ii, q * LPR);
                 const int tq = tri(mq);
                 double* Mq = reinterpret_cast<double*>(wbase + q * kRowBytes);
                 float* Lq = reinterpret_cast<float*>(Mq + RSD);
                 for (int t = lane; t < tq; t += 32) {
-                    const double v = a.M[(r0 + q) * a.tmc + t];
+                    const double v = a.M[iq * a.tmc + t];
                     Mq[t] = v;
                     Lq[t] = static_cast<float>(v);
                 }
@@ -1775,6 +1831,21 @@ __global__ void k_setup_diagonal(SetupArgs o) {
     }
 }
 
+// After step k's solve: the rows still active become the work list of step
+// k + 1 (two list buffers of n rows used in turn, counts[2]), so the later
+// steps' kernels spend no lanes on finished rows.
+afsai_status next_active_list(StepArgs& a, int32_t* lists, int32_t* counts, int32_t k, int blocks, cudaStream_t st) {
+    int32_t* out = lists + static_cast<size_t>(k & 1) * static_cast<size_t>(a.n);
+    int32_t* out_count = counts + (k & 1);
+    AFSAI_CUDA_TRY(cudaMemsetAsync(out_count, 0, sizeof(int32_t), st));
+    step_compact<<<blocks, 256, 0, st>>>(a.n, a.list, a.count, a.st, out, out_count);
+    AFSAI_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    a.list = out;
+    a.count = out_count;
+    return AFSAI_OK;
+}
+
 // LPR = 0: lane-per-row solve kernel (step_solve); LPR > 0: step_solve_wide
 // with LPR lanes per row (FP64 only).  INC: incremental gather.
 template <int MC, int HT, bool CHOL32, bool INC = false, int LPR = 0, int GGL = 32>
@@ -1861,11 +1932,17 @@ afsai_status run_stepwise_t(const SetupArgs& o, int32_t kiter, cudaStream_t st) 
     if (per_sm_s < 1 || per_sm_g < 1) return fail(AFSAI_ENOTSUP, "stepwise set-up does not fit in shared memory");
     const int rows_per_warp_s = LPR > 0 ? 32 / (LPR > 0 ? LPR : 1) : 32;
     const int blocks_s = std::max(1, std::min(per_sm_s * num_sms(), ceil_div(ceil_div(n, rows_per_warp_s), wpb)));
+    DevBuf<int32_t> lists, counts;
+    if (kiter > 1) {
+        AFSAI_TRY(lists.alloc(2 * static_cast<size_t>(n), st));
+        AFSAI_TRY(counts.alloc(2, st));
+    }
     for (int32_t k = 1; k <= kiter; ++k) {
         kg<<<blocks_g, 256, smem_g, st>>>(a);
         ks<<<blocks_s, 32 * wpb, smem_s, st>>>(a);
         AFSAI_CUDA_TRY(cudaGetLastError());
         count_launches(2);
+        if (k < kiter) AFSAI_TRY(next_active_list(a, lists.p, counts.p, k, vec_blocks, st));
     }
     step_finish<<<vec_blocks, 256, 0, st>>>(a, o);
     AFSAI_CUDA_TRY(cudaGetLastError());
@@ -1957,11 +2034,17 @@ afsai_status run_stepwise_lane(const SetupArgs& o, int32_t kiter, cudaStream_t s
     if (per_sm_s < 1 || per_sm_g < 1) return fail(AFSAI_ENOTSUP, "stepwise set-up does not fit in shared memory");
     const int blocks_g = std::max(1, std::min(per_sm_g * num_sms(), ceil_div(ceil_div(n, 32), wpb_g)));
     const int blocks_s = std::max(1, std::min(per_sm_s * num_sms(), ceil_div(ceil_div(n, RPW), wpb_s)));
+    DevBuf<int32_t> lists, counts;
+    if (kiter > 1) {
+        AFSAI_TRY(lists.alloc(2 * static_cast<size_t>(n), st));
+        AFSAI_TRY(counts.alloc(2, st));
+    }
     for (int32_t k = 1; k <= kiter; ++k) {
         kg<<<blocks_g, 32 * wpb_g, smem_g, st>>>(a);
         ks<<<blocks_s, 32 * wpb_s, smem_s, st>>>(a);
         AFSAI_CUDA_TRY(cudaGetLastError());
         count_launches(2);
+        if (k < kiter) AFSAI_TRY(next_active_list(a, lists.p, counts.p, k, vec_blocks, st));
     }
     step_finish<<<vec_blocks, 256, 0, st>>>(a, o);
     AFSAI_CUDA_TRY(cudaGetLastError());

@@ -333,8 +333,9 @@ TiledPlan plan_tiled(int32_t n, int64_t nnz, int32_t max_row, size_t val_size, c
 
 namespace {
 
-// x_i = +-(1 + f_i), f_i a pseudo-random fraction of 52 bits (splitmix64 of i).
-__global__ void k_tune_vector(int32_t n, double* __restrict__ x) {
+// x_i = +-(1 + f_i), f_i a pseudo-random fraction of 52 bits (splitmix64 of
+// i), stored as doubles or rounded to floats.
+__global__ void k_tune_vector(int32_t n, void* __restrict__ x, bool as_float) {
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         uint64_t z = static_cast<uint64_t>(i) + 0x9E3779B97F4A7C15ull;
@@ -342,7 +343,11 @@ __global__ void k_tune_vector(int32_t n, double* __restrict__ x) {
         z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
         z ^= z >> 31;
         const uint64_t bits = (0x3FFull << 52) | (z & 0xFFFFFFFFFFFFFull) | ((z >> 63) << 63);
-        x[i] = __longlong_as_double(static_cast<long long>(bits));
+        const double v = __longlong_as_double(static_cast<long long>(bits));
+        if (as_float)
+            static_cast<float*>(x)[i] = static_cast<float>(v);
+        else
+            static_cast<double*>(x)[i] = v;
     }
 }
 
@@ -565,7 +570,13 @@ bool spmv_wants_sliced(int role, const CsrDev& C) {
     return it == g_mode_cache.end() || it->second >= tiled::kModeSliced;
 }
 
-afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode* out, bool allow_tuning) {
+void fill_tune_vector(void* x, int32_t n, bool as_float, cudaStream_t st) {
+    if (n <= 0) return;
+    k_tune_vector<<<std::max(1, std::min(ceil_div(n, 256), num_sms() * 8)), 256, 0, st>>>(n, x, as_float);
+}
+
+afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode* out, bool allow_tuning,
+                           const RoleLaunch* how) {
     auto& mu = g_mode_mu;
     auto& cache = g_mode_cache;
     const int forced = forced_mode(role);
@@ -597,7 +608,7 @@ afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode*
         return AFSAI_OK;
     }
     // time the candidates on this matrix
-    std::vector<int> cand = {2, 3, 4, 6, 8, 101, 102, 103};
+    std::vector<int> cand = {2, 3, 4, 6, 8, 101, 102};
     if (avg <= 16.0) cand.insert(cand.begin(), 1);
     if (C.sell.nslices > 0) {
         cand.push_back(tiled::kModeSliced);
@@ -613,8 +624,13 @@ afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode*
     // a vector with full significands and both signs: the FP64 fma of this
     // GPU runs measurably faster on zero operands, so zeros would time the
     // engines on work they never see
-    k_tune_vector<<<std::max(1, std::min(ceil_div(C.n, 256), num_sms() * 8)), 256, 0, st>>>(C.n, xb.p);
+    // (x of a reduced-precision G^T is an FP32 vector)
+    const bool x_float = how ? how->x_float : (role == ROLE_GT && C.vtype != VAL_F64);
+    fill_tune_vector(xb.p, C.n, x_float, st);
     AFSAI_CUDA_TRY(cudaGetLastError());
+    auto run = [&](const SpmvMode& m) {
+        return how ? how->launch(m, xb.p, yb.p, st) : launch_role(role, m, C, xb.p, yb.p, st);
+    };
     // Matrices larger than the L2 cache: in a solve each product follows
     // other products that stream GBs through L2, so x is cold there; each
     // timed launch here follows a write of a scratch buffer twice the L2
@@ -635,7 +651,10 @@ afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode*
     for (int mode : cand) {
         SpmvMode m;
         if (!make_mode(mode, C, &m)) continue;
-        if (launch_role(role, m, C, xb.p, yb.p, st) != AFSAI_OK) continue;
+        if (run(m) != AFSAI_OK) {
+            cudaGetLastError();
+            continue;
+        }
         float ms = -1.f;
         for (int trial = 0; trial < 3; ++trial) {
             float t = 0.f;
@@ -643,7 +662,7 @@ afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode*
             for (int r = 0; r < 4 && ok; ++r) {
                 if (flush.p) cudaMemsetAsync(flush.p, r + trial, flush.n, st);
                 cudaEventRecord(e0, st);
-                launch_role(role, m, C, xb.p, yb.p, st);
+                run(m);
                 cudaEventRecord(e1, st);
                 float t1 = 0.f;
                 ok = cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t1, e0, e1) == cudaSuccess;
@@ -658,11 +677,9 @@ afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode*
                          role, C.n, static_cast<long long>(C.nnz), key.sliced, mode, ms / 4.0f,
                          flush.p ? " (L2 flushed)" : "");
         // candidates run from the simplest engine up; a later one must be
-        // faster by more than 3% to replace the best so far: the solve runs
-        // the product fused with its dot product and update (more
-        // registers, fewer resident blocks for the tiled engines), so near
-        // ties here do not carry over (rows of 7 entries: the tiled engine
-        // 1% ahead here, 15% behind in the solve)
+        // faster by more than 3% to replace the best so far (near ties flip
+        // from run to run, and the simpler engine keeps more blocks
+        // resident when the kernel around it changes)
         if (best < 0 || ms < 0.97f * best_ms) {
             best = mode;
             best_ms = ms;

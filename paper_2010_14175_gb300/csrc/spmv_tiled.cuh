@@ -22,6 +22,8 @@
 // returns without contributing to the grid reduction.
 #pragma once
 
+#include <functional>
+
 #include "afsai_internal.cuh"
 
 namespace afsai {
@@ -845,12 +847,28 @@ struct SpmvMode {
 // Roles of the matrices whose engine choice is cached.
 enum SpmvRole : int { ROLE_A = 0, ROLE_G = 1, ROLE_GT = 2 };
 
+// How a solve launches a role's product (fused with its dot product or
+// vector update): y = C x with engine m on a stream.  The engine timing
+// runs this launch when given, so the engines are ranked by the kernel
+// that will run (a fused kernel's registers, and so its resident blocks,
+// differ from the plain product's).  x_float: x holds n floats.
+struct RoleLaunch {
+    bool x_float = false;
+    std::function<afsai_status(const SpmvMode&, const void*, void*, cudaStream_t)> launch;
+};
+
 // Engine for a matrix: timed once per (role, shape, value type) among the
-// candidate engines on the given stream, then cached.  Must not be called
-// during stream capture.  With allow_tuning = false nothing is timed or
-// allocated: the cached engine is used if there is one, else a default
-// chosen from the average row length.
-afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode* out, bool allow_tuning = true);
+// candidate engines on the given stream (with `how`, else the plain
+// product of the role), then cached.  Must not be called during stream
+// capture.  With allow_tuning = false nothing is timed or allocated: the
+// cached engine is used if there is one, else a default chosen from the
+// average row length.
+afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode* out, bool allow_tuning = true,
+                           const RoleLaunch* how = nullptr);
+
+// n values with full significands and both signs, +-(1 + f) (doubles, or
+// floats with as_float), to time products on the data they see.
+void fill_tune_vector(void* x, int32_t n, bool as_float, cudaStream_t st);
 
 // Whether a sliced copy of C would serve `role`: the engine is pinned to
 // the sliced one, or it has not been chosen yet for this shape with a
