@@ -107,7 +107,12 @@ struct SellDev {
     int2* rowlen = nullptr;   // 32 nslices
     int32_t* col = nullptr;   // nslots
     void* val = nullptr;      // nslots, the value type of the CSR
+    // built with the sliced copy: for each tile of kTileOrderRows rows of
+    // the CSR, its rows by length (longest first; ties by row), as indices
+    // within the tile (n bytes)
+    uint8_t* order = nullptr;
 };
+constexpr int kTileOrderRows = 256;
 
 struct CsrDev {
     int32_t n = 0;

@@ -356,6 +356,7 @@ bool with_mode(int mode, F f) {
         case 101: f(std::integral_constant<int, 101>{}); return true;
         case 102: f(std::integral_constant<int, 102>{}); return true;
         case 103: f(std::integral_constant<int, 103>{}); return true;
+        case 104: f(std::integral_constant<int, 104>{}); return true;
         case tiled::kModeSliced: f(std::integral_constant<int, tiled::kModeSliced>{}); return true;
         case tiled::kModeSlicedPipe: f(std::integral_constant<int, tiled::kModeSlicedPipe>{}); return true;
         case tiled::kModeSlicedPipe8: f(std::integral_constant<int, tiled::kModeSlicedPipe8>{}); return true;

@@ -110,7 +110,33 @@ __global__ void sell_fill(int32_t nslices, const int32_t* __restrict__ kptr, con
 
 }  // namespace
 
+// Row order of each tile of kTileOrderRows rows, longest row first (ties
+// by row index): thread t of the tile counts the rows that precede its row
+// in that order (a deterministic rank; a few hundred comparisons per row,
+// once per matrix).
+__global__ void tile_order_kernel(int32_t n, const int32_t* __restrict__ rowptr, uint8_t* __restrict__ order) {
+    __shared__ int32_t len[kTileOrderRows];
+    const int t = threadIdx.x;
+    for (int64_t r0 = static_cast<int64_t>(blockIdx.x) * kTileOrderRows; r0 < n;
+         r0 += static_cast<int64_t>(gridDim.x) * kTileOrderRows) {
+        const int nr = static_cast<int>(n - r0 < kTileOrderRows ? n - r0 : kTileOrderRows);
+        const int32_t mine = t < nr ? rowptr[r0 + t + 1] - rowptr[r0 + t] : -1;
+        len[t] = mine;
+        __syncthreads();
+        if (t < nr) {
+            int rank = 0;
+            for (int j = 0; j < nr; ++j) {
+                const int32_t lj = len[j];
+                rank += (lj > mine || (lj == mine && j < t)) ? 1 : 0;
+            }
+            order[r0 + rank] = static_cast<uint8_t>(t);
+        }
+        __syncthreads();
+    }
+}
+
 void free_sell(SellDev* S, cudaStream_t st) {
+    if (S->order) cudaFreeAsync(S->order, st);
     if (S->kptr) cudaFreeAsync(S->kptr, st);
     if (S->rowlen) cudaFreeAsync(S->rowlen, st);
     if (S->col) cudaFreeAsync(S->col, st);
@@ -160,6 +186,13 @@ afsai_status build_sell(const CsrDev& C, SellDev* S, cudaStream_t st) {
                                                           reinterpret_cast<__nv_bfloat16*>(sval.p));
     AFSAI_CUDA_TRY(cudaGetLastError());
     count_launches(1);
+    DevBuf<uint8_t> order;
+    AFSAI_TRY(order.alloc(static_cast<size_t>(C.n), st));
+    const int oblocks = std::max(1, std::min(ceil_div(C.n, kTileOrderRows), num_sms() * 8));
+    tile_order_kernel<<<oblocks, kTileOrderRows, 0, st>>>(C.n, C.rowptr, order.p);
+    AFSAI_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    S->order = order.detach();
     S->nslices = nslices;
     S->nslots = nslots;
     S->kptr = kptr.detach();

@@ -409,6 +409,17 @@ bool make_mode(int mode, const CsrDev& C, SpmvMode* m) {
         m->cap = 0;
         return true;
     }
+    if (mode == 104) {
+        // one thread per row over tiles of the order's kTileOrderRows rows
+        if (C.sell.order == nullptr) return false;
+        const TiledPlan pl = plan_tiled(C.n, C.nnz, C.max_row, val_bytes(C.vtype), C.col, C.val, 1, 0);
+        if (!pl.ok || pl.tpr != 1 || pl.threads != kTileOrderRows) return false;
+        m->threads = pl.threads;
+        m->blocks = pl.blocks;
+        m->smem = pl.smem;
+        m->cap = pl.cap;
+        return true;
+    }
     if (mode > 100) {
         const TiledPlan pl = plan_tiled(C.n, C.nnz, C.max_row, val_bytes(C.vtype), C.col, C.val,
                                         mode == 103 ? 1 : mode - 100, mode == 103 ? tiled::kBalancedTileBytes : 0);
@@ -455,6 +466,7 @@ afsai_status launch_plain(const SpmvMode& m, const CsrDev& C, const XT* x, YT* y
         case 101: return launch_plain_mode<101, VT, XT, ACC, YT>(m, C, x, y, st);
         case 102: return launch_plain_mode<102, VT, XT, ACC, YT>(m, C, x, y, st);
         case 103: return launch_plain_mode<103, VT, XT, ACC, YT>(m, C, x, y, st);
+        case 104: return launch_plain_mode<104, VT, XT, ACC, YT>(m, C, x, y, st);
         case tiled::kModeSliced: return launch_plain_mode<tiled::kModeSliced, VT, XT, ACC, YT>(m, C, x, y, st);
         case tiled::kModeSlicedPipe:
             return launch_plain_mode<tiled::kModeSlicedPipe, VT, XT, ACC, YT>(m, C, x, y, st);
@@ -562,12 +574,12 @@ int spmv_engine_of(int role, int32_t n, int64_t nnz, int vtype) {
 
 bool spmv_wants_sliced(int role, const CsrDev& C) {
     const int forced = forced_mode(role);
-    if (forced) return forced >= tiled::kModeSliced;
+    if (forced) return forced >= tiled::kModeSliced || forced == 104;
     ModeKey key = key_of(role, C);
     key.sliced = 1;
     std::lock_guard<std::mutex> lock(g_mode_mu);
     auto it = g_mode_cache.find(key);
-    return it == g_mode_cache.end() || it->second >= tiled::kModeSliced;
+    return it == g_mode_cache.end() || it->second >= tiled::kModeSliced || it->second == 104;
 }
 
 void fill_tune_vector(void* x, int32_t n, bool as_float, cudaStream_t st) {
@@ -611,6 +623,7 @@ afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode*
     std::vector<int> cand = {2, 3, 4, 6, 8, 101, 102};
     if (avg <= 16.0) cand.insert(cand.begin(), 1);
     if (C.sell.nslices > 0) {
+        cand.push_back(104);
         cand.push_back(tiled::kModeSliced);
         cand.push_back(tiled::kModeSlicedPipe);
         cand.push_back(tiled::kModeSlicedPipe8);

@@ -138,14 +138,17 @@ __host__ __device__ inline size_t stage_bytes(int cap) {
 }
 
 // Row loop of one tile.  Epi::row(i, acc) consumes the result of row i
-// (called by the first thread of the row's group).
+// (called by the first thread of the row's group).  order (TPR = 1): the
+// tile's rows by length, so that each warp takes rows of similar length.
 template <int TPR, typename VT, typename XT, typename ACC, class Epi>
 __device__ __forceinline__ void tile_rows(int64_t r0, int64_t r1, const int32_t* __restrict__ rowptr,
                                           const int32_t* __restrict__ col, const VT* __restrict__ val,
                                           const XT* __restrict__ x, const int32_t* scol, const VT* sval,
-                                          int64_t c_lo, int64_t v_lo, bool staged, Epi& epi) {
+                                          int64_t c_lo, int64_t v_lo, bool staged, Epi& epi,
+                                          const uint8_t* __restrict__ order = nullptr) {
     const int t = threadIdx.x;
-    const int64_t i = r0 + t / TPR;
+    int64_t i = r0 + t / TPR;
+    if (TPR == 1 && order != nullptr && i < r1) i = r0 + order[i];
     const int part = t % TPR;
     ACC acc = ACC(0);
     if (i < r1) {
@@ -287,7 +290,8 @@ __device__ __forceinline__ void tile_rows_balanced(int64_t r0, int64_t r1, const
 template <int TPR, typename VT, typename XT, typename ACC, class Epi, bool BAL = false>
 __device__ bool spmv_tiles(int32_t n, int64_t nnz, const int32_t* __restrict__ rowptr,
                            const int32_t* __restrict__ col, const VT* __restrict__ val, const XT* __restrict__ x,
-                           int cap, int32_t* errflag, Epi& epi, long long wait) {
+                           int cap, int32_t* errflag, Epi& epi, long long wait,
+                           const uint8_t* __restrict__ order = nullptr) {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
     int32_t* scol = reinterpret_cast<int32_t*>(smem + 128);
@@ -341,12 +345,12 @@ __device__ bool spmv_tiles(int32_t n, int64_t nnz, const int32_t* __restrict__ r
             if constexpr (BAL)
                 tile_rows_balanced<VT, XT, ACC>(r0, r1, rowptr, col, val, x, scol, sval, c_lo, v_lo, true, B, epi);
             else
-                tile_rows<TPR, VT, XT, ACC>(r0, r1, rowptr, col, val, x, scol, sval, c_lo, v_lo, true, epi);
+                tile_rows<TPR, VT, XT, ACC>(r0, r1, rowptr, col, val, x, scol, sval, c_lo, v_lo, true, epi, order);
         } else {
             if constexpr (BAL)
                 tile_rows_balanced<VT, XT, ACC>(r0, r1, rowptr, col, val, x, scol, sval, c_lo, v_lo, false, B, epi);
             else
-                tile_rows<TPR, VT, XT, ACC>(r0, r1, rowptr, col, val, x, scol, sval, c_lo, v_lo, false, epi);
+                tile_rows<TPR, VT, XT, ACC>(r0, r1, rowptr, col, val, x, scol, sval, c_lo, v_lo, false, epi, order);
         }
         __syncthreads();  // the stage is reused by the next tile
     }
@@ -420,11 +424,12 @@ struct SellView {
     const int2* rowlen;
     const int32_t* col;
     const void* val;
+    const uint8_t* order;  // row order of the CSR's tiles (SellDev::order)
 };
 
 inline SellView sell_view(const SellDev& S) {
     return SellView{S.nslices, (S.nslices + kSellWindowSlices - 1) / kSellWindowSlices, S.kptr, S.rowlen, S.col,
-                    S.val};
+                    S.val, S.order};
 }
 
 // The engines sweep tasks (grid-stride).  In slice order (ILV = false) task
@@ -791,7 +796,9 @@ constexpr int kStagedWarps = 4;           // warps per block of the staged engin
 // SpMV row engine.  MODE 1, 2, 4, 8: strided with MODE lanes per row;
 // MODE 3, 6: grouped with MODE lanes per row; MODE 101, 102: TMA-staged
 // tiles with MODE - 100 threads per row; MODE 103: TMA-staged tiles with the
-// balanced row loop (tile_rows_balanced); MODE 200 - 203: the sliced copy,
+// balanced row loop (tile_rows_balanced); MODE 104: as 101, each tile's rows
+// taken longest first (SellDev::order, built with the sliced copy), so a
+// warp's rows have similar lengths; MODE 200 - 203: the sliced copy,
 // one lane per row (201, 202 software-pipelined by 4 and 8 entries, 203 as
 // 201 with the windows interleaved);
 // MODE 210, 211: the sliced copy staged through shared memory by bulk
@@ -820,6 +827,9 @@ __device__ __forceinline__ bool spmv_rows(int32_t n, int64_t nnz, const int32_t*
     } else if constexpr (MODE == kModeBalanced) {
         spmv_balanced<VT, XT, ACC>(n, rowptr, col, val, x, epi);
         return true;
+    } else if constexpr (MODE == 104) {
+        // tiles of kTileOrderRows rows (the plan's block size), rows by length
+        return spmv_tiles<1, VT, XT, ACC, Epi>(n, nnz, rowptr, col, val, x, cap, errflag, epi, wait, sv.order);
     } else if constexpr (MODE == 103) {
         return spmv_tiles<1, VT, XT, ACC, Epi, true>(n, nnz, rowptr, col, val, x, cap, errflag, epi, wait);
     } else if constexpr (MODE > 100) {
@@ -870,9 +880,10 @@ afsai_status spmv_mode_for(int role, const CsrDev& C, cudaStream_t st, SpmvMode*
 // floats with as_float), to time products on the data they see.
 void fill_tune_vector(void* x, int32_t n, bool as_float, cudaStream_t st);
 
-// Whether a sliced copy of C would serve `role`: the engine is pinned to
-// the sliced one, or it has not been chosen yet for this shape with a
-// sliced copy, or the sliced engine was chosen.
+// Whether a sliced copy of C (and the tile row order built with it) would
+// serve `role`: the engine is pinned to one that reads them, or it has not
+// been chosen yet for this shape with a sliced copy, or such an engine was
+// chosen.
 bool spmv_wants_sliced(int role, const CsrDev& C);
 
 // y = C x with the engine `m` and the value/vector types of `role`.

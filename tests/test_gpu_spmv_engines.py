@@ -20,7 +20,7 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-ENGINES = [1, 2, 3, 4, 6, 8, 101, 102, 103, 200, 201, 202, 203, 210, 211, 301]
+ENGINES = [1, 2, 3, 4, 6, 8, 101, 102, 103, 104, 200, 201, 202, 203, 210, 211, 301]
 
 _SCRIPT = r'''
 import sys
@@ -81,6 +81,10 @@ for name, A, kiter, s in cases:
     if name == "arrow":
         assert got[0] < 200 or got[0] == 301, (name, got)  # no sliced copy of A: a CSR engine serves
     elif mode in (1, 2, 3, 4, 6, 8, 103, 200, 201, 202, 203, 210, 211, 301):
+        assert got == (mode, mode, mode), (name, got)
+    elif mode == 104 and name in ("poisson20", "hubs"):
+        # tiles of 256 rows fit in shared memory here (not with the ~80-entry
+        # elasticity rows)
         assert got == (mode, mode, mode), (name, got)
 print("ok")
 '''
