@@ -174,8 +174,9 @@ afsai_status setup_precond(const afsai_csr* A, const afsai_params* p, cudaStream
 // Sparse building blocks (sparse.cu).
 afsai_status exclusive_scan_i32(const int32_t* in, int32_t* out, int32_t n, cudaStream_t st, int64_t* total_host);
 afsai_status build_transpose(const CsrDev& G, CsrDev* Gt, cudaStream_t st);
-// Sliced copy of C (sell.cu); *S stays empty on failure.
-afsai_status build_sell(const CsrDev& C, SellDev* S, cudaStream_t st);
+// Sliced copy of C (sell.cu), with_order: and the tile row order; *S stays
+// empty on failure.
+afsai_status build_sell(const CsrDev& C, SellDev* S, cudaStream_t st, bool with_order = true);
 void free_sell(SellDev* S, cudaStream_t st);
 afsai_status spmv_csr(const CsrDev& A, const double* x, double* y, cudaStream_t st);
 afsai_status apply_precond(const afsai_precond* M, const double* r, double* t, double* z, cudaStream_t st);

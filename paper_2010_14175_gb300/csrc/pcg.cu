@@ -622,7 +622,7 @@ afsai_status pcg_body(const CsrDev& Ain, const afsai_precond* M, const double* b
     SlicedA sa{Ain, st};
     if (spmv_wants_sliced(ROLE_A, Ain)) {
         const std::string keep = afsai_last_error();
-        if (build_sell(Ain, &sa.view.sell, st) != AFSAI_OK) {
+        if (build_sell(Ain, &sa.view.sell, st, spmv_wants_order(ROLE_A, Ain)) != AFSAI_OK) {
             cudaGetLastError();  // a failed allocation is not an error of the solve
             set_error(keep);
         }

@@ -144,7 +144,7 @@ void free_sell(SellDev* S, cudaStream_t st) {
     *S = SellDev{};
 }
 
-afsai_status build_sell(const CsrDev& C, SellDev* S, cudaStream_t st) {
+afsai_status build_sell(const CsrDev& C, SellDev* S, cudaStream_t st, bool with_order) {
     *S = SellDev{};
     if (C.n <= 0) return AFSAI_OK;
     const int32_t nslices = static_cast<int32_t>((static_cast<int64_t>(C.n) + 31) / 32);
@@ -186,13 +186,15 @@ afsai_status build_sell(const CsrDev& C, SellDev* S, cudaStream_t st) {
                                                           reinterpret_cast<__nv_bfloat16*>(sval.p));
     AFSAI_CUDA_TRY(cudaGetLastError());
     count_launches(1);
-    DevBuf<uint8_t> order;
-    AFSAI_TRY(order.alloc(static_cast<size_t>(C.n), st));
-    const int oblocks = std::max(1, std::min(ceil_div(C.n, kTileOrderRows), num_sms() * 8));
-    tile_order_kernel<<<oblocks, kTileOrderRows, 0, st>>>(C.n, C.rowptr, order.p);
-    AFSAI_CUDA_TRY(cudaGetLastError());
-    count_launches(1);
-    S->order = order.detach();
+    if (with_order) {
+        DevBuf<uint8_t> order;
+        AFSAI_TRY(order.alloc(static_cast<size_t>(C.n), st));
+        const int oblocks = std::max(1, std::min(ceil_div(C.n, kTileOrderRows), num_sms() * 8));
+        tile_order_kernel<<<oblocks, kTileOrderRows, 0, st>>>(C.n, C.rowptr, order.p);
+        AFSAI_CUDA_TRY(cudaGetLastError());
+        count_launches(1);
+        S->order = order.detach();
+    }
     S->nslices = nslices;
     S->nslots = nslots;
     S->kptr = kptr.detach();

@@ -2450,8 +2450,8 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
         // succeeds
         const std::string keep = afsai_last_error();
         const bool want_g = spmv_wants_sliced(ROLE_G, G), want_gt = spmv_wants_sliced(ROLE_GT, M->Gt);
-        if ((want_g && build_sell(G, &G.sell, st) != AFSAI_OK) ||
-            (want_gt && build_sell(M->Gt, &M->Gt.sell, st) != AFSAI_OK)) {
+        if ((want_g && build_sell(G, &G.sell, st, spmv_wants_order(ROLE_G, G)) != AFSAI_OK) ||
+            (want_gt && build_sell(M->Gt, &M->Gt.sell, st, spmv_wants_order(ROLE_GT, M->Gt)) != AFSAI_OK)) {
             free_sell(&G.sell, st);
             free_sell(&M->Gt.sell, st);
             cudaGetLastError();

@@ -572,6 +572,16 @@ int spmv_engine_of(int role, int32_t n, int64_t nnz, int vtype) {
     return 0;
 }
 
+bool spmv_wants_order(int role, const CsrDev& C) {
+    const int forced = forced_mode(role);
+    if (forced) return forced == 104;
+    ModeKey key = key_of(role, C);
+    key.sliced = 1;
+    std::lock_guard<std::mutex> lock(g_mode_mu);
+    auto it = g_mode_cache.find(key);
+    return it == g_mode_cache.end() || it->second == 104;
+}
+
 bool spmv_wants_sliced(int role, const CsrDev& C) {
     const int forced = forced_mode(role);
     if (forced) return forced >= tiled::kModeSliced || forced == 104;

@@ -886,6 +886,11 @@ void fill_tune_vector(void* x, int32_t n, bool as_float, cudaStream_t st);
 // chosen.
 bool spmv_wants_sliced(int role, const CsrDev& C);
 
+// Whether the tile row order (engine 104) would serve `role`: the engine is
+// pinned to 104, or not chosen yet for this shape with a sliced copy, or
+// 104 was chosen.
+bool spmv_wants_order(int role, const CsrDev& C);
+
 // y = C x with the engine `m` and the value/vector types of `role`.
 afsai_status spmv_launch_role(int role, const SpmvMode& m, const CsrDev& C, const void* x, void* y, cudaStream_t st);
 
