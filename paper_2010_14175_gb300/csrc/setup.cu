@@ -1162,7 +1162,7 @@ __global__ void __launch_bounds__(256) step_gather(StepArgs a) {
 // entries (7-point and 5-point stencils with s <= 4), a row's step touches
 // at most 11 x 8 entries of A and a few dozen distinct candidates, far too
 // little work for a warp; here every warp instruction serves 32 rows.  Each
-// lane owns a 64-slot open-addressing table in shared memory (lane-
+// lane owns a 48-slot open-addressing table in shared memory (lane-
 // interleaved, so a warp's accesses fall in distinct banks) with its
 // occupancy kept as a 64-bit mask in registers: no atomics, no clearing.
 // Gradient, selection and merge are those of step_gather (same operation
@@ -1172,8 +1172,20 @@ __global__ void __launch_bounds__(256) step_gather(StepArgs a) {
 // A row whose candidates exceed 7/8 of the table is marked for the retry
 // pass, as in the other kernels.
 // ---------------------------------------------------------------------------
-constexpr int kLaneHT = 64;
+constexpr int kLaneHT = 48;
 constexpr int kLaneRowMax = 8;
+
+// Home slot of column j in a lane's table of HT slots (a multiplicative
+// hash; HT need not be a power of two), and the next slot of a probe.
+template <int HT>
+__device__ __forceinline__ uint32_t lane_slot(int32_t j) {
+    const uint32_t hsh = static_cast<uint32_t>(j) * 0x9E3779B1u;
+    return static_cast<uint32_t>((static_cast<uint64_t>(hsh) * HT) >> 32);
+}
+template <int HT>
+__device__ __forceinline__ uint32_t lane_next(uint32_t h) {
+    return h + 1 == HT ? 0u : h + 1;
+}
 
 // Occupancy of a lane's table: one bit per slot, in registers.
 template <int HT>
@@ -1201,8 +1213,7 @@ struct Occ {
 template <int MC, int HT>
 __global__ void __launch_bounds__(128) step_gather_lane(StepArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int LOG2 = HT == 32 ? 5 : (HT == 64 ? 6 : 7);
-    static_assert((1 << LOG2) == HT && HT <= 128, "table size");
+    static_assert(HT >= 32 && HT <= 128, "table size");
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int nwb = blockDim.x >> 5;
@@ -1249,7 +1260,7 @@ __global__ void __launch_bounds__(128) step_gather_lane(StepArgs a) {
             for (int q = 0; q < kLaneRowMax; ++q) {
                 const int32_t j = c0[q];
                 if (j < i) {
-                    uint32_t h = slot_of(j, LOG2);
+                    uint32_t h = lane_slot<HT>(j);
                     for (int probe = 0; probe < HT; ++probe) {
                         if (!occ.test(h)) {
                             occ.set(h);
@@ -1259,7 +1270,7 @@ __global__ void __launch_bounds__(128) step_gather_lane(StepArgs a) {
                             break;
                         }
                         if (TK(h) == j) break;
-                        h = (h + 1) & (HT - 1);
+                        h = lane_next<HT>(h);
                     }
                     TV(h) = fma(v0[q], gr, TV(h));
                 }
@@ -1279,13 +1290,13 @@ __global__ void __launch_bounds__(128) step_gather_lane(StepArgs a) {
         // members of P are not eligible (i itself is never a candidate)
         for (int t = 0; t < m - 1; ++t) {
             const int32_t pj = TP(t);
-            uint32_t h = slot_of(pj, LOG2);
+            uint32_t h = lane_slot<HT>(pj);
             for (int probe = 0; probe < HT && occ.test(h); ++probe) {
                 if (TK(h) == pj) {
                     TV(h) = 0.0;
                     break;
                 }
-                h = (h + 1) & (HT - 1);
+                h = lane_next<HT>(h);
             }
         }
         // locality bound (Section 4): candidates outside the allowed stripes
@@ -2328,38 +2339,40 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
         count_launches(1);
     } else if (!fused_only && lane_gather_applies(mcap, p->s, max_row_nnz)) {
         // small stencils: lane-per-row gather, 2 lanes per row in the solve
-        // (AFSAI_LANE_HT = 32 or 64 table slots per row; AFSAI_SOLVE_SQRT =
-        // 0 IEEE FP64 or 1 integer-pipe square roots)
+        // (AFSAI_LANE_HT = 48 (default) or 64 table slots per row;
+        // AFSAI_SOLVE_SQRT = 0 IEEE FP64 or 1 integer-pipe square roots)
         static const int lane_ht = [] {
             const char* e = std::getenv("AFSAI_LANE_HT");
-            return e && std::atoi(e) == 32 ? 32 : 64;
+            return e && std::atoi(e) == 64 ? 64 : kLaneHT;
         }();
         static const bool sqrt_int = [] {
             const char* e = std::getenv("AFSAI_SOLVE_SQRT");
             return e && std::atoi(e) == 1;
         }();
         // patterns of 13 to 20 entries (kiter 8, s 2 in the uneven batch):
-        // up to ~60 distinct candidates, 128-slot tables, 4 lanes per row
+        // up to ~60 distinct candidates (63 for an anisotropic 7-point
+        // stencil), 96-slot tables (5 warps per SM; 128 slots: 4), 4 or 8
+        // lanes per row
         const int lpr = tune ? tune->lane_lpr : 0;
         if (mcap > 12) {
             if (lpr == 8)
-                AFSAI_TRY(chol32 ? (run_stepwise_lane<20, 8, true, 128>(a, p->kiter, st))
-                                 : (run_stepwise_lane<20, 8, false, 128>(a, p->kiter, st)));
+                AFSAI_TRY(chol32 ? (run_stepwise_lane<20, 8, true, 96>(a, p->kiter, st))
+                                 : (run_stepwise_lane<20, 8, false, 96>(a, p->kiter, st)));
             else
-                AFSAI_TRY(chol32 ? (run_stepwise_lane<20, 4, true, 128>(a, p->kiter, st))
-                                 : (run_stepwise_lane<20, 4, false, 128>(a, p->kiter, st)));
+                AFSAI_TRY(chol32 ? (run_stepwise_lane<20, 4, true, 96>(a, p->kiter, st))
+                                 : (run_stepwise_lane<20, 4, false, 96>(a, p->kiter, st)));
         } else if (lpr == 4) {
-            AFSAI_TRY(chol32 ? (run_stepwise_lane<12, 4, true, 64>(a, p->kiter, st))
-                             : (run_stepwise_lane<12, 4, false, 64>(a, p->kiter, st)));
+            AFSAI_TRY(chol32 ? (run_stepwise_lane<12, 4, true>(a, p->kiter, st))
+                             : (run_stepwise_lane<12, 4, false>(a, p->kiter, st)));
         } else if (chol32)
-            AFSAI_TRY(lane_ht == 32 ? (run_stepwise_lane<12, 2, true, 32>(a, p->kiter, st))
-                                    : (run_stepwise_lane<12, 2, true, 64>(a, p->kiter, st)));
+            AFSAI_TRY(lane_ht == 64 ? (run_stepwise_lane<12, 2, true, 64>(a, p->kiter, st))
+                                    : (run_stepwise_lane<12, 2, true>(a, p->kiter, st)));
         else if (sqrt_int)
-            AFSAI_TRY(lane_ht == 32 ? (run_stepwise_lane<12, 2, false, 32, true>(a, p->kiter, st))
-                                    : (run_stepwise_lane<12, 2, false, 64, true>(a, p->kiter, st)));
+            AFSAI_TRY(lane_ht == 64 ? (run_stepwise_lane<12, 2, false, 64, true>(a, p->kiter, st))
+                                    : (run_stepwise_lane<12, 2, false, kLaneHT, true>(a, p->kiter, st)));
         else
-            AFSAI_TRY(lane_ht == 32 ? (run_stepwise_lane<12, 2, false, 32>(a, p->kiter, st))
-                                    : (run_stepwise_lane<12, 2, false, 64>(a, p->kiter, st)));
+            AFSAI_TRY(lane_ht == 64 ? (run_stepwise_lane<12, 2, false, 64>(a, p->kiter, st))
+                                    : (run_stepwise_lane<12, 2, false>(a, p->kiter, st)));
     } else if (!fused_only && stepwise_supported(mcap) && !chol32)
         AFSAI_TRY(run_stepwise(a, mcap, ht, p->kiter, chol32, st, cand_bound));
     else if (!fused_only && (wide_lpr == 4 || wide_lpr == 8) && mcap > 20 && mcap <= 32 && (!chol32 || wide_mixed))
