@@ -49,6 +49,13 @@ struct BChunk {
     int32_t sys, row0, row1;
 };
 
+// The chunks a kernel visits: act[0 .. *count) (indices into the chunk
+// table), or the whole table (act null, *count the table's size).
+struct ChunkList {
+    const int32_t* act;
+    const int32_t* count;
+};
+
 struct PackSrc {
     int32_t n;
     int64_t nnz;
@@ -65,8 +72,20 @@ struct BatchEngine {
     BChunk* d_chunks = nullptr;
     double* d_partials = nullptr;
     double* d_partials2 = nullptr;
-    int32_t* d_counts = nullptr;  // [0] active systems, [1] chunks, [2] loop budget, [3] finished in a launch
+    // [0] active systems, [1] chunks, [2] loop budget, [3] finished in a
+    // launch, [4] chunks of running systems (d_act), [5] [3] when d_act was
+    // built, [6] d_act to be rebuilt
+    int32_t* d_counts = nullptr;
     int32_t* h_counts = nullptr;  // pinned
+    int32_t* d_act = nullptr;     // chunks of the running systems
+    ChunkList all() const { return ChunkList{nullptr, d_counts + 1}; }
+    ChunkList active() const { return ChunkList{d_act, d_counts + 4}; }
+    // The running systems' chunks listed again (forced, or when a system
+    // finished since the last listing): the iteration kernels then skip no
+    // chunk of a finished system, which at the tail of an uneven batch (a
+    // few systems running, tens of thousands of chunks) is most of their
+    // work.
+    afsai_status refresh_active(cudaStream_t st, bool force);
     int32_t cap_sys = 0;
     int64_t cap_chunks = 0;
     int32_t vtype = VAL_F64;

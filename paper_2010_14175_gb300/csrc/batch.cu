@@ -1,22 +1,26 @@
-// Batched aFSAI-PCG: many independent SPD systems of uneven size solved in
-// one set-up launch and one stream of graph-captured PCG iterations.
+// Batched aFSAI-PCG: many independent SPD systems of uneven size solved
+// with one set-up pass per bucket of systems and one graph launch of PCG.
 //
-// Set-up.  The systems' CSRs are packed into one block-diagonal matrix and
-// the fused set-up kernel runs once over all rows.  Rows are independent
-// and a row only sees columns of its own block, so each system's G is
-// exactly the G of that system alone.  G and G^T stay packed; their column
-// indices are made local to each system afterwards.
+// Set-up.  The systems are grouped by the longest row of their matrix
+// (small stencils: the lane-per-row path; longer rows: the warp-per-row
+// path); each bucket's CSRs are packed into one block-diagonal matrix and
+// set up in one pass over all its rows, with a solve tile chosen per
+// bucket by timing a sample.  Rows are independent and a row only sees
+// columns of its own block, so each system's G is exactly the G of that
+// system alone.  G and G^T stay packed; their column indices are made
+// local to each system afterwards.
 //
 // PCG.  Every system keeps its own vectors and scalars (rz, alpha, beta,
 // rr, convergence).  Work is cut into chunks of up to kChunk rows of one
 // system; a block handles one chunk at a time, one thread per row.  The SpMV
 // of a row is the plain sequential sum in CSR order, and every per-system
 // dot product is reduced over the system's own chunks in a fixed order
-// (fixed tree inside a chunk, chunks in order), so the result of a system
-// does not depend on which other systems share the batch.  A system that
-// has converged stops touching its vectors; the batch ends when the device
-// counter of active systems reaches zero, which the host polls between
-// launches of a graph of several iterations.
+// (fixed tree inside a chunk, chunks in table order), so the result of a
+// system does not depend on which other systems share the batch.  The
+// iteration kernels visit the chunks of running systems only (a list built
+// again after every body in which a system finished).  The whole loop is
+// one launch of a graph with a device-side while loop that ends when no
+// system runs or a body budget is spent.
 //
 // The descriptor and chunk tables live in device memory with a fixed
 // capacity and their counts are read on the device, so a captured graph
@@ -102,9 +106,10 @@ __device__ __forceinline__ double row_f64(const int32_t* __restrict__ rp, const 
 
 // ---- init: r = b - A x, bb, rr ------------------------------------------
 __global__ void kb_init(const BSys* __restrict__ sys, BScal* sc, const BChunk* __restrict__ chunks,
-                        const int32_t* nchunks, double* partials, double* partials2) {
+                        ChunkList L, double* partials, double* partials2) {
     __shared__ double sh[32];
-    for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
+    for (int32_t k = blockIdx.x; k < *L.count; k += gridDim.x) {
+        const int32_t c = L.act ? L.act[k] : k;
         const BChunk ch = chunks[c];
         BScal* s = &sc[ch.sys];
         if (!s->fresh) continue;
@@ -170,8 +175,9 @@ __device__ __forceinline__ TT row_Gt(const int32_t* __restrict__ rp, const int32
 
 template <typename VT, typename TT>
 __global__ void kb_G(const BSys* __restrict__ sys, const BScal* sc, const BChunk* __restrict__ chunks,
-                     const int32_t* nchunks, int init) {
-    for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
+                     ChunkList L, int init) {
+    for (int32_t k = blockIdx.x; k < *L.count; k += gridDim.x) {
+        const int32_t c = L.act ? L.act[k] : k;
         const BChunk ch = chunks[c];
         if (init ? !sc[ch.sys].fresh : (sc[ch.sys].done != 0)) continue;
         const BSys& sy = sys[ch.sys];
@@ -184,9 +190,10 @@ __global__ void kb_G(const BSys* __restrict__ sys, const BScal* sc, const BChunk
 // ---- z = G^T t, rz' = r.z, beta -------------------------------------------
 template <typename VT, typename TT>
 __global__ void kb_Gt_dot(const BSys* __restrict__ sys, BScal* sc, const BChunk* __restrict__ chunks,
-                          const int32_t* nchunks, double* partials, int init) {
+                          ChunkList L, double* partials, int init) {
     __shared__ double sh[32];
-    for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
+    for (int32_t k = blockIdx.x; k < *L.count; k += gridDim.x) {
+        const int32_t c = L.act ? L.act[k] : k;
         const BChunk ch = chunks[c];
         BScal* s = &sc[ch.sys];
         if (init ? !s->fresh : (s->done != 0)) continue;
@@ -215,8 +222,9 @@ __global__ void kb_Gt_dot(const BSys* __restrict__ sys, BScal* sc, const BChunk*
 
 // ---- p = z (init) ---------------------------------------------------------
 __global__ void kb_init_p(const BSys* __restrict__ sys, const BScal* sc, const BChunk* __restrict__ chunks,
-                          const int32_t* nchunks) {
-    for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
+                          ChunkList L) {
+    for (int32_t k = blockIdx.x; k < *L.count; k += gridDim.x) {
+        const int32_t c = L.act ? L.act[k] : k;
         const BChunk ch = chunks[c];
         if (!sc[ch.sys].fresh) continue;
         const BSys& sy = sys[ch.sys];
@@ -232,9 +240,10 @@ __global__ void kb_clear_fresh(BScal* sc, int32_t nslots) {
 
 // ---- q = A p, pq, alpha ---------------------------------------------------
 __global__ void kb_A_dot(const BSys* __restrict__ sys, BScal* sc, const BChunk* __restrict__ chunks,
-                         const int32_t* nchunks, double* partials) {
+                         ChunkList L, double* partials) {
     __shared__ double sh[32];
-    for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
+    for (int32_t k = blockIdx.x; k < *L.count; k += gridDim.x) {
+        const int32_t c = L.act ? L.act[k] : k;
         const BChunk ch = chunks[c];
         BScal* s = &sc[ch.sys];
         if (s->done || s->fresh) continue;
@@ -255,9 +264,10 @@ __global__ void kb_A_dot(const BSys* __restrict__ sys, BScal* sc, const BChunk* 
 
 // ---- x += alpha p, r -= alpha q, rr, convergence --------------------------
 __global__ void kb_update_xr(const BSys* __restrict__ sys, BScal* sc, const BChunk* __restrict__ chunks,
-                             const int32_t* nchunks, double* partials) {
+                             ChunkList L, double* partials) {
     __shared__ double sh[32];
-    for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
+    for (int32_t k = blockIdx.x; k < *L.count; k += gridDim.x) {
+        const int32_t c = L.act ? L.act[k] : k;
         const BChunk ch = chunks[c];
         BScal* s = &sc[ch.sys];
         if (s->done || s->fresh) continue;
@@ -293,9 +303,10 @@ __global__ void kb_update_xr(const BSys* __restrict__ sys, BScal* sc, const BChu
 // residual ||b - A x|| does too; otherwise its recurrence continues (the
 // rest of this iteration runs for it) ------------------------------------
 __global__ void kb_true_check(const BSys* __restrict__ sys, BScal* sc, const BChunk* __restrict__ chunks,
-                              const int32_t* nchunks, double* partials) {
+                              ChunkList L, double* partials) {
     __shared__ double sh[32];
-    for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
+    for (int32_t k = blockIdx.x; k < *L.count; k += gridDim.x) {
+        const int32_t c = L.act ? L.act[k] : k;
         const BChunk ch = chunks[c];
         BScal* s = &sc[ch.sys];
         if (s->done != 3) continue;
@@ -340,10 +351,45 @@ __global__ void kb_loop_cond(int32_t* counts, cudaGraphConditionalHandle h, int 
     }
 }
 
+// ---- the running systems' chunks (d_act), listed again when forced or when
+// a system finished since the last listing (counts[3] moved) ---------------
+__global__ void kb_act_begin(int32_t* counts, int force) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const bool go = force || counts[3] != counts[5];
+        counts[5] = counts[3];
+        counts[6] = go ? 1 : 0;
+        if (go) counts[4] = 0;
+    }
+}
+
+// Warps append their chunks of running systems (one atomic per warp); the
+// order of the list changes no result: each chunk keeps its partial slot
+// (its index in the table) and a system's partials are summed in table
+// order.
+__global__ void kb_act_build(const BScal* __restrict__ sc, const BChunk* __restrict__ chunks, int32_t* counts,
+                             int32_t* __restrict__ act) {
+    if (counts[6] == 0) return;
+    const int32_t n = counts[1];
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t w = w0; w * 32 < n; w += nw) {
+        const int64_t c = w * 32 + lane;
+        const bool keep = c < n && sc[chunks[c].sys].done == 0;
+        const unsigned mask = __ballot_sync(kFull, keep);
+        if (mask == 0u) continue;
+        int32_t base = 0;
+        if (lane == 0) base = atomicAdd(counts + 4, __popc(mask));
+        base = __shfl_sync(kFull, base, 0);
+        if (keep) act[base + __popc(mask & ((1u << lane) - 1u))] = static_cast<int32_t>(c);
+    }
+}
+
 // ---- p = z + beta p --------------------------------------------------------
 __global__ void kb_update_p(const BSys* __restrict__ sys, const BScal* sc, const BChunk* __restrict__ chunks,
-                            const int32_t* nchunks) {
-    for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
+                            ChunkList L) {
+    for (int32_t k = blockIdx.x; k < *L.count; k += gridDim.x) {
+        const int32_t c = L.act ? L.act[k] : k;
         const BChunk ch = chunks[c];
         const BScal* s = &sc[ch.sys];
         if (s->done || s->fresh) continue;
@@ -355,9 +401,10 @@ __global__ void kb_update_p(const BSys* __restrict__ sys, const BScal* sc, const
 
 // ---- true residual ||b - A x||^2 per system -------------------------------
 __global__ void kb_true_residual(const BSys* __restrict__ sys, BScal* sc, const BChunk* __restrict__ chunks,
-                                 const int32_t* nchunks, double* partials, int only_done) {
+                                 ChunkList L, double* partials, int only_done) {
     __shared__ double sh[32];
-    for (int32_t c = blockIdx.x; c < *nchunks; c += gridDim.x) {
+    for (int32_t k = blockIdx.x; k < *L.count; k += gridDim.x) {
+        const int32_t c = L.act ? L.act[k] : k;
         const BChunk ch = chunks[c];
         BScal* s = &sc[ch.sys];
         if (only_done && s->done == 0) continue;
@@ -445,8 +492,9 @@ afsai_status BatchEngine::reserve(int32_t max_sys, int64_t max_chunks, cudaStrea
     AFSAI_CUDA_TRY(lib_malloc_async(reinterpret_cast<void**>(&d_chunks), sizeof(BChunk) * cap_chunks, st));
     AFSAI_CUDA_TRY(lib_malloc_async(reinterpret_cast<void**>(&d_partials), sizeof(double) * cap_chunks, st));
     AFSAI_CUDA_TRY(lib_malloc_async(reinterpret_cast<void**>(&d_partials2), sizeof(double) * cap_chunks, st));
-    AFSAI_CUDA_TRY(lib_malloc_async(reinterpret_cast<void**>(&d_counts), sizeof(int32_t) * 4, st));
-    AFSAI_CUDA_TRY(cudaMemsetAsync(d_counts, 0, sizeof(int32_t) * 4, st));
+    AFSAI_CUDA_TRY(lib_malloc_async(reinterpret_cast<void**>(&d_act), sizeof(int32_t) * cap_chunks, st));
+    AFSAI_CUDA_TRY(lib_malloc_async(reinterpret_cast<void**>(&d_counts), sizeof(int32_t) * 8, st));
+    AFSAI_CUDA_TRY(cudaMemsetAsync(d_counts, 0, sizeof(int32_t) * 8, st));
     AFSAI_CUDA_TRY(cudaMallocHost(reinterpret_cast<void**>(&h_counts), sizeof(int32_t) * 4));
     return AFSAI_OK;
 }
@@ -460,6 +508,7 @@ void BatchEngine::release(cudaStream_t st) {
     if (d_partials) cudaFreeAsync(d_partials, st);
     if (d_partials2) cudaFreeAsync(d_partials2, st);
     if (d_counts) cudaFreeAsync(d_counts, st);
+    if (d_act) cudaFreeAsync(d_act, st);
     if (h_counts) cudaFreeHost(h_counts);
     d_sys = nullptr;
     d_sc = nullptr;
@@ -467,6 +516,7 @@ void BatchEngine::release(cudaStream_t st) {
     d_partials = nullptr;
     d_partials2 = nullptr;
     d_counts = nullptr;
+    d_act = nullptr;
     h_counts = nullptr;
     cap_sys = 0;
     cap_chunks = 0;
@@ -505,8 +555,9 @@ afsai_status BatchEngine::upload(const std::vector<BSys>& sys_in, const std::vec
 template <typename VT, typename TT>
 afsai_status launch_precond(BatchEngine& E, int init, cudaStream_t st) {
     const int gb = grid_blocks();
-    kb_G<VT, TT><<<gb, kChunk, 0, st>>>(E.d_sys, E.d_sc, E.d_chunks, E.d_counts + 1, init);
-    kb_Gt_dot<VT, TT><<<gb, kChunk, 0, st>>>(E.d_sys, E.d_sc, E.d_chunks, E.d_counts + 1, E.d_partials, init);
+    kb_G<VT, TT><<<gb, kChunk, 0, st>>>(E.d_sys, E.d_sc, E.d_chunks, init ? E.all() : E.active(), init);
+    kb_Gt_dot<VT, TT><<<gb, kChunk, 0, st>>>(E.d_sys, E.d_sc, E.d_chunks, init ? E.all() : E.active(),
+                                             E.d_partials, init);
     AFSAI_CUDA_TRY(cudaGetLastError());
     count_launches(2);
     return AFSAI_OK;
@@ -520,11 +571,11 @@ afsai_status BatchEngine::precond(int init, cudaStream_t st) {
 
 afsai_status BatchEngine::start(cudaStream_t st) {
     const int gb = grid_blocks();
-    kb_init<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, d_counts + 1, d_partials, d_partials2);
+    kb_init<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, all(), d_partials, d_partials2);
     AFSAI_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     AFSAI_TRY(precond(1, st));
-    kb_init_p<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, d_counts + 1);
+    kb_init_p<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, all());
     kb_clear_fresh<<<std::max(1, std::min(ceil_div(cap_sys, 256), 64)), 256, 0, st>>>(d_sc, cap_sys);
     AFSAI_CUDA_TRY(cudaGetLastError());
     count_launches(2);
@@ -569,13 +620,13 @@ afsai_status BatchEngine::set_scalars(int32_t slot, const BScal& sc_in, cudaStre
 
 afsai_status BatchEngine::iteration(cudaStream_t st) {
     const int gb = grid_blocks();
-    kb_A_dot<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, d_counts + 1, d_partials);
-    kb_update_xr<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, d_counts + 1, d_partials);
-    kb_true_check<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, d_counts + 1, d_partials);
+    kb_A_dot<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, active(), d_partials);
+    kb_update_xr<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, active(), d_partials);
+    kb_true_check<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, active(), d_partials);
     AFSAI_CUDA_TRY(cudaGetLastError());
     count_launches(3);
     AFSAI_TRY(precond(0, st));
-    kb_update_p<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, d_counts + 1);
+    kb_update_p<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, active());
     AFSAI_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     return AFSAI_OK;
@@ -603,6 +654,14 @@ afsai_status BatchEngine::capture(int iters_per_graph, cudaStream_t st) {
     const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     AFSAI_CUDA_TRY(ie);
+    return AFSAI_OK;
+}
+
+afsai_status BatchEngine::refresh_active(cudaStream_t st, bool force) {
+    kb_act_begin<<<1, 32, 0, st>>>(d_counts, force ? 1 : 0);
+    kb_act_build<<<grid_blocks(), kChunk, 0, st>>>(d_sc, d_chunks, d_counts, d_act);
+    AFSAI_CUDA_TRY(cudaGetLastError());
+    count_launches(2);
     return AFSAI_OK;
 }
 
@@ -643,6 +702,7 @@ afsai_status BatchEngine::capture_loop(int iters_per_body, int32_t max_bodies, c
     const int64_t before = launches_so_far();
     afsai_status cap = AFSAI_OK;
     for (int k = 0; k < iters_per_body && cap == AFSAI_OK; ++k) cap = iteration(st);
+    if (cap == AFSAI_OK) cap = refresh_active(st, false);
     if (cap == AFSAI_OK) {
         kb_loop_cond<<<1, 32, 0, st>>>(d_counts, handle, stop_on_retire ? 1 : 0, host_flag);
         count_launches(1);
@@ -659,6 +719,7 @@ afsai_status BatchEngine::capture_loop(int iters_per_body, int32_t max_bodies, c
 }
 
 afsai_status BatchEngine::launch_graph(cudaStream_t st) {
+    AFSAI_TRY(refresh_active(st, true));
     AFSAI_CUDA_TRY(cudaGraphLaunch(exec, st));
     count_launches(per_graph);
     return AFSAI_OK;
@@ -672,7 +733,7 @@ afsai_status BatchEngine::read_active(cudaStream_t st, int32_t* active) {
 }
 
 afsai_status BatchEngine::finish(cudaStream_t st, int only_done) {
-    kb_true_residual<<<grid_blocks(), kChunk, 0, st>>>(d_sys, d_sc, d_chunks, d_counts + 1, d_partials, only_done);
+    kb_true_residual<<<grid_blocks(), kChunk, 0, st>>>(d_sys, d_sc, d_chunks, all(), d_partials, only_done);
     AFSAI_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     return AFSAI_OK;
