@@ -2131,7 +2131,11 @@ afsai_status run_stepwise(const SetupArgs& o, int64_t mcap, int ht, int32_t kite
                         : (ht == 256 ? run_stepwise_t<20, 256, false, true, 2>(o, kiter, st)
                                      : run_stepwise_t<20, 512, false, true, 2>(o, kiter, st));
     }
-    if (chol32) return fail(AFSAI_ENOTSUP, "small-pattern stepwise path: FP64 only");
+    // FP32 Cholesky + FP64 refinement (the mixed form): 4 lanes per row
+    if (chol32 && mcap <= 20)
+        return ht == 256 ? run_stepwise_t<20, 256, true, true, 4>(o, kiter, st)
+                         : run_stepwise_t<20, 512, true, true, 4>(o, kiter, st);
+    if (chol32) return fail(AFSAI_ENOTSUP, "small-pattern stepwise path: up to 20 entries");
     if (mcap <= 12)
         return ht == 256 ? run_stepwise_t<12, 256, false>(o, kiter, st) : run_stepwise_t<12, 512, false>(o, kiter, st);
     if (mcap <= 20)
@@ -2376,7 +2380,7 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
         else
             AFSAI_TRY(lane_ht == 64 ? (run_stepwise_lane<12, 2, false, 64>(a, p->kiter, st))
                                     : (run_stepwise_lane<12, 2, false>(a, p->kiter, st)));
-    } else if (!fused_only && stepwise_supported(mcap) && !chol32)
+    } else if (!fused_only && stepwise_supported(mcap))
         AFSAI_TRY(run_stepwise(a, mcap, ht, p->kiter, chol32, st, cand_bound));
     else if (!fused_only && (wide_lpr == 4 || wide_lpr == 8) && mcap > 20 && mcap <= 32 && (!chol32 || wide_mixed))
         AFSAI_TRY(run_stepwise_wide(a, ht, wide_lpr, p->kiter, chol32, st));

@@ -238,3 +238,43 @@ def test_setup_paths_bit_identical(gpu, env):
     out = subprocess.run([sys.executable, "-c", _PATH_SCRIPT.format(root=root)], env={**os.environ, **env},
                          capture_output=True, text=True, timeout=600)
     assert out.returncode == 0 and out.stdout.strip().endswith("ok"), out.stderr[-2000:]
+
+
+_MIXED_SCRIPT = r"""
+import hashlib
+import sys
+import numpy as np
+sys.path.insert(0, {root!r})
+from paper_2010_14175_gb300 import afsai, matgen as mg
+afsai.load()
+cases = [(mg.stencil27_fe(9, 8, 7, scale=(1.0, 1.0, 100.0)), 8, 2), (mg.elasticity_hex(4, 17), 5, 3),
+         (mg.poisson7(13, 7, 11), 5, 2)]
+h = hashlib.sha256()
+for A, kiter, s in cases:
+    M = afsai.afsai_setup(afsai.DeviceCSR.from_host(A), afsai.params(kiter, s, 1e-3, 0, 1, 1))
+    rp, ci, va = M.export()
+    psi, steps = M.rows()
+    M.close()
+    for arr in (rp, ci, va, psi, steps):
+        h.update(np.ascontiguousarray(arr).tobytes())
+print(h.hexdigest())
+"""
+
+
+def test_mixed_form_paths_bit_identical(gpu):
+    """The mixed form (FP32 Cholesky + one FP64 refinement step) gives the
+    same G on every set-up path: the stepwise kernels (the table gather with
+    the FP32-Cholesky solve for 27-point and elasticity rows, the lane path
+    for the 7-point stencil) against the fused kernel, bit for bit."""
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    digests = []
+    for env in ({}, {"AFSAI_SETUP_FUSED_ONLY": "1"}):
+        out = subprocess.run([sys.executable, "-c", _MIXED_SCRIPT.format(root=root)], env={**os.environ, **env},
+                             capture_output=True, text=True, timeout=600)
+        assert out.returncode == 0, out.stderr[-2000:]
+        digests.append(out.stdout.strip().splitlines()[-1])
+    assert digests[0] == digests[1]
