@@ -105,8 +105,14 @@ __device__ __forceinline__ double row_f64(const int32_t* __restrict__ rp, const 
 }
 
 // ---- init: r = b - A x, bb, rr ------------------------------------------
+// r32: the G product accumulates in FP32 and reads an FP32 copy of r, kept
+// in the second half of the system's t slot (n doubles; t itself takes the
+// first n floats): rounded once per element here instead of once per entry
+// of G in the product (a double-to-float conversion runs on the FP64 pipe).
+__device__ __forceinline__ float* r32_of(const BSys& sy) { return static_cast<float*>(sy.t) + sy.n; }
+
 __global__ void kb_init(const BSys* __restrict__ sys, BScal* sc, const BChunk* __restrict__ chunks,
-                        ChunkList L, double* partials, double* partials2) {
+                        ChunkList L, double* partials, double* partials2, int r32) {
     __shared__ double sh[32];
     for (int32_t k = blockIdx.x; k < *L.count; k += gridDim.x) {
         const int32_t c = L.act ? L.act[k] : k;
@@ -119,6 +125,7 @@ __global__ void kb_init(const BSys* __restrict__ sys, BScal* sc, const BChunk* _
         if (i < ch.row1) {
             const double ri = sy.b[i] - row_f64(sy.Arp, sy.Acol, sy.Aval, sy.x, i);
             sy.r[i] = ri;
+            if (r32) r32_of(sy)[i] = static_cast<float>(ri);
             rr = ri * ri;
             bb = sy.b[i] * sy.b[i];
         }
@@ -146,7 +153,7 @@ __global__ void kb_init(const BSys* __restrict__ sys, BScal* sc, const BChunk* _
 // ---- t = G r --------------------------------------------------------------
 template <typename VT, typename TT>
 __device__ __forceinline__ TT row_G(const int32_t* __restrict__ rp, const int32_t* __restrict__ col,
-                                    const VT* __restrict__ val, const double* __restrict__ x, int32_t i) {
+                                    const VT* __restrict__ val, const TT* __restrict__ x, int32_t i) {
     if constexpr (sizeof(TT) == 8) {
         double acc = 0.0;
         for (int32_t k = rp[i]; k < rp[i + 1]; ++k)
@@ -154,8 +161,7 @@ __device__ __forceinline__ TT row_G(const int32_t* __restrict__ rp, const int32_
         return acc;
     } else {
         float acc = 0.0f;
-        for (int32_t k = rp[i]; k < rp[i + 1]; ++k)
-            acc = fmaf(vf<VT>(val[k]), static_cast<float>(__ldg(&x[__ldg(&col[k])])), acc);
+        for (int32_t k = rp[i]; k < rp[i + 1]; ++k) acc = fmaf(vf<VT>(val[k]), __ldg(&x[__ldg(&col[k])]), acc);
         return acc;
     }
 }
@@ -182,8 +188,14 @@ __global__ void kb_G(const BSys* __restrict__ sys, const BScal* sc, const BChunk
         if (init ? !sc[ch.sys].fresh : (sc[ch.sys].done != 0)) continue;
         const BSys& sy = sys[ch.sys];
         const int32_t i = ch.row0 + threadIdx.x;
-        if (i < ch.row1)
-            static_cast<TT*>(sy.t)[i] = row_G<VT, TT>(sy.Grp, sy.Gcol, static_cast<const VT*>(sy.Gval), sy.r, i);
+        if (i < ch.row1) {
+            const TT* rin;
+            if constexpr (sizeof(TT) == sizeof(float))
+                rin = r32_of(sy);
+            else
+                rin = sy.r;
+            static_cast<TT*>(sy.t)[i] = row_G<VT, TT>(sy.Grp, sy.Gcol, static_cast<const VT*>(sy.Gval), rin, i);
+        }
     }
 }
 
@@ -264,7 +276,7 @@ __global__ void kb_A_dot(const BSys* __restrict__ sys, BScal* sc, const BChunk* 
 
 // ---- x += alpha p, r -= alpha q, rr, convergence --------------------------
 __global__ void kb_update_xr(const BSys* __restrict__ sys, BScal* sc, const BChunk* __restrict__ chunks,
-                             ChunkList L, double* partials) {
+                             ChunkList L, double* partials, int r32) {
     __shared__ double sh[32];
     for (int32_t k = blockIdx.x; k < *L.count; k += gridDim.x) {
         const int32_t c = L.act ? L.act[k] : k;
@@ -279,6 +291,7 @@ __global__ void kb_update_xr(const BSys* __restrict__ sys, BScal* sc, const BChu
             sy.x[i] = fma(alpha, sy.p[i], sy.x[i]);
             const double ri = fma(-alpha, sy.q[i], sy.r[i]);
             sy.r[i] = ri;
+            if (r32) r32_of(sy)[i] = static_cast<float>(ri);
             part = ri * ri;
         }
         const double tp = chunk_sum(part, sh);
@@ -571,7 +584,7 @@ afsai_status BatchEngine::precond(int init, cudaStream_t st) {
 
 afsai_status BatchEngine::start(cudaStream_t st) {
     const int gb = grid_blocks();
-    kb_init<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, all(), d_partials, d_partials2);
+    kb_init<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, all(), d_partials, d_partials2, vtype != VAL_F64);
     AFSAI_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     AFSAI_TRY(precond(1, st));
@@ -621,7 +634,7 @@ afsai_status BatchEngine::set_scalars(int32_t slot, const BScal& sc_in, cudaStre
 afsai_status BatchEngine::iteration(cudaStream_t st) {
     const int gb = grid_blocks();
     kb_A_dot<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, active(), d_partials);
-    kb_update_xr<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, active(), d_partials);
+    kb_update_xr<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, active(), d_partials, vtype != VAL_F64);
     kb_true_check<<<gb, kChunk, 0, st>>>(d_sys, d_sc, d_chunks, active(), d_partials);
     AFSAI_CUDA_TRY(cudaGetLastError());
     count_launches(3);

@@ -116,12 +116,14 @@ __device__ __forceinline__ void abort_solve(Scalars* s) {
 
 // ---- init: r = b - q (q = A x), rr = r.r, bb = b.b ----------------------
 __global__ void k_init_residual(int32_t n, const double* __restrict__ b, const double* __restrict__ q,
-                                double* __restrict__ r, Scalars* s, double* partials, double rtol) {
+                                double* __restrict__ r, float* __restrict__ r32, Scalars* s, double* partials,
+                                double rtol) {
     double v[2] = {0.0, 0.0};
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const double ri = b[i] - q[i];
         r[i] = ri;
+        if (r32) r32[i] = static_cast<float>(ri);
         v[0] = fma(ri, ri, v[0]);
         v[1] = fma(b[i], b[i], v[1]);
     }
@@ -185,7 +187,7 @@ __global__ void k_spmv_A_dot(int32_t n, int64_t nnz, const int32_t* __restrict__
 // thread in flight; the per-thread dot partial runs over its elements in
 // index order.
 __global__ void k_update_xr(int32_t n, double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
-                            const double* __restrict__ q, Scalars* s, double* partials) {
+                            const double* __restrict__ q, float* __restrict__ r32, Scalars* s, double* partials) {
     if (s->done) return;
     const double alpha = s->alpha;
     double v[1] = {0.0};
@@ -209,6 +211,8 @@ __global__ void k_update_xr(int32_t n, double* __restrict__ x, double* __restric
             rv.y = fma(-alpha, qv.y, rv.y);
             x2[k] = xv;
             r2[k] = rv;
+            if (r32)
+                reinterpret_cast<float2*>(r32)[k] = make_float2(static_cast<float>(rv.x), static_cast<float>(rv.y));
             v[0] = fma(rv.x, rv.x, v[0]);
             v[0] = fma(rv.y, rv.y, v[0]);
         }
@@ -217,6 +221,7 @@ __global__ void k_update_xr(int32_t n, double* __restrict__ x, double* __restric
             x[i] = fma(alpha, p[i], x[i]);
             const double ri = fma(-alpha, q[i], r[i]);
             r[i] = ri;
+            if (r32) r32[i] = static_cast<float>(ri);
             v[0] = fma(ri, ri, v[0]);
         }
     } else {
@@ -224,6 +229,7 @@ __global__ void k_update_xr(int32_t n, double* __restrict__ x, double* __restric
             x[i] = fma(alpha, p[i], x[i]);
             const double ri = fma(-alpha, q[i], r[i]);
             r[i] = ri;
+            if (r32) r32[i] = static_cast<float>(ri);
             v[0] = fma(ri, ri, v[0]);
         }
     }
@@ -237,14 +243,18 @@ __global__ void k_update_xr(int32_t n, double* __restrict__ x, double* __restric
     }
 }
 
-// ---- t = G r (ACC/YT: double for an FP64 G, float otherwise) ---------------
+// ---- t = G r (ACC: double for an FP64 G, float otherwise; r in ACC too:
+// with FP32 accumulation the solve keeps an FP32 copy of r, rounded once
+// per element where the residual is written, instead of rounding each
+// gathered double in the product: a double-to-float conversion runs on
+// the FP64 pipe, and one per entry of G kept that pipe 85% busy) ----------
 template <int MODE, typename VT, typename ACC>
 __global__ void k_spmv_G(int32_t n, int64_t nnz, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                         const VT* __restrict__ val, const double* __restrict__ r, ACC* __restrict__ t, Scalars* s,
+                         const VT* __restrict__ val, const ACC* __restrict__ r, ACC* __restrict__ t, Scalars* s,
                          int cap, int init, tiled::SellView sv, long long wait) {
     if (!init && s->done) return;
     EpiStore<ACC, ACC> epi{t};
-    if (!tiled::spmv_rows<MODE, VT, double, ACC>(n, nnz, rowptr, col, val, r, cap, &s->err, epi, sv, wait))
+    if (!tiled::spmv_rows<MODE, VT, ACC, ACC>(n, nnz, rowptr, col, val, r, cap, &s->err, epi, sv, wait))
         abort_solve(s);
 }
 
@@ -383,6 +393,7 @@ struct Launcher {
     const CsrDev* A;
     const afsai_precond* M;
     double *x, *r, *p, *q, *z, *t;
+    float* r32 = nullptr;  // FP32 copy of r for an FP32-accumulated G product (in t's slot)
     const double* b;
     Scalars* s;
     double* partials;
@@ -420,7 +431,7 @@ struct Launcher {
                 constexpr int MD = decltype(Mc)::value;
                 fit(k_spmv_G<MD, VT, ACC>, m);
                 k_spmv_G<MD, VT, ACC><<<m.blocks, m.threads, m.smem, s2>>>(
-                    G.n, G.nnz, G.rowptr, G.col, static_cast<const VT*>(G.val), static_cast<const double*>(x),
+                    G.n, G.nnz, G.rowptr, G.col, static_cast<const VT*>(G.val), static_cast<const ACC*>(x),
                     static_cast<ACC*>(y), ts, m.cap, 1, tiled::sell_view(G.sell), tiled::kWaitCycles);
             }))
             return fail(AFSAI_EINVAL, "unknown SpMV mode");
@@ -445,6 +456,7 @@ struct Launcher {
     template <typename VT, typename ACC>
     afsai_status plan_G(Scalars* ts) {
         RoleLaunch lg, lt;
+        lg.x_float = sizeof(ACC) == sizeof(float);
         lg.launch = [&](const SpmvMode& m, const void* x, void* y, cudaStream_t s2) {
             return tune_G<VT, ACC>(m, x, y, s2, ts);
         };
@@ -521,9 +533,14 @@ struct Launcher {
     template <typename VT, typename ACC>
     void launch_G_pair(const CsrDev& G, const CsrDev& Gt, int init) {
         ACC* tt = reinterpret_cast<ACC*>(t);
+        const ACC* rin;
+        if constexpr (sizeof(ACC) == sizeof(float))
+            rin = r32;
+        else
+            rin = r;
         with_mode(mg.mode, [&](auto Mc) {
             k_spmv_G<decltype(Mc)::value, VT, ACC><<<mg.blocks, mg.threads, mg.smem, st>>>(
-                G.n, G.nnz, G.rowptr, G.col, static_cast<const VT*>(G.val), r, tt, s, mg.cap, init,
+                G.n, G.nnz, G.rowptr, G.col, static_cast<const VT*>(G.val), rin, tt, s, mg.cap, init,
                 tiled::sell_view(G.sell), wait);
         });
         mark(3);
@@ -560,7 +577,7 @@ struct Launcher {
     afsai_status head() {
         AFSAI_TRY(spmv_A_dot());
         mark(1);
-        k_update_xr<<<vec_blocks(n), kThreads, 0, st>>>(n, x, r, p, q, s, partials);
+        k_update_xr<<<vec_blocks(n), kThreads, 0, st>>>(n, x, r, p, q, r32, s, partials);
         AFSAI_CUDA_TRY(cudaGetLastError());
         count_launches(1);
         mark(2);
@@ -649,6 +666,9 @@ afsai_status pcg_body(const CsrDev& Ain, const afsai_precond* M, const double* b
     L.q = vec.p + 2 * vs;
     L.z = vec.p + 3 * vs;
     L.t = vec.p + 4 * vs;
+    // t's slot holds vs doubles; with an FP32-accumulated G product t uses
+    // its first n floats and the FP32 copy of r starts at float vs
+    if (M && M->G.vtype != VAL_F64 && !acc64()) L.r32 = reinterpret_cast<float*>(L.t) + vs;
     L.s = sc.p;
     L.partials = partials.p;
     L.st = st;
@@ -661,7 +681,7 @@ afsai_status pcg_body(const CsrDev& Ain, const afsai_precond* M, const double* b
     AFSAI_CUDA_TRY(cudaEventRecord(ev0, st));
     // r = b - A x ; z = M r ; p = z
     AFSAI_TRY(spmv_csr(A, x, L.q, st));
-    k_init_residual<<<vec_blocks(n), kThreads, 0, st>>>(n, b, L.q, L.r, sc.p, partials.p, rtol);
+    k_init_residual<<<vec_blocks(n), kThreads, 0, st>>>(n, b, L.q, L.r, L.r32, sc.p, partials.p, rtol);
     AFSAI_CUDA_TRY(cudaGetLastError());
     AFSAI_TRY(L.precond_dot(1));
     k_init_p<<<vec_blocks(n), kThreads, 0, st>>>(n, L.r, L.z, L.p, sc.p, partials.p);
