@@ -672,13 +672,19 @@ def run_serve(args, rank, world, local):
                 time.sleep(0.0005)
         return done
 
-    # capacity: saturate the server (all matrices' G built by a first pass)
+    # capacity: saturate the server (all matrices' G built by a first pass);
+    # one untimed burst, then the median of three timed bursts of 256
+    # requests (a single burst varied by 1.5x from run to run, and the
+    # arrival rate, hence the load, follows it)
     drain([S.submit(ids[m], np.ones(pool[m].n)) for m in range(len(pool))])
-    burst = [make_request() for _ in range(256)]
-    t0 = time.perf_counter()
-    res = drain([S.submit(ids[m], b) for m, b in burst])
-    cap_s = time.perf_counter() - t0
-    capacity = sum(b.shape[0] for _, b in burst) / cap_s  # solves/s
+    caps = []
+    for k in range(4):
+        burst = [make_request() for _ in range(256)]
+        t0 = time.perf_counter()
+        drain([S.submit(ids[m], b) for m, b in burst])
+        if k > 0:
+            caps.append(sum(b.shape[0] for _, b in burst) / (time.perf_counter() - t0))
+    capacity = float(np.median(caps))  # solves/s
     mean_rhs = 4.5
     lam = 0.7 * capacity / mean_rhs  # requests/s
     clocks = ClockSampler(local)

@@ -79,7 +79,11 @@ struct BatchEngine {
     int32_t* h_counts = nullptr;  // pinned
     int32_t* d_act = nullptr;     // chunks of the running systems
     ChunkList all() const { return ChunkList{nullptr, d_counts + 1}; }
-    ChunkList active() const { return ChunkList{d_act, d_counts + 4}; }
+    ChunkList active() const { return use_act ? ChunkList{d_act, d_counts + 4} : all(); }
+    // The solve server rebuilds the chunk table of running systems before
+    // every launch and ends a launch on any retirement, so it keeps the
+    // whole table (use_act = false; set before capture_loop).
+    bool use_act = true;
     // The running systems' chunks listed again (forced, or when a system
     // finished since the last listing): the iteration kernels then skip no
     // chunk of a finished system, which at the tail of an uneven batch (a

@@ -715,7 +715,7 @@ afsai_status BatchEngine::capture_loop(int iters_per_body, int32_t max_bodies, c
     const int64_t before = launches_so_far();
     afsai_status cap = AFSAI_OK;
     for (int k = 0; k < iters_per_body && cap == AFSAI_OK; ++k) cap = iteration(st);
-    if (cap == AFSAI_OK) cap = refresh_active(st, false);
+    if (cap == AFSAI_OK && use_act) cap = refresh_active(st, false);
     if (cap == AFSAI_OK) {
         kb_loop_cond<<<1, 32, 0, st>>>(d_counts, handle, stop_on_retire ? 1 : 0, host_flag);
         count_launches(1);
@@ -732,7 +732,7 @@ afsai_status BatchEngine::capture_loop(int iters_per_body, int32_t max_bodies, c
 }
 
 afsai_status BatchEngine::launch_graph(cudaStream_t st) {
-    AFSAI_TRY(refresh_active(st, true));
+    if (use_act) AFSAI_TRY(refresh_active(st, true));
     AFSAI_CUDA_TRY(cudaGraphLaunch(exec, st));
     count_launches(per_graph);
     return AFSAI_OK;

@@ -136,6 +136,7 @@ struct ServerImpl {
         AFSAI_CUDA_TRY(cudaHostAlloc(reinterpret_cast<void**>(&arrival_flag), sizeof(int32_t), cudaHostAllocMapped));
         *arrival_flag = 0;
         AFSAI_CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&arrival_flag_dev), arrival_flag, 0));
+        E.use_act = false;
         AFSAI_TRY(E.capture_loop(iters_per_step, max_bodies, st, true, arrival_flag_dev));
         return AFSAI_OK;
     }
