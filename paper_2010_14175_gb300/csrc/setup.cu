@@ -1385,25 +1385,53 @@ __global__ void __launch_bounds__(128) step_gather_lane(StepArgs a) {
 // its pattern: entry (P_t, c) of A with c <= P_t and c in P goes to packed
 // position tri(t) + pos(c) (the gather of the plain definition; only the
 // lower part of each row is read).  The LPR lanes of the row split the
-// rows of P; rows of A have at most kLaneRowMax entries here.
-template <int LPR, typename F>
+// rows of P; rows of A have at most kLaneRowMax entries here.  Each lane
+// first loads the row pointers of all its rows of P, then the entries of
+// two rows at a time, so that its global loads are issued in a few
+// independent batches rather than as one dependent chain per row (the
+// kernel's shared memory, not its registers, bounds its occupancy).  Every
+// entry has its own position, so the order of the puts changes nothing.
+template <int LPR, int MC, typename F>
 __device__ __forceinline__ void gather_rows_lower(const StepArgs& a, const int32_t* Ps, int m, int sub, F&& put) {
-    for (int t = sub; t < m; t += LPR) {
-        const int32_t pr = Ps[t];
-        const int32_t rb = __ldg(&a.rowptr[pr]), re = __ldg(&a.rowptr[pr + 1]);
-        int32_t c[kLaneRowMax];
-        double v[kLaneRowMax];
+    constexpr int NT = (MC + LPR - 1) / LPR;  // rows of P per lane, at most
+    constexpr int NT2 = (NT + 1) / 2 * 2;
+    int32_t rb[NT2], re[NT2];
 #pragma unroll
-        for (int q = 0; q < kLaneRowMax; ++q) {
-            const bool on = rb + q < re;
-            c[q] = on ? __ldg(&a.col[rb + q]) : INT_MAX;
-            v[q] = on ? __ldg(&a.val[rb + q]) : 0.0;
+    for (int j = 0; j < NT2; ++j) {
+        const int t = sub + j * LPR;
+        rb[j] = 0;
+        re[j] = 0;
+        if (j < NT && t < m) {
+            const int32_t pr = Ps[t];
+            rb[j] = __ldg(&a.rowptr[pr]);
+            re[j] = __ldg(&a.rowptr[pr + 1]);
         }
+    }
 #pragma unroll
-        for (int q = 0; q < kLaneRowMax; ++q) {
-            if (c[q] <= pr) {
-                const int pc = find_sorted(Ps, t + 1, c[q]);
-                if (pc >= 0) put(tri(t) + pc, v[q]);
+    for (int j = 0; j < NT2; j += 2) {
+        if (sub + j * LPR >= m) break;
+        int32_t c[2][kLaneRowMax];
+        double v[2][kLaneRowMax];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int q = 0; q < kLaneRowMax; ++q) {
+                const bool on = rb[j + u] + q < re[j + u];
+                c[u][q] = on ? __ldg(&a.col[rb[j + u] + q]) : INT_MAX;
+                v[u][q] = on ? __ldg(&a.val[rb[j + u] + q]) : 0.0;
+            }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int t = sub + (j + u) * LPR;
+            if (t < m) {
+                const int32_t pr = Ps[t];
+#pragma unroll
+                for (int q = 0; q < kLaneRowMax; ++q) {
+                    if (c[u][q] <= pr) {
+                        const int pc = find_sorted(Ps, t + 1, c[u][q]);
+                        if (pc >= 0) put(tri(t) + pc, v[u][q]);
+                    }
+                }
             }
         }
     }
@@ -1540,7 +1568,7 @@ __global__ void __launch_bounds__(128) step_solve_wide(StepArgs a) {
                 for (int t = sub; t < tri(m); t += LPR) M[t] = 0.0;
             }
             __syncwarp();
-            if (row) gather_rows_lower<LPR>(a, Ps, m, sub, [&](int idx, double v) { M[idx] = v; });
+            if (row) gather_rows_lower<LPR, MC>(a, Ps, m, sub, [&](int idx, double v) { M[idx] = v; });
         } else {
             // load the warp's triangles, one row at a time with all lanes
             for (int q = 0; q < RPW; ++q) {
@@ -1672,7 +1700,7 @@ __global__ void __launch_bounds__(128) step_solve_wide32(StepArgs a) {
             }
             __syncwarp();
             if (row)
-                gather_rows_lower<LPR>(a, Ps, m, sub, [&](int idx, double v) {
+                gather_rows_lower<LPR, MC>(a, Ps, m, sub, [&](int idx, double v) {
                     M[idx] = v;
                     L[idx] = static_cast<float>(v);
                 });
