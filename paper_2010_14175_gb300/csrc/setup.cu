@@ -1989,14 +1989,89 @@ afsai_status run_stepwise_t(const SetupArgs& o, int32_t kiter, cudaStream_t st) 
     return AFSAI_OK;
 }
 
+// Warps per block (1, 2 or 4) that maximise the resident warps per SM for a
+// kernel using per_warp bytes of shared memory per warp plus fixed bytes.
+int lane_best_wpb(size_t per_warp, size_t fixed) {
+    int wpb = 1, best = 0;
+    for (int cand = 1; cand <= 4; cand *= 2) {
+        const size_t blk = per_warp * cand + fixed + 1024;
+        if (blk > 200u * 1024u) break;
+        const int warps = static_cast<int>((227u * 1024u) / blk) * cand;
+        if (warps > best) {
+            best = warps;
+            wpb = cand;
+        }
+    }
+    return wpb;
+}
+
+// Launch plan of the small-stencil solve kernel for patterns of at most MCS
+// entries (its shared memory grows with MCS, so early steps, whose patterns
+// are small, run with a smaller capacity and more resident warps).
+template <int MCS, int LPR, bool CHOL32, bool SQRT_INT>
+struct LaneSolvePlan {
+    void (*k)(StepArgs) = nullptr;
+    size_t smem = 0;
+    int wpb = 1;
+    int blocks = 1;
+    afsai_status plan(int32_t n) {
+        constexpr int TMC = MCS * (MCS + 1) / 2;
+        if constexpr (CHOL32)
+            k = step_solve_wide32<MCS, LPR, true>;
+        else
+            k = step_solve_wide<MCS, LPR, true, SQRT_INT>;
+        constexpr int RPW = 32 / LPR;
+        const size_t per_row = CHOL32 ? ((TMC + MCS + (MCS + 1) / 2) | 1) * sizeof(double) +
+                                            (((TMC + MCS) | 1) + 1) * sizeof(float)
+                                      : ((TMC + 2 * MCS + (MCS + 1) / 2) | 1) * sizeof(double);
+        const size_t per_warp = per_row * RPW;
+        const size_t pair_bytes = (sizeof(uint16_t) * TMC + 15) / 16 * 16;
+        wpb = lane_best_wpb(per_warp, pair_bytes);
+        smem = per_warp * wpb + pair_bytes;
+        AFSAI_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        int per_sm = 0;
+        AFSAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * wpb, smem));
+        if (per_sm < 1) return fail(AFSAI_ENOTSUP, "stepwise set-up does not fit in shared memory");
+        blocks = std::max(1, std::min(per_sm * num_sms(), ceil_div(ceil_div(n, RPW), wpb)));
+        return AFSAI_OK;
+    }
+    void launch(const StepArgs& a, cudaStream_t st) const { k<<<blocks, 32 * wpb, smem, st>>>(a); }
+};
+
+// Launch plan of the lane-per-row gather kernel with HTS table slots.
+template <int MC, int HTS>
+struct LaneGatherPlan {
+    void (*k)(StepArgs) = nullptr;
+    size_t smem = 0;
+    int wpb = 1;
+    int blocks = 1;
+    afsai_status plan(int32_t n) {
+        k = step_gather_lane<MC, HTS>;
+        const size_t per_warp = static_cast<size_t>(HTS * 12 + MC * 4) * 32;
+        wpb = lane_best_wpb(per_warp, 0);
+        smem = per_warp * wpb;
+        AFSAI_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+        int per_sm = 0;
+        AFSAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 32 * wpb, smem));
+        if (per_sm < 1) return fail(AFSAI_ENOTSUP, "stepwise set-up does not fit in shared memory");
+        blocks = std::max(1, std::min(per_sm * num_sms(), ceil_div(ceil_div(n, 32), wpb)));
+        return AFSAI_OK;
+    }
+    void launch(const StepArgs& a, cudaStream_t st) const { k<<<blocks, 32 * wpb, smem, st>>>(a); }
+};
+
 // Small stencils (rows of A with at most kLaneRowMax entries, patterns of
 // at most MC entries, s <= 4): the lane-per-row gather kernel and the
 // LPR-lanes-per-row solve kernel that gathers its system from A.  No
-// per-row system slot is allocated.
+// per-row system slot is allocated.  Steps whose patterns hold at most 8
+// entries (1 + k s <= 8) run the solve kernel with that capacity, and
+// steps whose candidates cannot exceed 28 (|P_{k-1}| kLaneRowMax <= 28)
+// run the gather kernel with 32-slot tables: less shared memory per row,
+// more resident warps, the same results (a row's arithmetic does not
+// depend on its table size or on the capacity above its pattern).
 template <int MC, int LPR, bool CHOL32, int HT = kLaneHT, bool SQRT_INT = false>
 afsai_status run_stepwise_lane(const SetupArgs& o, int32_t kiter, cudaStream_t st) {
     const int32_t n = o.n;
-    constexpr int TMC = MC * (MC + 1) / 2;
     DevBuf<int32_t> P, mm, steps, stt;
     DevBuf<double> g, psi, psi0;
     AFSAI_TRY(P.alloc(static_cast<size_t>(n) * MC, st));
@@ -2015,7 +2090,7 @@ afsai_status run_stepwise_lane(const SetupArgs& o, int32_t kiter, cudaStream_t s
     a.exit_mode = o.exit_mode;
     a.eps = o.eps;
     a.mc = MC;
-    a.tmc = TMC;
+    a.tmc = MC * (MC + 1) / 2;
     a.P = P.p;
     a.g = g.p;
     a.M = nullptr;
@@ -2032,55 +2107,43 @@ afsai_status run_stepwise_lane(const SetupArgs& o, int32_t kiter, cudaStream_t s
     step_init<<<vec_blocks, 256, 0, st>>>(a);
     AFSAI_CUDA_TRY(cudaGetLastError());
     count_launches(1);
-    // warps per block (1, 2 or 4) that maximise resident warps per SM
-    auto best_wpb = [](size_t per_warp, size_t fixed) {
-        int wpb = 1, best = 0;
-        for (int cand = 1; cand <= 4; cand *= 2) {
-            const size_t blk = per_warp * cand + fixed + 1024;
-            if (blk > 200u * 1024u) break;
-            const int warps = static_cast<int>((227u * 1024u) / blk) * cand;
-            if (warps > best) {
-                best = warps;
-                wpb = cand;
-            }
-        }
-        return wpb;
-    };
-    auto kg = step_gather_lane<MC, HT>;
-    const size_t per_warp_g = static_cast<size_t>(HT * 12 + MC * 4) * 32;
-    const int wpb_g = best_wpb(per_warp_g, 0);
-    const size_t smem_g = per_warp_g * wpb_g;
-    AFSAI_CUDA_TRY(cudaFuncSetAttribute(kg, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_g)));
-    int per_sm_g = 0;
-    AFSAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_g, kg, 32 * wpb_g, smem_g));
-    auto ks = [] {
-        if constexpr (CHOL32)
-            return step_solve_wide32<MC, LPR, true>;
-        else
-            return step_solve_wide<MC, LPR, true, SQRT_INT>;
-    }();
-    constexpr int RPW = 32 / LPR;
-    const size_t per_row = CHOL32 ? ((TMC + MC + (MC + 1) / 2) | 1) * sizeof(double) +
-                                        (((TMC + MC) | 1) + 1) * sizeof(float)
-                                  : ((TMC + 2 * MC + (MC + 1) / 2) | 1) * sizeof(double);
-    const size_t per_warp_s = per_row * RPW;
-    const size_t pair_bytes = (sizeof(uint16_t) * TMC + 15) / 16 * 16;
-    const int wpb_s = best_wpb(per_warp_s, pair_bytes);
-    const size_t smem_s = per_warp_s * wpb_s + pair_bytes;
-    AFSAI_CUDA_TRY(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem_s)));
-    int per_sm_s = 0;
-    AFSAI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_s, ks, 32 * wpb_s, smem_s));
-    if (per_sm_s < 1 || per_sm_g < 1) return fail(AFSAI_ENOTSUP, "stepwise set-up does not fit in shared memory");
-    const int blocks_g = std::max(1, std::min(per_sm_g * num_sms(), ceil_div(ceil_div(n, 32), wpb_g)));
-    const int blocks_s = std::max(1, std::min(per_sm_s * num_sms(), ceil_div(ceil_div(n, RPW), wpb_s)));
+    LaneGatherPlan<MC, HT> gather;
+    AFSAI_TRY(gather.plan(n));
+    LaneSolvePlan<MC, LPR, CHOL32, SQRT_INT> solve;
+    AFSAI_TRY(solve.plan(n));
+    // the smaller variants (only when they are smaller)
+    constexpr int kSmallMC = MC > 8 ? 8 : MC;
+    constexpr int kSmallHT = HT > 32 ? 32 : HT;
+    LaneGatherPlan<MC, kSmallHT> gather_small;
+    LaneSolvePlan<kSmallMC, LPR, CHOL32, SQRT_INT> solve_small;
+    if (kSmallHT < HT) AFSAI_TRY(gather_small.plan(n));
+    if (kSmallMC < MC) AFSAI_TRY(solve_small.plan(n));
     DevBuf<int32_t> lists, counts;
     if (kiter > 1) {
         AFSAI_TRY(lists.alloc(2 * static_cast<size_t>(n), st));
         AFSAI_TRY(counts.alloc(2, st));
     }
+    // AFSAI_LANE_SMALL: bit 0 the small gather tables, bit 1 the small solve
+    // capacity.  Default (measured on the 256^3 diffusion set-up): both for
+    // the FP64 Cholesky (107.9 -> 102.7 ms); the tables only for the FP32
+    // Cholesky of patterns up to 12 entries (93.9 -> 93.0 ms; with the small
+    // solve too 95.6 ms)
+    static const int small_env = [] {
+        const char* e = std::getenv("AFSAI_LANE_SMALL");
+        return e ? std::atoi(e) : -1;
+    }();
+    const int small_mask = small_env >= 0 ? small_env : ((CHOL32 && MC <= 12) ? 1 : 3);
     for (int32_t k = 1; k <= kiter; ++k) {
-        kg<<<blocks_g, 32 * wpb_g, smem_g, st>>>(a);
-        ks<<<blocks_s, 32 * wpb_s, smem_s, st>>>(a);
+        const int64_t prev = 1 + static_cast<int64_t>(k - 1) * o.s;  // |P_{k-1}| at most
+        const int64_t next = prev + o.s;                              // |P_k| at most
+        if ((small_mask & 1) && kSmallHT < HT && prev * kLaneRowMax <= kSmallHT - (kSmallHT >> 3))
+            gather_small.launch(a, st);
+        else
+            gather.launch(a, st);
+        if ((small_mask & 2) && kSmallMC < MC && next <= kSmallMC)
+            solve_small.launch(a, st);
+        else
+            solve.launch(a, st);
         AFSAI_CUDA_TRY(cudaGetLastError());
         count_launches(2);
         if (k < kiter) AFSAI_TRY(next_active_list(a, lists.p, counts.p, k, vec_blocks, st));

@@ -202,7 +202,9 @@ def test_locality_bound_arguments(gpu):
 
 # Every set-up path must stay bit-identical to the oracle, not only the
 # default one per pattern size: the fused kernel for all sizes, the
-# one-lane-per-row stepwise solve, and the other lane widths.  The path
+# one-lane-per-row stepwise solve, the other lane widths, and the
+# small-stencil kernels at full capacity for every step or with only the
+# smaller solve capacity of the early steps.  The path
 # switches are read once per process, so each runs in a child process.
 _PATH_SCRIPT = r"""
 import sys
@@ -227,8 +229,10 @@ print("ok")
 
 @pytest.mark.parametrize("env", [{"AFSAI_SETUP_FUSED_ONLY": "1"}, {"AFSAI_STEPWISE_SMALL_LPR": "1"},
                                  {"AFSAI_STEPWISE_SMALL_LPR": "4", "AFSAI_STEPWISE_WIDE": "4"},
-                                 {"AFSAI_STEPWISE_WIDE": "0"}],
-                         ids=["fused_only", "lane_per_row", "lpr4_wide4", "wide_off"])
+                                 {"AFSAI_STEPWISE_WIDE": "0"}, {"AFSAI_LANE_SMALL": "0"},
+                                 {"AFSAI_LANE_SMALL": "2"}],
+                         ids=["fused_only", "lane_per_row", "lpr4_wide4", "wide_off", "lane_full_capacity",
+                              "lane_small_solve_only"])
 def test_setup_paths_bit_identical(gpu, env):
     import os
     import subprocess
