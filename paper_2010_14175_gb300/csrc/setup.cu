@@ -831,27 +831,41 @@ afsai_status dispatch(int mcap_t, int ht, int gl, const SetupArgs& a, int64_t nr
     }
 }
 
-// Per-row compaction into CSR with value conversion, plus column counts of
-// G (for the transpose) and the longest row.
+// Per-row compaction into CSR with value conversion, and the longest row.
+// A warp takes 32 consecutive rows, whose CSR entries form one contiguous
+// range: lane l handles entries l, l + 32, ... of the range and finds its
+// row by a binary search over the 32 row starts, so that the writes are
+// coalesced and every lane works whatever the row lengths.
 template <typename VT>
-__global__ void compact_rows_kernel(int32_t n, int64_t mcap, const int32_t* __restrict__ len,
-                                    const int32_t* __restrict__ ocol, const double* __restrict__ oval,
-                                    const int32_t* __restrict__ rowptr, int32_t* __restrict__ col,
-                                    VT* __restrict__ val, int32_t* __restrict__ colcount, int32_t* __restrict__ maxrow) {
+__global__ void __launch_bounds__(256) compact_rows_kernel(int32_t n, int64_t mcap, const int32_t* __restrict__ len,
+                                                           const int32_t* __restrict__ ocol,
+                                                           const double* __restrict__ oval,
+                                                           const int32_t* __restrict__ rowptr,
+                                                           int32_t* __restrict__ col, VT* __restrict__ val,
+                                                           int32_t* __restrict__ maxrow) {
+    __shared__ int32_t srp[8][33];  // row starts of each warp's rows (blockDim.x == 256)
     const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
     const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
     int localmax = 0;
-    for (int64_t i = gw; i < n; i += nw) {
-        const int m = len[i];
-        const int32_t base = rowptr[i];
-        for (int t = lane; t < m; t += 32) {
-            const int32_t c = ocol[i * mcap + t];
-            col[base + t] = c;
-            val[base + t] = static_cast<VT>(oval[i * mcap + t]);
-            atomicAdd(&colcount[c], 1);
+    for (int64_t r0 = gw * 32; r0 < n; r0 += nw * 32) {
+        const int nr = static_cast<int>(n - r0 < 32 ? n - r0 : 32);
+        const int32_t end = rowptr[r0 + nr];
+        srp[w][lane] = lane < nr ? rowptr[r0 + lane] : end;
+        if (lane == 0) srp[w][32] = end;
+        if (lane < nr) localmax = max(localmax, len[r0 + lane]);
+        __syncwarp();
+        for (int32_t k = srp[w][0] + lane; k < end; k += 32) {
+            int q = 0;  // the last row starting at or before k (empty rows are skipped)
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (srp[w][q + step] <= k) q += step;
+            const int64_t src = (r0 + q) * mcap + (k - srp[w][q]);
+            col[k] = ocol[src];
+            val[k] = static_cast<VT>(oval[src]);
         }
-        localmax = m > localmax ? m : localmax;
+        __syncwarp();
     }
     if (lane == 0 && localmax > 0) atomicMax(maxrow, localmax);
 }
@@ -1824,9 +1838,13 @@ __global__ void step_finish(StepArgs a, SetupArgs o) {
         if (stv == kStActive || stv == kStStop) {
             const int m = a.m[i];
             const double sq = sqrt(a.g[i * a.mc + m - 1]);
+            // the row's divisions on the integer pipes (rn::, the IEEE
+            // quotients bit for bit) with one prepared divisor: as FP64
+            // divisions they kept this kernel FP64-pipe bound
+            const rn::Divisor dv = rn::make_divisor(sq);
             for (int t = 0; t < m; ++t) {
                 o.out_col[i * o.mcap + t] = a.P[i * a.mc + t];
-                o.out_val[i * o.mcap + t] = a.g[i * a.mc + t] / sq;
+                o.out_val[i * o.mcap + t] = rn::div_rn(a.g[i * a.mc + t], dv);
             }
             o.out_len[i] = m;
             o.psi[i] = a.psi[i];
@@ -2538,23 +2556,19 @@ afsai_status setup_impl(const afsai_csr* A, const afsai_params* p, int32_t max_r
     G.nnz = nnz;
     AFSAI_CUDA_TRY(lib_malloc_async(reinterpret_cast<void**>(&G.col), sizeof(int32_t) * std::max<int64_t>(nnz, 1), st));
     AFSAI_CUDA_TRY(lib_malloc_async(&G.val, val_bytes(G.vtype) * std::max<int64_t>(nnz, 1), st));
-    DevBuf<int32_t> colcount;
-    AFSAI_TRY(colcount.alloc(static_cast<size_t>(n) + 1, st));
-    AFSAI_CUDA_TRY(cudaMemsetAsync(colcount.p, 0, sizeof(int32_t) * (n + 1), st));
     AFSAI_CUDA_TRY(cudaMemsetAsync(counters.p, 0, sizeof(int32_t), st));
     {
-        const int threads = 256;
-        const int blocks = std::max(1, std::min(ceil_div(static_cast<int64_t>(n) * 32, threads), num_sms() * 16));
+        const int threads = 256;  // compact_rows_kernel's shared row starts assume 8 warps
+        const int blocks = std::max(1, std::min(ceil_div(static_cast<int64_t>(n), threads), num_sms() * 16));
         if (G.vtype == VAL_F64)
             compact_rows_kernel<double><<<blocks, threads, 0, st>>>(n, mcap, len.p, ocol.p, oval.p, G.rowptr, G.col,
-                                                                   static_cast<double*>(G.val), colcount.p, counters.p);
+                                                                   static_cast<double*>(G.val), counters.p);
         else if (G.vtype == VAL_F32)
             compact_rows_kernel<float><<<blocks, threads, 0, st>>>(n, mcap, len.p, ocol.p, oval.p, G.rowptr, G.col,
-                                                                  static_cast<float*>(G.val), colcount.p, counters.p);
+                                                                  static_cast<float*>(G.val), counters.p);
         else
             compact_rows_kernel<__nv_bfloat16><<<blocks, threads, 0, st>>>(
-                n, mcap, len.p, ocol.p, oval.p, G.rowptr, G.col, static_cast<__nv_bfloat16*>(G.val), colcount.p,
-                counters.p);
+                n, mcap, len.p, ocol.p, oval.p, G.rowptr, G.col, static_cast<__nv_bfloat16*>(G.val), counters.p);
         AFSAI_CUDA_TRY(cudaGetLastError());
         count_launches(1);
     }

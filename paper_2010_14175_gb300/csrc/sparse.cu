@@ -128,20 +128,38 @@ __global__ void count_cols(const int32_t* __restrict__ col, int64_t nnz, int32_t
         atomicAdd(&cnt[col[e]], 1);
 }
 
+// Each entry (i, j) of G goes to the next free place of row j of G^T.  A
+// warp takes 32 consecutive rows of G, whose entries form one contiguous
+// range: lane l handles entries l, l + 32, ... and finds its row by a
+// binary search over the 32 row starts (coalesced reads, every lane busy
+// whatever the row lengths).
 template <typename VT>
-__global__ void scatter_transpose(int32_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                  const VT* __restrict__ val, const int32_t* __restrict__ trowptr,
-                                  int32_t* __restrict__ fill, int32_t* __restrict__ tcol, VT* __restrict__ tval) {
+__global__ void __launch_bounds__(256) scatter_transpose(int32_t n, const int32_t* __restrict__ rowptr,
+                                                         const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                                         const int32_t* __restrict__ trowptr,
+                                                         int32_t* __restrict__ fill, int32_t* __restrict__ tcol,
+                                                         VT* __restrict__ tval) {
+    __shared__ int32_t srp[8][33];  // row starts of each warp's rows (blockDim.x == 256)
     const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
     const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-    for (int64_t i = gw; i < n; i += nw) {
-        for (int32_t e = rowptr[i] + lane; e < rowptr[i + 1]; e += 32) {
+    for (int64_t r0 = gw * 32; r0 < n; r0 += nw * 32) {
+        const int nr = static_cast<int>(n - r0 < 32 ? n - r0 : 32);
+        const int32_t end = rowptr[r0 + nr];
+        srp[w][lane] = lane < nr ? rowptr[r0 + lane] : end;
+        __syncwarp();
+        for (int32_t e = srp[w][0] + lane; e < end; e += 32) {
+            int q = 0;  // the last row starting at or before e
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+                if (srp[w][q + step] <= e) q += step;
             const int32_t j = col[e];
             const int32_t pos = trowptr[j] + atomicAdd(&fill[j], 1);
-            tcol[pos] = static_cast<int32_t>(i);
+            tcol[pos] = static_cast<int32_t>(r0 + q);
             tval[pos] = val[e];
         }
+        __syncwarp();
     }
 }
 
@@ -280,7 +298,7 @@ static afsai_status transpose_typed(const CsrDev& G, CsrDev* Gt, cudaStream_t st
     int64_t tot = 0;
     AFSAI_TRY(exclusive_scan_i32(cnt.p, Gt->rowptr, n, st, &tot));
     AFSAI_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * (n + 1), st));
-    scatter_transpose<VT><<<grid_for(static_cast<int64_t>(n) * 32, threads), threads, 0, st>>>(
+    scatter_transpose<VT><<<grid_for(n, threads), threads, 0, st>>>(
         n, G.rowptr, G.col, static_cast<const VT*>(G.val), Gt->rowptr, cnt.p, ucol.p, uval.p);
     AFSAI_CUDA_TRY(cudaGetLastError());
     sort_rows_rank<VT><<<grid_for(static_cast<int64_t>(n) * 32, threads), threads, 0, st>>>(
