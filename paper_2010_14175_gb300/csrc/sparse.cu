@@ -167,32 +167,69 @@ __global__ void __launch_bounds__(256) scatter_transpose(int32_t n, const int32_
 // index of G) so that every G^T row is sorted and the SpMV order is fixed.
 // Rank sort: an entry's position is the number of smaller keys in its row
 // (keys are distinct).  Reads from the unsorted copy, writes the final.
+// A warp takes two rows at a time, a half-warp each, when both have at
+// most 16 entries (most rows of G^T); otherwise it sorts the two rows one
+// after the other with all its lanes.
+template <typename VT>
+__device__ __forceinline__ void sort_row_warp(int32_t b, int32_t len, int lane, const int32_t* __restrict__ ucol,
+                                              const VT* __restrict__ uval, int32_t* __restrict__ col,
+                                              VT* __restrict__ val) {
+    if (len <= 32) {
+        const int32_t k = lane < len ? ucol[b + lane] : INT_MAX;
+        int rank = 0;
+        for (int t = 0; t < len; ++t) {
+            const int32_t o = __shfl_sync(kFull, k, t);
+            rank += (o < k);
+        }
+        if (lane < len) {
+            col[b + rank] = k;
+            val[b + rank] = uval[b + lane];
+        }
+    } else {
+        for (int32_t u = lane; u < len; u += 32) {
+            const int32_t k = ucol[b + u];
+            int rank = 0;
+            for (int32_t t = 0; t < len; ++t) rank += (ucol[b + t] < k);
+            col[b + rank] = k;
+            val[b + rank] = uval[b + u];
+        }
+    }
+}
+
 template <typename VT>
 __global__ void sort_rows_rank(int32_t n, const int32_t* __restrict__ rowptr, const int32_t* __restrict__ ucol,
                                const VT* __restrict__ uval, int32_t* __restrict__ col, VT* __restrict__ val) {
     const int lane = threadIdx.x & 31;
+    const int half = lane >> 4;
+    const int hl = lane & 15;
     const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-    for (int64_t j = gw; j < n; j += nw) {
-        const int32_t b = rowptr[j], e = rowptr[j + 1], len = e - b;
-        if (len <= 32) {
-            const int32_t k = lane < len ? ucol[b + lane] : INT_MAX;
+    for (int64_t j0 = gw * 2; j0 < n; j0 += nw * 2) {
+        const int64_t j = j0 + half;
+        int32_t b = 0, len = 0;
+        if (j < n) {
+            b = rowptr[j];
+            len = rowptr[j + 1] - b;
+        }
+        const int32_t lmax = max(len, __shfl_xor_sync(kFull, len, 16));
+        if (lmax <= 16) {
+            // keys past a row's end read as INT_MAX and never count
+            const int32_t k = hl < len ? ucol[b + hl] : INT_MAX;
             int rank = 0;
-            for (int t = 0; t < len; ++t) {
-                const int32_t o = __shfl_sync(kFull, k, t);
+            for (int t = 0; t < lmax; ++t) {
+                const int32_t o = __shfl_sync(kFull, k, t, 16);
                 rank += (o < k);
             }
-            if (lane < len) {
+            if (hl < len) {
                 col[b + rank] = k;
-                val[b + rank] = uval[b + lane];
+                val[b + rank] = uval[b + hl];
             }
         } else {
-            for (int32_t u = lane; u < len; u += 32) {
-                const int32_t k = ucol[b + u];
-                int rank = 0;
-                for (int32_t t = 0; t < len; ++t) rank += (ucol[b + t] < k);
-                col[b + rank] = k;
-                val[b + rank] = uval[b + u];
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                const int32_t bh = __shfl_sync(kFull, b, h * 16);
+                const int32_t lh = __shfl_sync(kFull, len, h * 16);
+                sort_row_warp<VT>(bh, lh, lane, ucol, uval, col, val);
             }
         }
     }
