@@ -2082,7 +2082,8 @@ struct LaneGatherPlan {
 // at most MC entries, s <= 4): the lane-per-row gather kernel and the
 // LPR-lanes-per-row solve kernel that gathers its system from A.  No
 // per-row system slot is allocated.  Steps whose patterns hold at most 8
-// entries (1 + k s <= 8) run the solve kernel with that capacity, and
+// entries (1 + k s <= 8) run the solve kernel with that capacity (then 10
+// or 12 entries, below the full capacity), and
 // steps whose candidates cannot exceed 28 (|P_{k-1}| kLaneRowMax <= 28)
 // run the gather kernel with 32-slot tables: less shared memory per row,
 // more resident warps, the same results (a row's arithmetic does not
@@ -2129,13 +2130,17 @@ afsai_status run_stepwise_lane(const SetupArgs& o, int32_t kiter, cudaStream_t s
     AFSAI_TRY(gather.plan(n));
     LaneSolvePlan<MC, LPR, CHOL32, SQRT_INT> solve;
     AFSAI_TRY(solve.plan(n));
-    // the smaller variants (only when they are smaller)
+    // the smaller variants (only when they are smaller): solve capacities 8
+    // and 10 (patterns of up to 12) or 8 and 12 (up to 20)
     constexpr int kSmallMC = MC > 8 ? 8 : MC;
+    constexpr int kMidMC = MC > 12 ? 12 : (MC > 10 ? 10 : MC);
     constexpr int kSmallHT = HT > 32 ? 32 : HT;
     LaneGatherPlan<MC, kSmallHT> gather_small;
     LaneSolvePlan<kSmallMC, LPR, CHOL32, SQRT_INT> solve_small;
+    LaneSolvePlan<kMidMC, LPR, CHOL32, SQRT_INT> solve_mid;
     if (kSmallHT < HT) AFSAI_TRY(gather_small.plan(n));
     if (kSmallMC < MC) AFSAI_TRY(solve_small.plan(n));
+    if (kMidMC < MC && kMidMC > kSmallMC) AFSAI_TRY(solve_mid.plan(n));
     DevBuf<int32_t> lists, counts;
     if (kiter > 1) {
         AFSAI_TRY(lists.alloc(2 * static_cast<size_t>(n), st));
@@ -2160,6 +2165,8 @@ afsai_status run_stepwise_lane(const SetupArgs& o, int32_t kiter, cudaStream_t s
             gather.launch(a, st);
         if ((small_mask & 2) && kSmallMC < MC && next <= kSmallMC)
             solve_small.launch(a, st);
+        else if ((small_mask & 2) && kMidMC < MC && kMidMC > kSmallMC && next <= kMidMC)
+            solve_mid.launch(a, st);
         else
             solve.launch(a, st);
         AFSAI_CUDA_TRY(cudaGetLastError());
