@@ -2085,7 +2085,8 @@ struct LaneGatherPlan {
 // entries (1 + k s <= 8) run the solve kernel with that capacity (then 10
 // or 12 entries, below the full capacity), and
 // steps whose candidates cannot exceed 28 (|P_{k-1}| kLaneRowMax <= 28)
-// run the gather kernel with 32-slot tables: less shared memory per row,
+// run the gather kernel with 32-slot tables (and steps with at most 42,
+// below 96-slot tables, with 48-slot ones): less shared memory per row,
 // more resident warps, the same results (a row's arithmetic does not
 // depend on its table size or on the capacity above its pattern).
 template <int MC, int LPR, bool CHOL32, int HT = kLaneHT, bool SQRT_INT = false>
@@ -2135,10 +2136,13 @@ afsai_status run_stepwise_lane(const SetupArgs& o, int32_t kiter, cudaStream_t s
     constexpr int kSmallMC = MC > 8 ? 8 : MC;
     constexpr int kMidMC = MC > 12 ? 12 : (MC > 10 ? 10 : MC);
     constexpr int kSmallHT = HT > 32 ? 32 : HT;
+    constexpr int kMidHT = HT > 48 ? 48 : HT;
     LaneGatherPlan<MC, kSmallHT> gather_small;
+    LaneGatherPlan<MC, kMidHT> gather_mid;
     LaneSolvePlan<kSmallMC, LPR, CHOL32, SQRT_INT> solve_small;
     LaneSolvePlan<kMidMC, LPR, CHOL32, SQRT_INT> solve_mid;
     if (kSmallHT < HT) AFSAI_TRY(gather_small.plan(n));
+    if (kMidHT < HT && kMidHT > kSmallHT) AFSAI_TRY(gather_mid.plan(n));
     if (kSmallMC < MC) AFSAI_TRY(solve_small.plan(n));
     if (kMidMC < MC && kMidMC > kSmallMC) AFSAI_TRY(solve_mid.plan(n));
     DevBuf<int32_t> lists, counts;
@@ -2161,6 +2165,8 @@ afsai_status run_stepwise_lane(const SetupArgs& o, int32_t kiter, cudaStream_t s
         const int64_t next = prev + o.s;                              // |P_k| at most
         if ((small_mask & 1) && kSmallHT < HT && prev * kLaneRowMax <= kSmallHT - (kSmallHT >> 3))
             gather_small.launch(a, st);
+        else if ((small_mask & 1) && kMidHT < HT && kMidHT > kSmallHT && prev * kLaneRowMax <= kMidHT - (kMidHT >> 3))
+            gather_mid.launch(a, st);
         else
             gather.launch(a, st);
         if ((small_mask & 2) && kSmallMC < MC && next <= kSmallMC)
