@@ -940,25 +940,40 @@ __device__ __forceinline__ StepRows step_rows(const StepArgs& a) {
 
 // The rows of `in` (every row when `in` is null) that are still active
 // after a step's solve, appended to `out` (*out_count zeroed before).  Each
-// warp keeps the order of its 32 entries; warps append in any order, which
-// changes no result (rows are independent) and keeps runs of neighbouring
-// rows together for the gathers from A.
+// block keeps the order of its blockDim.x entries (warp ballots and a scan
+// of the block's warp counts) and appends them with one atomic (one per
+// warp put every warp of the GPU on the same counter); blocks append in any
+// order, which changes no result (rows are independent) and keeps runs of
+// neighbouring rows together for the gathers from A.  blockDim.x is a
+// multiple of 32, at most 1024.
 __global__ void step_compact(int32_t n, const int32_t* __restrict__ in, const int32_t* __restrict__ in_count,
                              const int32_t* __restrict__ st, int32_t* __restrict__ out, int32_t* out_count) {
+    __shared__ int32_t wbase[32];
+    __shared__ int32_t bbase;
     const int64_t cnt = in ? *in_count : n;
     const int lane = threadIdx.x & 31;
-    const int64_t w0 = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-    for (int64_t w = w0; w * 32 < cnt; w += nw) {
-        const int64_t q = w * 32 + lane;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    for (int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x; t0 < cnt;
+         t0 += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t q = t0 + threadIdx.x;
         const int32_t i = q < cnt ? (in ? in[q] : static_cast<int32_t>(q)) : -1;
         const bool keep = i >= 0 && st[i] == kStActive;
         const unsigned mask = __ballot_sync(0xffffffffu, keep);
-        if (mask == 0u) continue;
-        int32_t base = 0;
-        if (lane == 0) base = atomicAdd(out_count, __popc(mask));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (keep) out[base + __popc(mask & ((1u << lane) - 1u))] = i;
+        if (lane == 0) wbase[warp] = __popc(mask);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int32_t tot = 0;
+            for (int w = 0; w < nwarps; ++w) {
+                const int32_t c = wbase[w];
+                wbase[w] = tot;
+                tot += c;
+            }
+            bbase = tot > 0 ? atomicAdd(out_count, tot) : 0;
+        }
+        __syncthreads();
+        if (keep) out[bbase + wbase[warp] + __popc(mask & ((1u << lane) - 1u))] = i;
+        __syncthreads();  // wbase and bbase are rewritten for the next rows
     }
 }
 
@@ -969,7 +984,7 @@ __global__ void step_init(StepArgs a) {
         for (int32_t e = a.rowptr[i]; e < a.rowptr[i + 1]; ++e)
             if (a.col[e] == i) aii = a.val[e];
         a.P[i * a.mc] = static_cast<int32_t>(i);
-        a.g[i * a.mc] = 1.0 / aii;
+        a.g[i * a.mc] = rn::div_rn(1.0, rn::make_divisor(aii));  // the IEEE quotient, on the integer pipes
         if (a.M) a.M[i * a.tmc] = aii;  // the 1 x 1 system, extended incrementally
         a.m[i] = 1;
         a.steps[i] = 0;
@@ -1873,9 +1888,10 @@ __global__ void k_setup_diagonal(SetupArgs o) {
         for (int32_t e = o.rowptr[i]; e < o.rowptr[i + 1]; ++e)
             if (o.col[e] == i) aii = o.val[e];
         if (positive(aii)) {
-            const double g = 1.0 / aii;
+            // IEEE quotients on the integer pipes (rn::), as in the other paths
+            const double g = rn::div_rn(1.0, rn::make_divisor(aii));
             o.out_col[i * o.mcap] = static_cast<int32_t>(i);
-            o.out_val[i * o.mcap] = g / sqrt(g);
+            o.out_val[i * o.mcap] = rn::div_rn(g, rn::make_divisor(sqrt(g)));
             o.out_len[i] = 1;
             o.psi[i] = aii;
             o.steps[i] = 0;
