@@ -2097,14 +2097,14 @@ struct LaneGatherPlan {
 // Small stencils (rows of A with at most kLaneRowMax entries, patterns of
 // at most MC entries, s <= 4): the lane-per-row gather kernel and the
 // LPR-lanes-per-row solve kernel that gathers its system from A.  No
-// per-row system slot is allocated.  Steps whose patterns hold at most 8
-// entries (1 + k s <= 8) run the solve kernel with that capacity (then 10
-// or 12 entries, below the full capacity), and
-// steps whose candidates cannot exceed 28 (|P_{k-1}| kLaneRowMax <= 28)
-// run the gather kernel with 32-slot tables (and steps with at most 42,
-// below 96-slot tables, with 48-slot ones): less shared memory per row,
-// more resident warps, the same results (a row's arithmetic does not
-// depend on its table size or on the capacity above its pattern).
+// per-row system slot is allocated.  Steps below the full capacity run
+// smaller kernels: the solve kernel compiled for 8 entries when the
+// step's patterns hold at most 8 (1 + k s <= 8), then for 10 (of 12) or
+// 12 (of 20); the gather kernel with 32-slot tables when the step's
+// candidates cannot exceed 28 (|P_{k-1}| kLaneRowMax <= 28), then with
+// 48-slot tables up to 42 below 96-slot ones.  Less shared memory per
+// row, more resident warps, the same results (a row's arithmetic depends
+// neither on its table size nor on the capacity above its pattern).
 template <int MC, int LPR, bool CHOL32, int HT = kLaneHT, bool SQRT_INT = false>
 afsai_status run_stepwise_lane(const SetupArgs& o, int32_t kiter, cudaStream_t st) {
     const int32_t n = o.n;
@@ -2166,11 +2166,12 @@ afsai_status run_stepwise_lane(const SetupArgs& o, int32_t kiter, cudaStream_t s
         AFSAI_TRY(lists.alloc(2 * static_cast<size_t>(n), st));
         AFSAI_TRY(counts.alloc(2, st));
     }
-    // AFSAI_LANE_SMALL: bit 0 the small gather tables, bit 1 the small solve
-    // capacity.  Default (measured on the 256^3 diffusion set-up): both for
-    // the FP64 Cholesky (107.9 -> 102.7 ms); the tables only for the FP32
-    // Cholesky of patterns up to 12 entries (93.9 -> 93.0 ms; with the small
-    // solve too 95.6 ms)
+    // AFSAI_LANE_SMALL: bit 0 the smaller gather tables, bit 1 the smaller
+    // solve capacities.  Default (measured on the 256^3 diffusion set-up):
+    // both for the FP64 Cholesky (107.9 -> 97.9 ms); the tables only for the
+    // FP32 Cholesky of patterns up to 12 entries (93.9 -> 93.0 ms; with the
+    // capacity of 8 too, 95.6 ms); both for patterns up to 20 (the uneven
+    // batch: 495 -> 468 ms)
     static const int small_env = [] {
         const char* e = std::getenv("AFSAI_LANE_SMALL");
         return e ? std::atoi(e) : -1;
